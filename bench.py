@@ -1,0 +1,410 @@
+"""Throughput of batched fire-spread simulations on GB300.
+
+One step = one GA generation of the 512 x 512 calibration workload: 256
+parameter vectors drawn from the Gauss(0, 5) initial distribution (Table 1)
+x 16 replicate seeds = 4096 independent simulations from the fixed centre
+ignition, each run to extinction and scored against the reference burnt map
+(Eq. 2 counts fused in the simulation kernel, fitness ratios by a second
+kernel).  Inputs are resident on the device before timing; every step uses
+fresh seeds; L2 is flushed (256 MB write) between timed steps.
+
+Prints one JSON line (see the keys below).  ``--impl reference`` times the
+CPU oracle on the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_1701_03549_gb300 import parallel, synth, workloads  # noqa: E402
+
+METRIC = "CA sims/s"
+UNIT = "sims/s"
+POP, REPS = 256, 16
+SIMS = POP * REPS
+# Algorithmic operations of one trial (one Philox4x32-10 output word plus the
+# screened threshold decision): see the roofline section of the design notes.
+OPS_PER_TRIAL = 37
+ALU_LANES_PER_SM = 128
+WORKLOAD = ("ga_generation_512: 512x512 map, 256 Gauss(0,5) parameter "
+            "vectors x 16 replicates = 4096 simulations/step, centre "
+            "ignition, constant 45 deg wind, target from the reference "
+            "parameters")
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0,
+                "sm_max_mhz": 2070.0}, "fallback"
+
+
+def _kernel_hash():
+    h = hashlib.sha256()
+    for f in ("fire_kernels.cu", "fire_device.cuh", "fire_internal.h"):
+        with open(os.path.join(ROOT, "paper_1701_03549_gb300", "csrc", f),
+                  "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def _committed_traffic():
+    """DRAM bytes per launch of the simulation kernel from the committed ncu
+    summary, or None when the kernel changed since it was captured."""
+    p = os.path.join(ROOT, "profiles", "k_simulate_traffic.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+    except OSError:
+        return None
+    if d.get("source_sha256") != _kernel_hash():
+        return None
+    return d.get("dram_bytes_per_launch")
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,"
+              "clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.proc = None
+        self.path = None
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(index),
+                 f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"),
+                stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) != 7:
+                    continue
+                try:
+                    rows.append((float(parts[0]), float(parts[1]), parts[3:]))
+                except ValueError:
+                    continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                 "sw_power_cap")
+        reasons = sorted({names[i] for _, _, r in rows for i, v in enumerate(r)
+                          if v.lower() in ("active", "1", "yes")})
+        return {"sm_mhz": statistics.median(r[0] for r in rows),
+                "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+_WORKER = {}
+
+
+def _oracle_init(land_args, target):
+    """Spawned worker: build the oracle's covariates and target once."""
+    import oracle
+
+    _WORKER["F"] = oracle.Features(synth.landscape(*land_args))
+    _WORKER["target"] = target
+
+
+def _oracle_job(args):
+    """One oracle simulation in a worker process; returns its step count."""
+    beta, ign, seed = args
+    res, _ = _WORKER["F"].simulate(beta, ign, int(seed),
+                                   target=_WORKER["target"], want_steps=False)
+    return res["steps"]
+
+
+def oracle_throughput(wl, target, nsims: int, cores: int):
+    """Oracle simulations/s on the first nsims simulations of the workload,
+    one simulation per task, `cores` single-threaded worker processes."""
+    import multiprocessing as mp
+
+    p = synth.PRESETS["ga_generation_512"]
+    land_args = (p["H"], p["W"], p["map_seed"], p["wind_seed"])
+    jobs = [(wl.params[i], wl.ignition, int(wl.seeds[i]))
+            for i in range(nsims)]
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores, initializer=_oracle_init,
+                  initargs=(land_args, target)) as pool:
+        pool.map(_oracle_job, [(np.full(5, -1000.0), wl.ignition, 1)] * cores,
+                 chunksize=1)  # wait until every worker is initialised
+        t0 = time.perf_counter()
+        steps = pool.map(_oracle_job, jobs, chunksize=1)
+        dt = time.perf_counter() - t0
+    return nsims / dt, dt, sum(steps)
+
+
+def oracle_target(wl):
+    import oracle
+
+    F = oracle.Features(wl.land)
+    return workloads.pick_target(
+        lambda s: F.simulate(synth.TRUTH_BETA, wl.ignition, s)[1] >= 0,
+        int(F.burnable.sum()))
+
+
+def run_reference(args):
+    rank, world, _ = parallel.env_rank()
+    if rank != 0:
+        return 0
+    cores = os.cpu_count() or 1
+    wl = workloads.ga_generation_512(POP, REPS)
+    _, target = oracle_target(wl)
+    per_step = min(SIMS, 4 * cores)
+    times = []
+    for k in range(args.warmup + args.steps):
+        sub = workloads.ga_generation_512(POP, REPS,
+                                          first_seed=1 + k * SIMS)
+        v, dt, _ = oracle_throughput(sub, target, per_step, cores)
+        if k >= args.warmup:
+            times.append(dt)
+    total = sum(times)
+    value = per_step * args.steps / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "H": 512,
+                                        "W": 512, "sims_per_step": per_step},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores,
+                         "kind": "oracle",
+                         "sample": f"first {per_step} simulations of each "
+                                   "4096-simulation generation"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def run_native(args):
+    import torch
+
+    rank, world, local = parallel.env_rank()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    if not torch.cuda.is_available():
+        print(json.dumps({"metric": METRIC, "error": "no CUDA device"}))
+        return 1
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_1701_03549_gb300 import fire
+
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    ctx = fire.Context(local, stream)
+    first = parallel.rank_seed_offset(rank, SIMS * (args.warmup + args.steps + 2))
+    wl = workloads.ga_generation_512(POP, REPS, first_seed=first)
+    m = ctx.landscape_upload(wl.land)
+    H, W = wl.shape
+    # target: reference parameters, first seed from TARGET_SEED with a
+    # non-trivial fire (simulated on this GPU)
+    burnable = int((wl.land.veg != 0).sum())
+
+    def sim_target(seed):
+        _, bs = m.simulate_batch(np.asarray([synth.TRUTH_BETA]),
+                                 np.asarray([wl.ignition], np.int32),
+                                 np.asarray([seed], np.uint64),
+                                 want_steps=True)
+        return bs[0] >= 0
+
+    tseed, target = workloads.pick_target(sim_target, burnable)
+    m.target_upload(target)
+
+    nsteps = args.warmup + args.steps
+    p_dev = torch.tensor(wl.params, dtype=torch.float64, device=dev)
+    g_dev = torch.tensor(wl.ignitions, dtype=torch.int32, device=dev)
+    seeds_all = [wl.seeds + np.uint64(k * SIMS) for k in range(nsteps)]
+    s_dev = [torch.tensor(s.view(np.int64), device=dev) for s in seeds_all]
+    outs = [torch.zeros((SIMS, 6), dtype=torch.int32, device=dev)
+            for _ in range(nsteps)]
+    fit = [torch.zeros(SIMS, dtype=torch.float64, device=dev)
+           for _ in range(nsteps)]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    torch.cuda.synchronize()
+
+    def step(k):
+        m.simulate_batch(p_dev, g_dev, s_dev[k], device=True, out=outs[k])
+        fire.fire_fitness(ctx, outs[k], fire.FITNESS_JACCARD, device=True,
+                          out=fit[k])
+
+    for k in range(args.warmup):
+        flush.zero_()
+        step(k)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+
+    ev = [(torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = Clocks(local)
+    for j in range(args.steps):
+        k = args.warmup + j
+        flush.zero_()
+        e0, e1, e2 = ev[j]
+        e0.record(stream)
+        m.simulate_batch(p_dev, g_dev, s_dev[k], device=True, out=outs[k])
+        e1.record(stream)
+        fire.fire_fitness(ctx, outs[k], fire.FITNESS_JACCARD, device=True,
+                          out=fit[k])
+        e2.record(stream)
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    if world > 1:
+        torch.distributed.barrier()
+    sim_ms = [ev[j][0].elapsed_time(ev[j][1]) for j in range(args.steps)]
+    step_ms = [ev[j][0].elapsed_time(ev[j][2]) for j in range(args.steps)]
+    total_s = sum(step_ms) / 1e3
+    total_s = parallel.max_over_ranks(total_s, world, dev)
+
+    # statistics of the timed steps
+    res = [fire.results_view(outs[args.warmup + j]) for j in range(args.steps)]
+    steps_sum = sum(int(r["steps"].astype(np.int64).sum()) for r in res)
+    trials_sum = sum(int(r["trials"].astype(np.int64).sum()) for r in res)
+    assert all(int((r["status"] & (fire.STATUS_BAD_IGNITION
+                                    | fire.STATUS_TIMEOUT)).max()) == 0
+               for r in res)
+    sims_total = SIMS * args.steps * world
+    value = sims_total / total_s
+
+    # roofline of the simulation kernel (ALU bound): algorithmic operations
+    # per launch over its mean event-timed duration
+    peaks, peaks_kind = _peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    props = torch.cuda.get_device_properties(dev)
+    peak_ops = props.multi_processor_count * ALU_LANES_PER_SM * sm_max * 1e6
+    mean_sim_s = sum(sim_ms) / len(sim_ms) / 1e3
+    ops_per_launch = trials_sum / args.steps * OPS_PER_TRIAL
+    achieved = ops_per_launch / mean_sim_s
+    traffic = _committed_traffic()
+
+    # end to end through the C ABI with host buffers (pinned)
+    pin_p = torch.from_numpy(wl.params.copy()).pin_memory().numpy()
+    pin_g = torch.from_numpy(wl.ignitions.copy()).pin_memory().numpy()
+    e2e_steps = max(3, min(args.steps, 10))
+    e2e_seeds = [torch.from_numpy((wl.seeds + np.uint64((nsteps + j) * SIMS))
+                                  .view(np.int64)).pin_memory().numpy()
+                 .view(np.uint64) for j in range(e2e_steps)]
+    m.simulate_batch(pin_p, pin_g, e2e_seeds[0])   # warm the staging buffers
+    t0 = time.perf_counter()
+    for j in range(e2e_steps):
+        r, _ = m.simulate_batch(pin_p, pin_g, e2e_seeds[j])
+        f = fire.fire_fitness(ctx, r, fire.FITNESS_JACCARD)
+    e2e_s = time.perf_counter() - t0
+    e2e_s = parallel.max_over_ranks(e2e_s, world, dev)
+    e2e_value = SIMS * e2e_steps * world / e2e_s
+    h2d = SIMS * (40 + 8 + 8) + SIMS * 24
+    d2h = SIMS * 24 + SIMS * 8
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cores = os.cpu_count() or 1
+        tw = workloads.ga_generation_512(POP, REPS, first_seed=first)
+        nsample = min(SIMS, 32 * cores)
+        v, dt, _ = oracle_throughput(tw, target, nsample, cores)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"first {nsample} simulations of one 4096-simulation "
+                         f"generation ({dt:.1f} s wall)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total_s / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "H": H, "W": W,
+                       "sims_per_step": SIMS, "target_seed": tseed,
+                       "target_cells": int(target.sum()),
+                       "l2": "flushed between timed steps (256 MB write)",
+                       "parallelism": f"replicas x{world}"},
+            "cell_updates_per_s": steps_sum * H * W * world / total_s,
+            "trials_per_s": trials_sum * world / total_s,
+            "mean_steps_per_sim": steps_sum / (SIMS * args.steps),
+            "roofline": {"bound": "alu", "achieved": achieved / 1e12,
+                         "peak": peak_ops / 1e12, "unit": "Tops/s",
+                         "frac": achieved / peak_ops, "traffic": traffic,
+                         "kernel": "k_simulate",
+                         "peak_source": f"{props.multi_processor_count} SMs x "
+                                        f"{ALU_LANES_PER_SM} lanes x "
+                                        f"{sm_max:.0f} MHz ({peaks_kind} max "
+                                        "SM clock)",
+                         "ops_per_trial": OPS_PER_TRIAL,
+                         "kernel_ms": 1e3 * mean_sim_s},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": UNIT,
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": 2 * args.steps,
+            "clocks": ck,
+        }
+        print(json.dumps(line))
+    m.free()
+    ctx.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("native", "reference"),
+                    default="native")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_native(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,225 @@
+/*
+ * fire.h -- C ABI of libfire: many independent stochastic cellular-automaton
+ * fire-spread simulations on one GPU, each scored against a target burnt map.
+ *
+ * The method is that of Denham & Laneri, "Using efficient parallelization in
+ * Graphic Processing Units to parameterize stochastic fire propagation
+ * models" (arXiv:1701.03549):
+ *   - Eq. 1 (Sec. 2.1): a burning cell ignites a neighbouring target cell
+ *     with probability p = 1 / (1 + exp(-(b0 + b1 I_f + b2 psi + b3 omega +
+ *     b4 sigma))), where I_f is the forest indicator, psi = cos(aspect - 315
+ *     deg) for slopes above 5 degrees, omega = cos(wind bearing - bearing from
+ *     the burning cell to the target) and sigma = slope / 100 when the target
+ *     lies above the burning cell;
+ *   - Sec. 2.1 rules: cells are burnable, burning, burnt or non-burnable; all
+ *     cells update synchronously; a burning cell burns out after one step; a
+ *     fire runs until no cell burns;
+ *   - Sec. 2.3: random numbers come from the counter-based Philox generator;
+ *   - Eq. 2 (Sec. 2.2): a simulation is scored against the reference burnt
+ *     map by delta = (|A u A*| - |A n A*|) / |A|.
+ *
+ * Conventions used throughout this interface.
+ *   Grid: row-major, row 0 is the northern edge and column 0 the western edge.
+ *     The paper's ignition coordinates (x, y) are (col, row).
+ *   Directions: d = 0..7 is the bearing 45*d degrees (N, NE, E, SE, S, SW, W,
+ *     NW) of the step from a burning cell to a target cell.
+ *   Angles: aspect is the bearing the slope faces (downslope), wind is the
+ *     bearing the wind blows toward, both in degrees clockwise from north.
+ *   Trials: a target cell with k burning neighbours runs k independent trials
+ *     (so it ignites with probability 1 - prod(1 - p_i), Sec. 2.1); the trial
+ *     of target cell c (= row * W + col) at step t from direction d succeeds
+ *     iff u < T, where u is word d % 4 of Philox4x32-10 with counter
+ *     (c, t, d / 4, 0) and key (seed & 0xffffffff, seed >> 32), and
+ *     T = floor(p * 2^32) with p evaluated in double precision in the order
+ *     of Eq. 1.  A simulation's result therefore depends only on its map,
+ *     parameters, ignition and seed: not on its position in a batch, the batch
+ *     size or the launch shape.
+ *   Pointers: every pointer argument is a host pointer unless the call's
+ *     flags contain FIRE_DEVICE_PTRS, in which case every array argument of
+ *     that call (inputs and outputs) is a device pointer valid on the
+ *     context's device.  The caller owns all argument buffers; the library
+ *     copies inputs it keeps (maps, targets) and owns the device memory of
+ *     contexts and maps until fire_destroy / fire_map_free.
+ *   Streams: work is issued on the context's stream.  With host output
+ *     pointers the call returns after the results have been copied back.
+ *     With FIRE_DEVICE_PTRS the call is asynchronous unless FIRE_SYNC is set;
+ *     argument errors that can only be seen on the device (an ignition
+ *     outside the grid) are reported per simulation in fire_result.status.
+ *   Errors: functions return FIRE_OK (0) or a negative FIRE_E* code;
+ *     fire_last_error() describes the last failure on a context.  A context
+ *     may be used by one host thread at a time.
+ *   Limits: H, W >= 1; the grid is processed in 32 x 32 tiles and at most
+ *     FIRE_MAX_TILES tiles are supported; n <= 2^31 - 1 simulations per call.
+ */
+#ifndef FIRE_H
+#define FIRE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Symbols of the ABI are exported with default visibility; everything else
+ * in the library is hidden. */
+#if defined(__GNUC__)
+#define FIRE_API __attribute__((visibility("default")))
+#else
+#define FIRE_API
+#endif
+
+typedef struct fire_ctx fire_ctx;
+typedef struct fire_map fire_map;
+
+/* beta_0 .. beta_4 of Eq. 1 (baseline, forest, aspect, wind, slope). */
+typedef struct { double b[5]; } fire_params;
+
+/* Ignition cell (Sec. 2.1: "ignition point"); the paper's (x, y) = (col, row). */
+typedef struct { int32_t row, col; } fire_cell;
+
+/* Per-simulation result.
+ *   burnt  |A*|: cells that burnt, ignition included;
+ *   inter  |A n A*| against the map's target (0 without a target);
+ *   target |A| of the map's target;
+ *   steps  number of steps in which some cell was burning (1 when only the
+ *          ignition burnt);
+ *   status FIRE_STATUS_* bits;
+ *   trials number of (target cell, burning neighbour) trials evaluated. */
+typedef struct {
+    uint32_t burnt, inter, target, steps, status, trials;
+} fire_result;
+
+enum {
+    FIRE_OK = 0,
+    FIRE_EINVAL = -1,     /* bad argument (sizes, NULL, non-finite params)   */
+    FIRE_ENOMEM = -2,     /* device or host allocation failed                */
+    FIRE_ECUDA = -3,      /* CUDA runtime error (launch, copy, sync)         */
+    FIRE_EIGNITION = -4,  /* host ignition outside the grid / non-burnable   */
+    FIRE_ETIMEOUT = -5,   /* a bounded device wait ran out                   */
+    FIRE_ESTEPS = -6      /* a simulation reached the step cap               */
+};
+
+#define FIRE_MAX_TILES 24576
+
+/* call flags */
+#define FIRE_DEVICE_PTRS 1u  /* array arguments are device pointers          */
+#define FIRE_WANT_STEPS 2u   /* fill burn_step (see fire_simulate_batch)     */
+#define FIRE_SYNC 4u         /* block until the work has finished            */
+
+/* fire_result.status bits */
+#define FIRE_STATUS_BORDER 1u        /* a burnt cell lies on the grid edge   */
+#define FIRE_STATUS_STEP_CAP 2u      /* stopped at the step cap              */
+#define FIRE_STATUS_BAD_IGNITION 4u  /* ignition outside grid/non-burnable   */
+#define FIRE_STATUS_TIMEOUT 8u       /* a bounded device wait ran out        */
+
+/* fitness kinds */
+#define FIRE_FITNESS_PAPER_DELTA 0  /* Eq. 2: (|AuA*| - |AnA*|) / |A|          */
+#define FIRE_FITNESS_JACCARD 1      /* (|AuA*| - |AnA*|) / |AuA*|             */
+
+/* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t
+ * to issue work on (NULL: the context creates and owns a stream; pass
+ * cudaStreamLegacy, (void *)1, for the legacy default stream). */
+FIRE_API int fire_create(fire_ctx **out, int device, void *cuda_stream);
+
+/* Release a context and everything it owns (maps must be freed first). */
+FIRE_API void fire_destroy(fire_ctx *ctx);
+
+/* Text of the last error on this context ("" if none).  Owned by ctx. */
+FIRE_API const char *fire_last_error(const fire_ctx *ctx);
+
+/* Block until all work issued on the context's stream has finished. */
+FIRE_API int fire_sync(fire_ctx *ctx);
+
+/* Launch shape used by later calls: warps per block (1..32) and blocks per
+ * SM (0: as many as fit).  Results do not depend on it (see Trials above). */
+FIRE_API int fire_set_launch(fire_ctx *ctx, int warps_per_block, int blocks_per_sm);
+
+/* Upload the raster maps of one landscape (Sec. 2.1, Fig. 1) and precompute
+ * the per-cell covariates of Eq. 1 on the device:
+ *   veg[H*W]     uint8 vegetation code: 0 non-burnable, 1 forest, 2.. other
+ *   elev[H*W]    elevation (any unit; only comparisons are used)
+ *   slope[H*W]   slope in degrees
+ *   aspect[H*W]  aspect in degrees (downslope bearing)
+ *   wind[H*W]    wind direction in degrees (bearing blown toward)
+ * cell_m is recorded for reference only.  The map starts without a target. */
+FIRE_API int fire_maps_upload(fire_ctx *ctx, int H, int W, float cell_m,
+                     const uint8_t *veg, const float *elev, const float *slope,
+                     const float *aspect, const float *wind, uint32_t flags,
+                     fire_map **out);
+
+/* Free a map and its device memory. */
+FIRE_API void fire_map_free(fire_map *map);
+
+/* Grid shape of a map. */
+FIRE_API int fire_map_shape(const fire_map *map, int *H, int *W);
+
+/* Set the reference (target) burnt map A of Eq. 2: burnt[H*W] uint8, nonzero
+ * means burnt.  |A| is counted on the device. */
+FIRE_API int fire_target_upload(fire_ctx *ctx, fire_map *map, const uint8_t *burnt,
+                       uint32_t flags);
+
+/* Run n independent simulations on one map (Sec. 2.1 rules, Eq. 1, Sec. 2.3)
+ * and score each against the map's target (Eq. 2 counts).
+ *   params[n]     beta vectors (finite)
+ *   ignitions[n]  ignition cells (must be burnable)
+ *   seeds[n]      64-bit Philox keys, one per simulation
+ *   out[n]        results
+ *   burn_step     NULL, or n*H*W int32 written when FIRE_WANT_STEPS is set:
+ *                 step at which each cell ignited (0 for the ignition cell),
+ *                 -1 for burnable cells that did not burn, -2 for
+ *                 non-burnable cells; simulation i occupies
+ *                 burn_step[i*H*W .. (i+1)*H*W).
+ *   max_steps     0 for no cap, else stop a fire after that many steps and
+ *                 set FIRE_STATUS_STEP_CAP.
+ * Host ignitions that are outside the grid or non-burnable make the call
+ * return FIRE_EIGNITION before any work is issued. */
+FIRE_API int fire_simulate_batch(fire_ctx *ctx, const fire_map *map, int n,
+                        const fire_params *params, const fire_cell *ignitions,
+                        const uint64_t *seeds, uint32_t max_steps,
+                        uint32_t flags, fire_result *out, int32_t *burn_step);
+
+/* Fitness of n results (Eq. 2 or the Jaccard distance), double precision,
+ * computed on the device.  A zero denominator gives NaN. */
+FIRE_API int fire_fitness(fire_ctx *ctx, const fire_result *results, int n, int kind,
+                 uint32_t flags, double *out);
+
+/* Debug export of the ignition thresholds T = floor(p 2^32) of Eq. 1 for one
+ * parameter vector: out[d*H*W + cell], int64 in [0, 2^32], every direction d
+ * and cell (whether or not the source cell lies in the grid). */
+FIRE_API int fire_thresholds(fire_ctx *ctx, const fire_map *map,
+                    const fire_params *params, uint32_t flags, int64_t *out);
+
+/* Debug export of the propagation probability p of Eq. 1 per direction and
+ * cell: p32 as the simulation kernel's single-precision screen computes it,
+ * p64 in double precision as the thresholds use it (either may be NULL). */
+FIRE_API int fire_probabilities(fire_ctx *ctx, const fire_map *map,
+                       const fire_params *params, uint32_t flags, float *p32,
+                       double *p64);
+
+/* Debug export of the precomputed covariates: psi, sig (= slope / 100), cos
+ * and sin of the wind bearing (float[H*W] each) and cell flags (uint16[H*W]:
+ * bit d < 8 target higher than the source of direction d, bit 8 forest, bit 9
+ * burnable).  Any pointer may be NULL. */
+FIRE_API int fire_map_features(fire_ctx *ctx, const fire_map *map, uint32_t flags,
+                      float *psi, float *sig, float *cos_wind, float *sin_wind,
+                      uint16_t *cell_flags);
+
+/* Self-check of the single-precision screen that decides most trials: draws
+ * n random (parameters, covariates, direction, u) cases from `seed`, decides
+ * each through the screen and through the double-precision threshold, and
+ * writes counts[0] = cases, counts[1] = cases sent to double precision,
+ * counts[2] = cases where the two decisions differ (must be 0), and
+ * max_abs_dp[0] = largest |p32 - p64| seen.  Host outputs. */
+FIRE_API int fire_screen_selftest(fire_ctx *ctx, uint64_t n, uint64_t seed,
+                         uint64_t counts[3], double max_abs_dp[1]);
+
+/* Debug export of raw Philox4x32-10 blocks: out[4*i .. 4*i+3] is the block of
+ * counter (c0 + i, c1, c2, c3) under key (k0, k1), for i < n. */
+FIRE_API int fire_philox_blocks(fire_ctx *ctx, uint64_t n, const uint32_t ctr[4],
+                       const uint32_t key[2], uint32_t flags, uint32_t *out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FIRE_H */

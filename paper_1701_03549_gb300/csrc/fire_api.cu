@@ -1,0 +1,686 @@
+// C ABI of libfire (see include/fire.h): contexts, maps, argument checks,
+// host <-> device staging and kernel launch configuration.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "fire_internal.h"
+
+using namespace fire;
+
+struct fire_ctx {
+    int device = 0;
+    int num_sms = 0;
+    size_t max_smem_optin = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int warps_per_block = 0;   // 0: heuristic
+    int blocks_per_sm = 0;     // 0: as many as fit
+    std::string err;
+    // device scratch
+    uint32_t *counter = nullptr;     // work counter + error word
+    void *staging = nullptr;         // inputs / outputs of host-pointer calls
+    size_t staging_bytes = 0;
+    uint32_t *gstate = nullptr;      // global-state simulation buffers
+    size_t gstate_bytes = 0;
+    void *host_pinned = nullptr;     // pinned bounce buffer
+    size_t host_pinned_bytes = 0;
+};
+
+struct fire_map {
+    fire_ctx *ctx = nullptr;
+    MapDev dev{};
+    float cell_m = 0.f;
+    float4 *feat = nullptr;
+    uint16_t *cfl = nullptr;
+    uint32_t *blk = nullptr;
+    uint32_t *tgt = nullptr;
+    uint32_t *tgt_count = nullptr;
+    std::vector<uint8_t> burnable_host;
+};
+
+namespace {
+
+int set_err(fire_ctx *ctx, int code, const char *fmt, ...)
+{
+    if (ctx) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        ctx->err = buf;
+    }
+    return code;
+}
+
+int cuda_err(fire_ctx *ctx, cudaError_t e, const char *what)
+{
+    return set_err(ctx, FIRE_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CUDA_TRY(ctx, expr, what)                         \
+    do {                                                  \
+        cudaError_t e_ = (expr);                          \
+        if (e_ != cudaSuccess) return cuda_err(ctx, e_, what); \
+    } while (0)
+
+int ensure_device(fire_ctx *ctx)
+{
+    int cur = -1;
+    cudaError_t e = cudaGetDevice(&cur);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "cudaGetDevice");
+    if (cur != ctx->device) {
+        e = cudaSetDevice(ctx->device);
+        if (e != cudaSuccess) return cuda_err(ctx, e, "cudaSetDevice");
+    }
+    return FIRE_OK;
+}
+
+int grow_device(fire_ctx *ctx, void **buf, size_t *cap, size_t need,
+                const char *what)
+{
+    if (need <= *cap) return FIRE_OK;
+    if (*buf) cudaFree(*buf);
+    *buf = nullptr;
+    *cap = 0;
+    size_t n = need + need / 4 + 256;
+    cudaError_t e = cudaMalloc(buf, n);
+    if (e != cudaSuccess) {
+        *buf = nullptr;
+        return set_err(ctx, FIRE_ENOMEM, "cudaMalloc(%zu) for %s: %s", n, what,
+                       cudaGetErrorString(e));
+    }
+    *cap = n;
+    return FIRE_OK;
+}
+
+int grow_pinned(fire_ctx *ctx, size_t need)
+{
+    if (need <= ctx->host_pinned_bytes) return FIRE_OK;
+    if (ctx->host_pinned) cudaFreeHost(ctx->host_pinned);
+    ctx->host_pinned = nullptr;
+    ctx->host_pinned_bytes = 0;
+    size_t n = need + need / 4 + 256;
+    cudaError_t e = cudaMallocHost(&ctx->host_pinned, n);
+    if (e != cudaSuccess)
+        return set_err(ctx, FIRE_ENOMEM, "cudaMallocHost(%zu): %s", n,
+                       cudaGetErrorString(e));
+    ctx->host_pinned_bytes = n;
+    return FIRE_OK;
+}
+
+size_t round16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+bool valid_map(const fire_map *m) { return m && m->ctx && m->feat; }
+
+}  // namespace
+
+extern "C" {
+
+int fire_create(fire_ctx **out, int device, void *cuda_stream)
+{
+    if (!out) return FIRE_EINVAL;
+    *out = nullptr;
+    fire_ctx *ctx = new (std::nothrow) fire_ctx();
+    if (!ctx) return FIRE_ENOMEM;
+    ctx->device = device;
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || device < 0 || device >= ndev) {
+        delete ctx;
+        return FIRE_ECUDA;
+    }
+    e = cudaSetDevice(device);
+    if (e != cudaSuccess) { delete ctx; return FIRE_ECUDA; }
+    cudaDeviceProp prop;
+    e = cudaGetDeviceProperties(&prop, device);
+    if (e != cudaSuccess) { delete ctx; return FIRE_ECUDA; }
+    ctx->num_sms = prop.multiProcessorCount;
+    ctx->max_smem_optin = prop.sharedMemPerBlockOptin;
+    if (cuda_stream) {
+        ctx->stream = (cudaStream_t)cuda_stream;
+    } else {
+        e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) { delete ctx; return FIRE_ECUDA; }
+        ctx->own_stream = true;
+    }
+    e = cudaMalloc(&ctx->counter, 256);
+    if (e != cudaSuccess) {
+        if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+        delete ctx;
+        return FIRE_ENOMEM;
+    }
+    cudaMemset(ctx->counter, 0, 256);
+    *out = ctx;
+    return FIRE_OK;
+}
+
+void fire_destroy(fire_ctx *ctx)
+{
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    if (ctx->counter) cudaFree(ctx->counter);
+    if (ctx->staging) cudaFree(ctx->staging);
+    if (ctx->gstate) cudaFree(ctx->gstate);
+    if (ctx->host_pinned) cudaFreeHost(ctx->host_pinned);
+    if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+}
+
+const char *fire_last_error(const fire_ctx *ctx)
+{
+    return ctx ? ctx->err.c_str() : "null context";
+}
+
+int fire_sync(fire_ctx *ctx)
+{
+    if (!ctx) return FIRE_EINVAL;
+    int rc = ensure_device(ctx);
+    if (rc) return rc;
+    CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
+    uint32_t errw = 0;
+    CUDA_TRY(ctx, cudaMemcpy(&errw, ctx->counter + 1, 4, cudaMemcpyDeviceToHost),
+             "read error word");
+    if (errw) {
+        cudaMemset(ctx->counter + 1, 0, 4);
+        return set_err(ctx, FIRE_ETIMEOUT, "a bounded device wait ran out");
+    }
+    return FIRE_OK;
+}
+
+int fire_set_launch(fire_ctx *ctx, int warps_per_block, int blocks_per_sm)
+{
+    if (!ctx) return FIRE_EINVAL;
+    if (warps_per_block < 0 || warps_per_block > 16 || blocks_per_sm < 0)
+        return set_err(ctx, FIRE_EINVAL, "bad launch shape %d x %d",
+                       warps_per_block, blocks_per_sm);
+    ctx->warps_per_block = warps_per_block;
+    ctx->blocks_per_sm = blocks_per_sm;
+    return FIRE_OK;
+}
+
+int fire_maps_upload(fire_ctx *ctx, int H, int W, float cell_m,
+                     const uint8_t *veg, const float *elev, const float *slope,
+                     const float *aspect, const float *wind, uint32_t flags,
+                     fire_map **out)
+{
+    if (!ctx || !out) return FIRE_EINVAL;
+    *out = nullptr;
+    if (H <= 0 || W <= 0)
+        return set_err(ctx, FIRE_EINVAL, "grid %d x %d is empty", H, W);
+    if (!veg || !elev || !slope || !aspect || !wind)
+        return set_err(ctx, FIRE_EINVAL, "NULL map pointer");
+    const long long TH = (H + 31) / 32, TW = (W + 31) / 32;
+    if (TH * TW > FIRE_MAX_TILES || (long long)H * W > 0x7fffffffll)
+        return set_err(ctx, FIRE_EINVAL, "grid %d x %d exceeds %d tiles", H, W,
+                       FIRE_MAX_TILES);
+    int rc = ensure_device(ctx);
+    if (rc) return rc;
+    const size_t HW = (size_t)H * W;
+    const bool dev = flags & FIRE_DEVICE_PTRS;
+
+    fire_map *m = new (std::nothrow) fire_map();
+    if (!m) return FIRE_ENOMEM;
+    m->ctx = ctx;
+    m->cell_m = cell_m;
+    m->dev.H = H;
+    m->dev.W = W;
+    m->dev.TH = (int)TH;
+    m->dev.TW = (int)TW;
+    m->dev.ntiles = (int)(TH * TW);
+    const size_t words = (size_t)m->dev.ntiles * 32;
+    cudaError_t e = cudaSuccess;
+    if ((e = cudaMalloc(&m->feat, HW * sizeof(float4))) != cudaSuccess ||
+        (e = cudaMalloc(&m->cfl, HW * sizeof(uint16_t))) != cudaSuccess ||
+        (e = cudaMalloc(&m->blk, words * 4)) != cudaSuccess ||
+        (e = cudaMalloc(&m->tgt, words * 4)) != cudaSuccess ||
+        (e = cudaMalloc(&m->tgt_count, 16)) != cudaSuccess) {
+        fire_map_free(m);
+        return set_err(ctx, FIRE_ENOMEM, "map allocation: %s",
+                       cudaGetErrorString(e));
+    }
+    m->dev.feat = m->feat;
+    m->dev.cfl = m->cfl;
+    m->dev.blk = m->blk;
+    m->dev.tgt = m->tgt;
+    m->dev.tgt_count = m->tgt_count;
+
+    // stage the inputs on the device
+    const uint8_t *dveg = veg;
+    const float *delev = elev, *dslope = slope, *daspect = aspect, *dwind = wind;
+    void *tmp = nullptr;
+    if (!dev) {
+        const size_t bytes = round16(HW) + 4 * round16(HW * 4);
+        if ((e = cudaMalloc(&tmp, bytes)) != cudaSuccess) {
+            fire_map_free(m);
+            return set_err(ctx, FIRE_ENOMEM, "staging: %s", cudaGetErrorString(e));
+        }
+        char *p = (char *)tmp;
+        uint8_t *v = (uint8_t *)p;
+        p += round16(HW);
+        float *f[4];
+        for (int i = 0; i < 4; ++i) { f[i] = (float *)p; p += round16(HW * 4); }
+        const float *src[4] = {elev, slope, aspect, wind};
+        e = cudaMemcpyAsync(v, veg, HW, cudaMemcpyHostToDevice, ctx->stream);
+        for (int i = 0; i < 4 && e == cudaSuccess; ++i)
+            e = cudaMemcpyAsync(f[i], src[i], HW * 4, cudaMemcpyHostToDevice,
+                                ctx->stream);
+        if (e != cudaSuccess) {
+            cudaFree(tmp);
+            fire_map_free(m);
+            return cuda_err(ctx, e, "map upload");
+        }
+        dveg = v;
+        delev = f[0];
+        dslope = f[1];
+        daspect = f[2];
+        dwind = f[3];
+    }
+    e = launch_features(H, W, dveg, delev, dslope, daspect, dwind, m->feat,
+                        m->cfl, ctx->stream);
+    if (e == cudaSuccess) e = launch_blocked(m->dev, dveg, m->blk, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(m->tgt, 0, words * 4, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(m->tgt_count, 0, 16, ctx->stream);
+    // host copy of the burnable mask for validating host ignitions
+    m->burnable_host.resize(HW);
+    if (e == cudaSuccess) {
+        if (dev) {
+            e = cudaMemcpyAsync(m->burnable_host.data(), veg, HW,
+                                cudaMemcpyDeviceToHost, ctx->stream);
+        } else {
+            std::memcpy(m->burnable_host.data(), veg, HW);
+        }
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (tmp) cudaFree(tmp);
+    if (e != cudaSuccess) {
+        fire_map_free(m);
+        return cuda_err(ctx, e, "feature precompute");
+    }
+    *out = m;
+    return FIRE_OK;
+}
+
+void fire_map_free(fire_map *m)
+{
+    if (!m) return;
+    if (m->ctx) cudaSetDevice(m->ctx->device);
+    if (m->feat) cudaFree(m->feat);
+    if (m->cfl) cudaFree(m->cfl);
+    if (m->blk) cudaFree(m->blk);
+    if (m->tgt) cudaFree(m->tgt);
+    if (m->tgt_count) cudaFree(m->tgt_count);
+    delete m;
+}
+
+int fire_map_shape(const fire_map *m, int *H, int *W)
+{
+    if (!valid_map(m)) return FIRE_EINVAL;
+    if (H) *H = m->dev.H;
+    if (W) *W = m->dev.W;
+    return FIRE_OK;
+}
+
+int fire_target_upload(fire_ctx *ctx, fire_map *m, const uint8_t *burnt,
+                       uint32_t flags)
+{
+    if (!ctx || !valid_map(m) || !burnt) return set_err(ctx, FIRE_EINVAL,
+                                                         "bad target arguments");
+    int rc = ensure_device(ctx);
+    if (rc) return rc;
+    const size_t HW = (size_t)m->dev.H * m->dev.W;
+    const uint8_t *src = burnt;
+    void *tmp = nullptr;
+    cudaError_t e;
+    if (!(flags & FIRE_DEVICE_PTRS)) {
+        if ((e = cudaMalloc(&tmp, HW)) != cudaSuccess)
+            return set_err(ctx, FIRE_ENOMEM, "target staging");
+        e = cudaMemcpyAsync(tmp, burnt, HW, cudaMemcpyHostToDevice, ctx->stream);
+        if (e != cudaSuccess) { cudaFree(tmp); return cuda_err(ctx, e, "target copy"); }
+        src = (const uint8_t *)tmp;
+    }
+    e = launch_target(m->dev, src, m->tgt, m->tgt_count, ctx->stream);
+    if (e == cudaSuccess && (tmp || (flags & FIRE_SYNC)))
+        e = cudaStreamSynchronize(ctx->stream);
+    if (tmp) cudaFree(tmp);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "target pack");
+    return FIRE_OK;
+}
+
+int fire_simulate_batch(fire_ctx *ctx, const fire_map *m, int n,
+                        const fire_params *params, const fire_cell *ignitions,
+                        const uint64_t *seeds, uint32_t max_steps,
+                        uint32_t flags, fire_result *out, int32_t *burn_step)
+{
+    if (!ctx) return FIRE_EINVAL;
+    if (!valid_map(m)) return set_err(ctx, FIRE_EINVAL, "invalid map");
+    if (n < 0) return set_err(ctx, FIRE_EINVAL, "n = %d", n);
+    if (n == 0) return FIRE_OK;
+    if (!params || !ignitions || !seeds || !out)
+        return set_err(ctx, FIRE_EINVAL, "NULL argument");
+    const bool want_steps = (flags & FIRE_WANT_STEPS) != 0;
+    if (want_steps && !burn_step)
+        return set_err(ctx, FIRE_EINVAL, "FIRE_WANT_STEPS without burn_step");
+    int rc = ensure_device(ctx);
+    if (rc) return rc;
+    const bool dev = flags & FIRE_DEVICE_PTRS;
+    const int H = m->dev.H, W = m->dev.W;
+    if (!dev) {
+        for (int i = 0; i < n; ++i) {
+            for (int j = 0; j < 5; ++j)
+                if (!std::isfinite(params[i].b[j]))
+                    return set_err(ctx, FIRE_EINVAL,
+                                   "params[%d].b[%d] is not finite", i, j);
+            const fire_cell g = ignitions[i];
+            if (g.row < 0 || g.row >= H || g.col < 0 || g.col >= W ||
+                !m->burnable_host[(size_t)g.row * W + g.col])
+                return set_err(ctx, FIRE_EIGNITION,
+                               "ignition %d (%d, %d) is outside the grid or "
+                               "non-burnable", i, g.row, g.col);
+        }
+    }
+
+    // launch shape
+    const int ntiles = m->dev.ntiles;
+    int nwarps = ctx->warps_per_block;
+    if (nwarps <= 0) nwarps = ntiles <= 64 ? 4 : 8;
+    const SimLayout Ls = sim_layout(ntiles, nwarps, true);
+    const bool smem_state = Ls.total <= ctx->max_smem_optin;
+    const SimLayout L = smem_state ? Ls : sim_layout(ntiles, nwarps, false);
+    const void *kfn = simulate_kernel_ptr(smem_state);
+    CUDA_TRY(ctx, cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)L.total),
+             "cudaFuncSetAttribute");
+    int occ = 0;
+    CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kfn, nwarps * 32,
+                                                                L.total),
+             "occupancy");
+    if (occ < 1) return set_err(ctx, FIRE_EINVAL, "kernel does not fit (%zu B smem)",
+                                L.total);
+    int bps = ctx->blocks_per_sm > 0 ? std::min(ctx->blocks_per_sm, occ) : occ;
+    long long grid = (long long)bps * ctx->num_sms;
+    if (grid > n) grid = n;
+
+    // staging of host arguments
+    const fire_params *dparams = params;
+    const fire_cell *dign = ignitions;
+    const uint64_t *dseeds = seeds;
+    fire_result *dout = out;
+    if (!dev) {
+        const size_t bp = round16((size_t)n * sizeof(fire_params));
+        const size_t bi = round16((size_t)n * sizeof(fire_cell));
+        const size_t bs = round16((size_t)n * sizeof(uint64_t));
+        const size_t bo = round16((size_t)n * sizeof(fire_result));
+        rc = grow_device(ctx, &ctx->staging, &ctx->staging_bytes,
+                         bp + bi + bs + bo, "argument staging");
+        if (rc) return rc;
+        char *p = (char *)ctx->staging;
+        fire_params *sp = (fire_params *)p;
+        fire_cell *si = (fire_cell *)(p + bp);
+        uint64_t *ss = (uint64_t *)(p + bp + bi);
+        dout = (fire_result *)(p + bp + bi + bs);
+        CUDA_TRY(ctx, cudaMemcpyAsync(sp, params, (size_t)n * sizeof(fire_params),
+                                      cudaMemcpyHostToDevice, ctx->stream), "params H2D");
+        CUDA_TRY(ctx, cudaMemcpyAsync(si, ignitions, (size_t)n * sizeof(fire_cell),
+                                      cudaMemcpyHostToDevice, ctx->stream), "ignitions H2D");
+        CUDA_TRY(ctx, cudaMemcpyAsync(ss, seeds, (size_t)n * sizeof(uint64_t),
+                                      cudaMemcpyHostToDevice, ctx->stream), "seeds H2D");
+        dparams = sp;
+        dign = si;
+        dseeds = ss;
+    }
+    int32_t *dsteps = nullptr;
+    void *steps_tmp = nullptr;
+    if (want_steps) {
+        if (dev) {
+            dsteps = burn_step;
+        } else {
+            const size_t bytes = (size_t)n * H * W * sizeof(int32_t);
+            cudaError_t e = cudaMalloc(&steps_tmp, bytes);
+            if (e != cudaSuccess)
+                return set_err(ctx, FIRE_ENOMEM, "burn-step buffer (%zu B)", bytes);
+            dsteps = (int32_t *)steps_tmp;
+        }
+    }
+    if (!smem_state) {
+        const size_t need = (size_t)grid * 2 * ntiles * 128;
+        rc = grow_device(ctx, (void **)&ctx->gstate, &ctx->gstate_bytes, need,
+                         "simulation state");
+        if (rc) { if (steps_tmp) cudaFree(steps_tmp); return rc; }
+    }
+
+    SimLaunch a;
+    a.map = m->dev;
+    a.n = n;
+    a.params = dparams;
+    a.ign = dign;
+    a.seeds = dseeds;
+    a.out = dout;
+    a.burn_step = dsteps;
+    a.work_counter = ctx->counter;
+    a.gstate = ctx->gstate;
+    a.error_word = ctx->counter + 1;
+    a.max_steps = max_steps;
+    cudaError_t e = cudaMemsetAsync(ctx->counter, 0, 4, ctx->stream);
+    if (e == cudaSuccess)
+        e = launch_simulate(a, smem_state, nwarps, (int)grid, L.total, ctx->stream);
+    if (e != cudaSuccess) {
+        if (steps_tmp) cudaFree(steps_tmp);
+        return cuda_err(ctx, e, "simulate launch");
+    }
+    if (!dev) {
+        e = cudaMemcpyAsync(out, dout, (size_t)n * sizeof(fire_result),
+                            cudaMemcpyDeviceToHost, ctx->stream);
+        if (e == cudaSuccess && want_steps)
+            e = cudaMemcpyAsync(burn_step, dsteps,
+                                (size_t)n * H * W * sizeof(int32_t),
+                                cudaMemcpyDeviceToHost, ctx->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+        if (steps_tmp) cudaFree(steps_tmp);
+        if (e != cudaSuccess) return cuda_err(ctx, e, "results D2H");
+        return fire_sync(ctx);
+    }
+    if (flags & FIRE_SYNC) return fire_sync(ctx);
+    return FIRE_OK;
+}
+
+int fire_fitness(fire_ctx *ctx, const fire_result *results, int n, int kind,
+                 uint32_t flags, double *out)
+{
+    if (!ctx) return FIRE_EINVAL;
+    if (n < 0 || !results || !out || (kind != 0 && kind != 1))
+        return set_err(ctx, FIRE_EINVAL, "bad fitness arguments");
+    if (n == 0) return FIRE_OK;
+    int rc = ensure_device(ctx);
+    if (rc) return rc;
+    if (flags & FIRE_DEVICE_PTRS) {
+        CUDA_TRY(ctx, launch_fitness(results, n, kind, out, ctx->stream), "fitness");
+        if (flags & FIRE_SYNC) return fire_sync(ctx);
+        return FIRE_OK;
+    }
+    const size_t br = round16((size_t)n * sizeof(fire_result));
+    const size_t bo = round16((size_t)n * sizeof(double));
+    rc = grow_device(ctx, &ctx->staging, &ctx->staging_bytes, br + bo, "fitness staging");
+    if (rc) return rc;
+    fire_result *dr = (fire_result *)ctx->staging;
+    double *dout = (double *)((char *)ctx->staging + br);
+    CUDA_TRY(ctx, cudaMemcpyAsync(dr, results, (size_t)n * sizeof(fire_result),
+                                  cudaMemcpyHostToDevice, ctx->stream), "results H2D");
+    CUDA_TRY(ctx, launch_fitness(dr, n, kind, dout, ctx->stream), "fitness");
+    CUDA_TRY(ctx, cudaMemcpyAsync(out, dout, (size_t)n * sizeof(double),
+                                  cudaMemcpyDeviceToHost, ctx->stream), "fitness D2H");
+    CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream), "fitness sync");
+    return FIRE_OK;
+}
+
+namespace {
+
+// Runs `body(dev_beta, dev_outs...)` with host or device output buffers.
+int with_beta(fire_ctx *ctx, const fire_params *params, uint32_t flags,
+              double **dbeta)
+{
+    const size_t need = 64;
+    int rc = grow_device(ctx, &ctx->staging, &ctx->staging_bytes, need, "beta");
+    if (rc) return rc;
+    *dbeta = (double *)ctx->staging;
+    CUDA_TRY(ctx, cudaMemcpyAsync(*dbeta, params->b, 5 * sizeof(double),
+                                  (flags & FIRE_DEVICE_PTRS) ? cudaMemcpyDeviceToDevice
+                                                             : cudaMemcpyHostToDevice,
+                                  ctx->stream), "beta copy");
+    return FIRE_OK;
+}
+
+}  // namespace
+
+int fire_thresholds(fire_ctx *ctx, const fire_map *m, const fire_params *params,
+                    uint32_t flags, int64_t *out)
+{
+    if (!ctx) return FIRE_EINVAL;
+    if (!valid_map(m) || !params || !out)
+        return set_err(ctx, FIRE_EINVAL, "bad thresholds arguments");
+    int rc = ensure_device(ctx);
+    if (rc) return rc;
+    const size_t cnt = 8 * (size_t)m->dev.H * m->dev.W;
+    double *dbeta = nullptr;
+    int64_t *dout = out;
+    void *tmp = nullptr;
+    if (!(flags & FIRE_DEVICE_PTRS)) {
+        CUDA_TRY(ctx, cudaMalloc(&tmp, cnt * 8), "threshold buffer");
+        dout = (int64_t *)tmp;
+    }
+    rc = with_beta(ctx, params, flags, &dbeta);
+    if (!rc) {
+        cudaError_t e = launch_thresholds(m->dev, dbeta, dout, ctx->stream);
+        if (e == cudaSuccess && tmp)
+            e = cudaMemcpyAsync(out, dout, cnt * 8, cudaMemcpyDeviceToHost, ctx->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) rc = cuda_err(ctx, e, "thresholds");
+    }
+    if (tmp) cudaFree(tmp);
+    return rc;
+}
+
+int fire_probabilities(fire_ctx *ctx, const fire_map *m, const fire_params *params,
+                       uint32_t flags, float *p32, double *p64)
+{
+    if (!ctx) return FIRE_EINVAL;
+    if (!valid_map(m) || !params || (!p32 && !p64))
+        return set_err(ctx, FIRE_EINVAL, "bad probabilities arguments");
+    int rc = ensure_device(ctx);
+    if (rc) return rc;
+    const size_t cnt = 8 * (size_t)m->dev.H * m->dev.W;
+    float *d32 = p32;
+    double *d64 = p64;
+    void *tmp = nullptr;
+    if (!(flags & FIRE_DEVICE_PTRS)) {
+        CUDA_TRY(ctx, cudaMalloc(&tmp, cnt * 12 + 64), "probability buffer");
+        d64 = p64 ? (double *)tmp : nullptr;
+        d32 = p32 ? (float *)((char *)tmp + cnt * 8) : nullptr;
+    }
+    double *dbeta = nullptr;
+    rc = with_beta(ctx, params, flags, &dbeta);
+    if (!rc) {
+        cudaError_t e = launch_probabilities(m->dev, dbeta, d32, d64, ctx->stream);
+        if (e == cudaSuccess && tmp && p32)
+            e = cudaMemcpyAsync(p32, d32, cnt * 4, cudaMemcpyDeviceToHost, ctx->stream);
+        if (e == cudaSuccess && tmp && p64)
+            e = cudaMemcpyAsync(p64, d64, cnt * 8, cudaMemcpyDeviceToHost, ctx->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) rc = cuda_err(ctx, e, "probabilities");
+    }
+    if (tmp) cudaFree(tmp);
+    return rc;
+}
+
+int fire_map_features(fire_ctx *ctx, const fire_map *m, uint32_t flags,
+                      float *psi, float *sig, float *cos_wind, float *sin_wind,
+                      uint16_t *cell_flags)
+{
+    if (!ctx) return FIRE_EINVAL;
+    if (!valid_map(m)) return set_err(ctx, FIRE_EINVAL, "invalid map");
+    int rc = ensure_device(ctx);
+    if (rc) return rc;
+    const size_t HW = (size_t)m->dev.H * m->dev.W;
+    if (flags & FIRE_DEVICE_PTRS) {
+        CUDA_TRY(ctx, launch_features_export(m->dev, psi, sig, cos_wind, sin_wind,
+                                             cell_flags, ctx->stream), "features");
+        CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream), "features sync");
+        return FIRE_OK;
+    }
+    void *tmp = nullptr;
+    CUDA_TRY(ctx, cudaMalloc(&tmp, HW * 18 + 64), "feature buffer");
+    float *f = (float *)tmp;
+    uint16_t *c = (uint16_t *)((char *)tmp + HW * 16);
+    cudaError_t e = launch_features_export(m->dev, f, f + HW, f + 2 * HW, f + 3 * HW,
+                                           c, ctx->stream);
+    float *dst[4] = {psi, sig, cos_wind, sin_wind};
+    for (int i = 0; i < 4 && e == cudaSuccess; ++i)
+        if (dst[i])
+            e = cudaMemcpyAsync(dst[i], f + i * HW, HW * 4, cudaMemcpyDeviceToHost,
+                                ctx->stream);
+    if (e == cudaSuccess && cell_flags)
+        e = cudaMemcpyAsync(cell_flags, c, HW * 2, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    cudaFree(tmp);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "features export");
+    return FIRE_OK;
+}
+
+int fire_screen_selftest(fire_ctx *ctx, uint64_t n, uint64_t seed,
+                         uint64_t counts[3], double max_abs_dp[1])
+{
+    if (!ctx) return FIRE_EINVAL;
+    if (!counts || !max_abs_dp) return set_err(ctx, FIRE_EINVAL, "NULL output");
+    int rc = ensure_device(ctx);
+    if (rc) return rc;
+    unsigned long long *d = nullptr;
+    CUDA_TRY(ctx, cudaMalloc(&d, 64), "selftest buffer");
+    cudaError_t e = cudaMemsetAsync(d, 0, 64, ctx->stream);
+    if (e == cudaSuccess) e = launch_screen_selftest(n, seed, d, d + 3, ctx->stream);
+    unsigned long long h[4] = {0, 0, 0, 0};
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h, d, 32, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    cudaFree(d);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "screen selftest");
+    for (int i = 0; i < 3; ++i) counts[i] = h[i];
+    double v;
+    std::memcpy(&v, &h[3], 8);
+    max_abs_dp[0] = v;
+    return FIRE_OK;
+}
+
+int fire_philox_blocks(fire_ctx *ctx, uint64_t n, const uint32_t ctr[4],
+                       const uint32_t key[2], uint32_t flags, uint32_t *out)
+{
+    if (!ctx) return FIRE_EINVAL;
+    if (!ctr || !key || !out) return set_err(ctx, FIRE_EINVAL, "NULL argument");
+    if (n == 0) return FIRE_OK;
+    int rc = ensure_device(ctx);
+    if (rc) return rc;
+    const uint4 c = make_uint4(ctr[0], ctr[1], ctr[2], ctr[3]);
+    const uint2 k = make_uint2(key[0], key[1]);
+    if (flags & FIRE_DEVICE_PTRS) {
+        CUDA_TRY(ctx, launch_philox_blocks(n, c, k, out, ctx->stream), "philox");
+        if (flags & FIRE_SYNC) return fire_sync(ctx);
+        return FIRE_OK;
+    }
+    void *tmp = nullptr;
+    CUDA_TRY(ctx, cudaMalloc(&tmp, n * 16), "philox buffer");
+    cudaError_t e = launch_philox_blocks(n, c, k, (uint32_t *)tmp, ctx->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(out, tmp, n * 16, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    cudaFree(tmp);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "philox");
+    return FIRE_OK;
+}
+
+}  // extern "C"

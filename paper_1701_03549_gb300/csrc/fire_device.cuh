@@ -1,0 +1,355 @@
+// Device arithmetic of the fire-spread automaton (arXiv:1701.03549):
+// counter-based random numbers (Sec. 2.3), the ignition probability of Eq. 1
+// evaluated exactly in double precision, and the single-precision screen that
+// decides almost every trial without it.
+//
+// Double-precision definition of a trial threshold (identical, operation by
+// operation, to what the test oracle computes independently):
+//   z = ((((b0 + b1*If) + b2*psi) + b3*omega_d) + b4*sigma_d)
+//   p = 1 / (1 + exp(-z)),  T = floor(p * 2^32) in [0, 2^32]
+// with every step a single IEEE-754 double operation (no contraction), exp
+// evaluated by Cody-Waite reduction and a degree-13 Taylor series, and
+// omega_d = cos(phi_w - 45 d) expanded with the exact values of cos and sin at
+// multiples of 45 degrees.  A trial succeeds iff u < T.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace fire {
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11).  Round:
+//   (hi0, lo0) = M0 * x0, (hi1, lo1) = M1 * x2,
+//   x' = (hi1 ^ x1 ^ k0, lo1, hi0 ^ x3 ^ k1, lo0),
+// with the key advanced by the Weyl increments between rounds.
+constexpr uint32_t kPhiloxM0 = 0xD2511F53u;
+constexpr uint32_t kPhiloxM1 = 0xCD9E8D57u;
+constexpr uint32_t kPhiloxW0 = 0x9E3779B9u;
+constexpr uint32_t kPhiloxW1 = 0xBB67AE85u;
+
+__device__ __forceinline__ uint4 philox4x32_10(uint32_t x0, uint32_t x1,
+                                               uint32_t x2, uint32_t x3,
+                                               uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = kPhiloxM0 * x0;
+        const uint32_t hi0 = __umulhi(kPhiloxM0, x0);
+        const uint32_t lo1 = kPhiloxM1 * x2;
+        const uint32_t hi1 = __umulhi(kPhiloxM1, x2);
+        const uint32_t n0 = hi1 ^ x1 ^ k0;
+        const uint32_t n2 = hi0 ^ x3 ^ k1;
+        x0 = n0; x1 = lo1; x2 = n2; x3 = lo0;
+        k0 += kPhiloxW0;
+        k1 += kPhiloxW1;
+    }
+    return make_uint4(x0, x1, x2, x3);
+}
+
+// ---------------------------------------------------------------------------
+// Double-precision exp on |x| <= 40: x = k ln2 + r, |r| <= ln2/2, Taylor
+// series of e^r to degree 13, times 2^k.  ln2 is split into a 40-bit head
+// (k * head exact) and a tail.
+namespace spec {
+
+constexpr double kInvLn2 = 0x1.71547652b82fep+0;
+constexpr double kLn2Head = 0x1.62e42fefa4000p-1;
+constexpr double kLn2Tail = -0x1.8432a1b0e2634p-43;
+constexpr double kPiOver180 = 0x1.1df46a2529d39p-6;
+constexpr double kHalfSqrt2 = 0x1.6a09e667f3bcdp-1;
+
+// 1/n! rounded to nearest
+constexpr double kF2 = 0x1.0000000000000p-1;
+constexpr double kF3 = 0x1.5555555555555p-3;
+constexpr double kF4 = 0x1.5555555555555p-5;
+constexpr double kF5 = 0x1.1111111111111p-7;
+constexpr double kF6 = 0x1.6c16c16c16c17p-10;
+constexpr double kF7 = 0x1.a01a01a01a01ap-13;
+constexpr double kF8 = 0x1.a01a01a01a01ap-16;
+constexpr double kF9 = 0x1.71de3a556c734p-19;
+constexpr double kF10 = 0x1.27e4fb7789f5cp-22;
+constexpr double kF11 = 0x1.ae64567f544e4p-26;
+constexpr double kF12 = 0x1.1eed8eff8d898p-29;
+constexpr double kF13 = 0x1.6124613a86d09p-33;
+constexpr double kF14 = 0x1.93974a8c07c9dp-37;
+constexpr double kF15 = 0x1.ae7f3e733b81fp-41;
+constexpr double kF16 = 0x1.ae7f3e733b81fp-45;
+constexpr double kF17 = 0x1.952c77030ad4ap-49;
+constexpr double kF18 = 0x1.6827863b97d97p-53;
+constexpr double kF19 = 0x1.2f49b46814157p-57;
+
+__device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
+
+static __device__ __noinline__ double exp_small(double x)
+{
+    const double k = rint(mul(x, kInvLn2));
+    const double r = sub(sub(x, mul(k, kLn2Head)), mul(k, kLn2Tail));
+    double s = kF13;
+    s = add(mul(s, r), kF12);
+    s = add(mul(s, r), kF11);
+    s = add(mul(s, r), kF10);
+    s = add(mul(s, r), kF9);
+    s = add(mul(s, r), kF8);
+    s = add(mul(s, r), kF7);
+    s = add(mul(s, r), kF6);
+    s = add(mul(s, r), kF5);
+    s = add(mul(s, r), kF4);
+    s = add(mul(s, r), kF3);
+    s = add(mul(s, r), kF2);
+    s = add(mul(s, r), 1.0);
+    s = add(mul(s, r), 1.0);
+    const long long ik = (long long)k;
+    const double two_k = __longlong_as_double((ik + 1023LL) << 52);
+    return mul(s, two_k);
+}
+
+// T = floor(2^32 / (1 + exp(-z))) in [0, 2^32].
+static __device__ __noinline__ uint64_t threshold_of_z(double z)
+{
+    if (!(z > -40.0)) return 0ull;
+    if (z >= 40.0) return 1ull << 32;
+    const double e = exp_small(-z);
+    const double p = __ddiv_rn(1.0, add(1.0, e));
+    return (uint64_t)floor(mul(p, 4294967296.0));
+}
+
+// p = 1 / (1 + exp(-z)) in double precision (debug exports); the argument of
+// exp is clamped to [-700, 700], where 2^k stays a normal double.
+__device__ __forceinline__ double logistic(double z)
+{
+    if (z != z) return z;
+    const double zc = fmin(fmax(z, -700.0), 700.0);
+    const double e = exp_small(-zc);
+    return __ddiv_rn(1.0, add(1.0, e));
+}
+
+// cos / sin of an angle in degrees: y = deg - 90 k, |y| <= 45, Taylor series
+// in radians to degree 18 / 19, rotated by the quadrant k mod 4.
+__device__ __forceinline__ double cos_series(double t)
+{
+    const double s2 = mul(t, t);
+    double c = -kF18;
+    c = add(mul(c, s2), kF16);
+    c = add(mul(c, s2), -kF14);
+    c = add(mul(c, s2), kF12);
+    c = add(mul(c, s2), -kF10);
+    c = add(mul(c, s2), kF8);
+    c = add(mul(c, s2), -kF6);
+    c = add(mul(c, s2), kF4);
+    c = add(mul(c, s2), -kF2);
+    c = add(mul(c, s2), 1.0);
+    return c;
+}
+
+__device__ __forceinline__ double sin_series(double t)
+{
+    const double s2 = mul(t, t);
+    double c = -kF19;
+    c = add(mul(c, s2), kF17);
+    c = add(mul(c, s2), -kF15);
+    c = add(mul(c, s2), kF13);
+    c = add(mul(c, s2), -kF11);
+    c = add(mul(c, s2), kF9);
+    c = add(mul(c, s2), -kF7);
+    c = add(mul(c, s2), kF5);
+    c = add(mul(c, s2), -kF3);
+    c = add(mul(c, s2), 1.0);
+    return mul(t, c);
+}
+
+__device__ __forceinline__ void reduce_deg(double deg, double &t, int &q)
+{
+    const double k = rint(__ddiv_rn(deg, 90.0));
+    const double y = sub(deg, mul(k, 90.0));
+    t = mul(y, kPiOver180);
+    const long long kq = (long long)k;
+    q = (int)(((kq % 4) + 4) % 4);
+}
+
+static __device__ __noinline__ double cosd(double deg)
+{
+    double t; int q;
+    reduce_deg(deg, t, q);
+    if (q == 0) return cos_series(t);
+    if (q == 1) return -sin_series(t);
+    if (q == 2) return -cos_series(t);
+    return sin_series(t);
+}
+
+static __device__ __noinline__ double sind(double deg)
+{
+    double t; int q;
+    reduce_deg(deg, t, q);
+    if (q == 0) return sin_series(t);
+    if (q == 1) return cos_series(t);
+    if (q == 2) return -sin_series(t);
+    return -cos_series(t);
+}
+
+// omega_d = cos(phi_w - 45 d) from cw = cos(phi_w), sw = sin(phi_w).
+__device__ __forceinline__ double omega(float cwf, float swf, int d)
+{
+    const double c = (double)cwf, s = (double)swf;
+    switch (d & 7) {
+    case 0: return c;
+    case 1: return mul(add(c, s), kHalfSqrt2);
+    case 2: return s;
+    case 3: return mul(sub(s, c), kHalfSqrt2);
+    case 4: return -c;
+    case 5: return -mul(add(c, s), kHalfSqrt2);
+    case 6: return -s;
+    default: return mul(sub(c, s), kHalfSqrt2);
+    }
+}
+
+// z of Eq. 1 in the equation's order.
+__device__ __forceinline__ double z_of(const double b[5], bool forest,
+                                       float psi, float sig, float cw,
+                                       float sw, bool up, int d)
+{
+    const double If = forest ? 1.0 : 0.0;
+    const double om = omega(cw, sw, d);
+    const double sg = up ? (double)sig : 0.0;
+    double z = add(b[0], mul(b[1], If));
+    z = add(z, mul(b[2], (double)psi));
+    z = add(z, mul(b[3], om));
+    z = add(z, mul(b[4], sg));
+    return z;
+}
+
+}  // namespace spec
+
+// ---------------------------------------------------------------------------
+// Single-precision screen.  z is accumulated as an unevaluated float pair
+// (hi + lo, error-free products by FMA and two-sums), so the only roundings
+// left are that of z to float (relative 2^-24), of the exponential and of
+// the reciprocal.  With p(1-p) <= 1/4 and max_z z p(1-p) < 0.23 this keeps
+// |p32 - p64| below 4e-7; a trial is decided in single precision when
+// |p32 - (u + 1) 2^-32| > kScreenMargin and otherwise re-decided through the
+// exact double-precision threshold (success <=> u < floor(p 2^32) <=>
+// (u + 1) 2^-32 <= p64).
+constexpr float kScreenMargin = 4.0e-6f;
+
+struct ff { float h, l; };
+
+__device__ __forceinline__ ff ff_from_double(double x)
+{
+    const float h = __double2float_rn(x);
+    const float l = __double2float_rn(__dsub_rn(x, (double)h));
+    return {h, l};
+}
+
+// (a.h + a.l) * b, unnormalised; error below 2^-46 |a b|.
+__device__ __forceinline__ ff ff_mul_f(ff a, float b)
+{
+    const float h = __fmul_rn(a.h, b);
+    float l = __fmaf_rn(a.h, b, -h);
+    l = __fmaf_rn(a.l, b, l);
+    return {h, l};
+}
+
+__device__ __forceinline__ ff ff_add(ff a, ff b)
+{
+    const float s = __fadd_rn(a.h, b.h);
+    const float bb = __fsub_rn(s, a.h);
+    const float e = __fadd_rn(__fsub_rn(a.h, __fsub_rn(s, bb)),
+                              __fsub_rn(b.h, bb));
+    const float l = __fadd_rn(e, __fadd_rn(a.l, b.l));
+    const float h = __fadd_rn(s, l);
+    return {h, __fsub_rn(l, __fsub_rn(h, s))};
+}
+
+__device__ __forceinline__ ff ff_neg(ff a) { return {-a.h, -a.l}; }
+
+// (a.h + a.l) * (sqrt(2) / 2) with the constant as a float pair.
+__device__ __forceinline__ ff ff_mul_r2(ff a)
+{
+    constexpr float r2h = 0x1.6a09e6p-1f;
+    constexpr float r2l = 0x1.9fcef4p-27f;  // sqrt(2)/2 - r2h
+    const float h = __fmul_rn(a.h, r2h);
+    float l = __fmaf_rn(a.h, r2h, -h);
+    l = __fmaf_rn(a.h, r2l, l);
+    l = __fmaf_rn(a.l, r2h, l);
+    return {h, l};
+}
+
+// Per-parameter-set constants of the screen.
+struct ScreenParams {
+    ff K[2];   // b0 + b1 * If for If = 0, 1
+    ff b2, b3, b4;
+};
+
+__device__ __forceinline__ ScreenParams screen_params(const double b[5])
+{
+    ScreenParams s;
+    s.K[0] = ff_from_double(b[0]);
+    s.K[1] = ff_from_double(__dadd_rn(b[0], b[1]));
+    s.b2 = ff_from_double(b[2]);
+    s.b3 = ff_from_double(b[3]);
+    s.b4 = ff_from_double(b[4]);
+    return s;
+}
+
+// Per-target-cell partial sums of z.
+struct ScreenCell {
+    ff base;   // b0 + b1 If + b2 psi
+    ff A, B;   // b3 cos(phi_w), b3 sin(phi_w)
+    ff G;      // b4 sig
+};
+
+__device__ __forceinline__ ScreenCell screen_cell(const ScreenParams &sp,
+                                                  bool forest, float psi,
+                                                  float sig, float cw,
+                                                  float sw)
+{
+    ScreenCell c;
+    c.base = ff_add(sp.K[forest ? 1 : 0], ff_mul_f(sp.b2, psi));
+    c.A = ff_mul_f(sp.b3, cw);
+    c.B = ff_mul_f(sp.b3, sw);
+    c.G = ff_mul_f(sp.b4, sig);
+    return c;
+}
+
+// b3 * omega_d as a float pair.
+__device__ __forceinline__ ff screen_wind(const ScreenCell &c, int d)
+{
+    switch (d & 7) {
+    case 0: return c.A;
+    case 1: return ff_mul_r2(ff_add(c.A, c.B));
+    case 2: return c.B;
+    case 3: return ff_mul_r2(ff_add(c.B, ff_neg(c.A)));
+    case 4: return ff_neg(c.A);
+    case 5: return ff_neg(ff_mul_r2(ff_add(c.A, c.B)));
+    case 6: return ff_neg(c.B);
+    default: return ff_mul_r2(ff_add(c.A, ff_neg(c.B)));
+    }
+}
+
+__device__ __forceinline__ float screen_z(const ScreenCell &c, bool up, int d)
+{
+    ff z = ff_add(c.base, screen_wind(c, d));
+    if (up) z = ff_add(z, c.G);
+    return z.h;
+}
+
+__device__ __forceinline__ float screen_p(float z)
+{
+    const float e = __expf(-z);
+    return __frcp_rn(__fadd_rn(1.0f, e));
+}
+
+// Decision of the trial with draw u.  Returns 1 success, 0 failure, -1 when
+// the screen cannot decide and the exact threshold is needed.
+__device__ __forceinline__ int screen_decide(float p32, uint32_t u)
+{
+    const float v = __fmaf_rn(__uint2float_rn(u), 0x1p-32f, 0x1p-32f);
+    const float d = __fsub_rn(p32, v);
+    if (d > kScreenMargin) return 1;
+    if (d < -kScreenMargin) return 0;
+    return -1;
+}
+
+}  // namespace fire

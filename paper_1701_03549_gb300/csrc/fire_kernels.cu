@@ -1,0 +1,862 @@
+// Kernels of libfire: covariate precompute (Sec. 2.1), target packing, the
+// batched fire-spread simulation (Sec. 2.1 rules, Eq. 1, Sec. 2.3) with the
+// burnt-map comparison of Eq. 2 fused into it, fitness, and debug exports.
+//
+// Simulation kernel design (one thread block per simulation at a time,
+// persistent blocks pulling simulations from a global counter):
+//  * State: two bit planes X, Y (one bit per cell each) in 32 x 32-cell tiles,
+//    tile-major, in shared memory when they fit (else in a per-block global
+//    buffer).  A cell's 2-bit code is 00 burnable and unburnt, 11 burnt or
+//    non-burnable, and 10 / 01 burning, the code alternating with the parity
+//    of the step at which the cell ignited.  Within step t the sources are the
+//    cells coded "burning, parity t"; a tile's owner warp writes new cells
+//    with the other parity code and retires the previous step's burning cells
+//    to 11, and neither write changes the parity-t burning set that other
+//    warps read across tile edges.  One block barrier per step suffices.
+//  * Frontier: a worklist of active tiles per step (tiles holding burning
+//    cells, tiles bordering them across an edge that has burning cells, and
+//    tiles whose burning cells must be retired), deduplicated with per-tile
+//    mark bits; quiet tiles are never touched.  The fire is extinct when the
+//    list is empty.
+//  * Per tile (one warp, lane = tile row): eight bit masks of targets with a
+//    burning source in each direction, built with shifts across tile edges;
+//    the candidates are queued and spread evenly over the warp's lanes; each
+//    candidate draws one Philox block per half of its directions (counter =
+//    (cell, step, d/4, 0), key = seed) and decides each trial through the
+//    single-precision screen, falling back to the exact double-precision
+//    threshold only near the decision boundary.
+//  * Fused fitness: |A*| and |A n A*| are accumulated as cells ignite, by
+//    popcount of the new-cell words against the target bit plane.
+#include <cstdio>
+
+#include "fire_device.cuh"
+#include "fire_internal.h"
+
+namespace fire {
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+__constant__ int kDR[8] = {-1, -1, 0, 1, 1, 1, 0, -1};
+__constant__ int kDC[8] = {0, 1, 1, 1, 0, -1, -1, -1};
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Covariates of Eq. 1 for every cell (Sec. 2.1): psi = cos(aspect - 315) for
+// slopes above 5 degrees, sig = slope / 100, cos and sin of the wind bearing,
+// uphill mask per direction (target strictly above the source), forest and
+// burnable flags.
+__global__ void k_features(int H, int W, const uint8_t *__restrict__ veg,
+                           const float *__restrict__ elev,
+                           const float *__restrict__ slope,
+                           const float *__restrict__ aspect,
+                           const float *__restrict__ wind,
+                           float4 *__restrict__ feat,
+                           uint16_t *__restrict__ cfl)
+{
+    const long long n = (long long)H * W;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int r = (int)(i / W), c = (int)(i - (long long)r * W);
+        const float sl = slope[i];
+        const float psi =
+            sl > 5.0f ? __double2float_rn(
+                            spec::cosd(spec::sub((double)aspect[i], 315.0)))
+                      : 0.0f;
+        const float sig = __double2float_rn(__ddiv_rn((double)sl, 100.0));
+        const double wd = (double)wind[i];
+        const float cw = __double2float_rn(spec::cosd(wd));
+        const float sw = __double2float_rn(spec::sind(wd));
+        const float e = elev[i];
+        uint16_t f = 0;
+#pragma unroll
+        for (int d = 0; d < 8; ++d) {
+            const int sr = r - kDR[d], sc = c - kDC[d];
+            if (sr < 0 || sr >= H || sc < 0 || sc >= W) continue;
+            if (e > elev[(long long)sr * W + sc]) f |= (uint16_t)(1u << d);
+        }
+        const uint8_t v = veg[i];
+        if (v == 1) f |= kFlagForest;
+        if (v != 0) f |= kFlagBurnable;
+        feat[i] = make_float4(psi, sig, cw, sw);
+        cfl[i] = f;
+    }
+}
+
+// Tile-major bit plane of a per-cell byte map: bit set where pred(byte).
+template <bool kTarget>
+__global__ void k_pack_bits(int H, int W, int TW, int nwords,
+                            const uint8_t *__restrict__ src,
+                            uint32_t *__restrict__ dst,
+                            uint32_t *__restrict__ count)
+{
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t word = 0;
+    if (w < nwords) {
+        const int k = w >> 5, r = w & 31;
+        const int ti = k / TW, tj = k - ti * TW;
+        const int R = ti * 32 + r;
+        for (int i = 0; i < 32; ++i) {
+            const int C = tj * 32 + i;
+            const bool in = R < H && C < W;
+            bool bit;
+            if (kTarget) bit = in && src[(long long)R * W + C] != 0;
+            else bit = !in || src[(long long)R * W + C] == 0;
+            word |= (uint32_t)bit << i;
+        }
+        dst[w] = word;
+    }
+    if (kTarget) {
+        uint32_t c = __reduce_add_sync(kFull, w < nwords ? __popc(word) : 0u);
+        if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, c);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Simulation kernel helpers.
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, uint32_t n)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(n)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long *bar,
+                                                      uint32_t bytes)
+{
+    asm volatile(
+        "mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(
+            smem_u32(bar)),
+        "r"(bytes)
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar,
+                                              uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bulk (TMA engine) copy global -> shared, completing on an mbarrier.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src,
+                                         uint32_t bytes,
+                                         unsigned long long *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes "
+        "[%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ uint32_t burning(uint32_t x, uint32_t y,
+                                            uint32_t par)
+{
+    return par ? (y & ~x) : (x & ~y);
+}
+
+struct SimCtx {
+    const SimLaunch *a;
+    SimShared *sh;
+    uint32_t *marks;
+    uint16_t *lists;
+    uint32_t *X, *Y;
+    int ntiles;
+    int sim;
+};
+
+// Append tile kk to the worklist of step tn unless it is already there.
+__device__ __forceinline__ void mark_tile(const SimCtx &s, int kk, uint32_t tn)
+{
+    const uint32_t bit = 1u << (2 * (kk & 15) + (tn & 1));
+    const uint32_t old = atomicOr(&s.marks[kk >> 4], bit);
+    if (!(old & bit)) {
+        const uint32_t slot = tn % 3;
+        const uint32_t idx = atomicAdd(&s.sh->count[slot], 1u);
+        s.lists[slot * s.ntiles + idx] = (uint16_t)kk;
+    }
+}
+
+// Decide trials of directions base..base+3 of one candidate cell.
+template <int kBase>
+__device__ __forceinline__ bool try_half(uint32_t dm, uint4 u4,
+                                         const ScreenCell &sc, uint32_t up,
+                                         const double *beta, bool forest,
+                                         const float4 &f)
+{
+    const uint32_t us[4] = {u4.x, u4.y, u4.z, u4.w};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int d = kBase + j;
+        if (!((dm >> d) & 1u)) continue;
+        const bool upd = (up >> d) & 1u;
+        const float p32 = screen_p(screen_z(sc, upd, d));
+        int dec = screen_decide(p32, us[j]);
+        if (dec < 0) {
+            const uint64_t T = spec::threshold_of_z(
+                spec::z_of(beta, forest, f.x, f.y, f.z, f.w, upd, d));
+            dec = (uint64_t)us[j] < T;
+        }
+        if (dec) return true;
+    }
+    return false;
+}
+
+// One active tile of step t, processed by one warp (lane = tile row).
+__device__ __forceinline__ void process_tile(const SimCtx &s, WarpScratch &ws,
+                                             int k, uint32_t t, int lane)
+{
+    const SimLaunch &a = *s.a;
+    const MapDev &m = a.map;
+    SimShared &sh = *s.sh;
+    const int TW = m.TW, TH = m.TH;
+    const int ti = k / TW, tj = k - ti * TW;
+    const uint32_t par = t & 1u;
+    uint32_t *X = s.X, *Y = s.Y;
+
+    if (lane == 0) atomicAnd(&s.marks[k >> 4], ~(1u << (2 * (k & 15) + par)));
+
+    const int w = k * 32 + lane;
+    const uint32_t x = X[w], y = Y[w];
+    const uint32_t b = burning(x, y, par);
+    uint32_t bl = 0, br = 0;
+    if (tj > 0) bl = burning(X[w - 32], Y[w - 32], par);
+    if (tj < TW - 1) br = burning(X[w + 32], Y[w + 32], par);
+    uint32_t bu = __shfl_up_sync(kFull, b, 1);
+    uint32_t blu = __shfl_up_sync(kFull, bl, 1);
+    uint32_t bru = __shfl_up_sync(kFull, br, 1);
+    uint32_t bd = __shfl_down_sync(kFull, b, 1);
+    uint32_t bld = __shfl_down_sync(kFull, bl, 1);
+    uint32_t brd = __shfl_down_sync(kFull, br, 1);
+    if (lane == 0) {
+        bu = blu = bru = 0;
+        if (ti > 0) {
+            const int wa = (k - TW) * 32 + 31;
+            bu = burning(X[wa], Y[wa], par);
+            if (tj > 0) blu = burning(X[wa - 32], Y[wa - 32], par);
+            if (tj < TW - 1) bru = burning(X[wa + 32], Y[wa + 32], par);
+        }
+    }
+    if (lane == 31) {
+        bd = bld = brd = 0;
+        if (ti < TH - 1) {
+            const int wb = (k + TW) * 32;
+            bd = burning(X[wb], Y[wb], par);
+            if (tj > 0) bld = burning(X[wb - 32], Y[wb - 32], par);
+            if (tj < TW - 1) brd = burning(X[wb + 32], Y[wb + 32], par);
+        }
+    }
+    // Targets of row `lane` with a burning source in direction d (the source
+    // of direction d lies at target - off(d)).
+    const uint32_t avail = ~(x | y);
+    uint32_t md[8];
+    md[0] = bd;                               // N : source below
+    md[1] = (bd << 1) | (bld >> 31);          // NE: source below-left
+    md[2] = (b << 1) | (bl >> 31);            // E : source left
+    md[3] = (bu << 1) | (blu >> 31);          // SE: source above-left
+    md[4] = bu;                               // S : source above
+    md[5] = (bu >> 1) | (bru << 31);          // SW: source above-right
+    md[6] = (b >> 1) | (br << 31);            // W : source right
+    md[7] = (bd >> 1) | (brd << 31);          // NW: source below-right
+    uint32_t cand = 0, ntr = 0;
+#pragma unroll
+    for (int d = 0; d < 8; ++d) {
+        md[d] &= avail;
+        cand |= md[d];
+        ntr += __popc(md[d]);
+    }
+    const uint32_t c = __popc(cand);
+    uint32_t incl = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t v = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += v;
+    }
+    const uint32_t total = __shfl_sync(kFull, incl, 31);
+    const uint32_t excl = incl - c;
+
+    uint32_t nrow = 0;
+    if (total) {
+#pragma unroll
+        for (int d = 0; d < 8; ++d) ws.Md[d][lane] = md[d];
+        const uint32_t key0 = sh.key0, key1 = sh.key1;
+        for (uint32_t base = 0; base < total; base += kQueueCap) {
+            const uint32_t lo = max(excl, base);
+            const uint32_t hi = min(excl + c, base + (uint32_t)kQueueCap);
+            if (lo < hi) {
+                uint32_t mm = cand;
+                for (uint32_t q = excl; q < lo; ++q) mm &= mm - 1;
+                for (uint32_t pos = lo; pos < hi; ++pos) {
+                    const int i = __ffs(mm) - 1;
+                    mm &= mm - 1;
+                    ws.q[pos - base] = (uint16_t)((lane << 5) | i);
+                }
+            }
+            __syncwarp();
+            const uint32_t cnt = min(total - base, (uint32_t)kQueueCap);
+            for (uint32_t qi = lane; qi < cnt; qi += 32) {
+                const uint32_t e = ws.q[qi];
+                const int r = (int)(e >> 5), i = (int)(e & 31);
+                uint32_t dm = 0;
+#pragma unroll
+                for (int d = 0; d < 8; ++d) dm |= ((ws.Md[d][r] >> i) & 1u) << d;
+                const int R = ti * 32 + r, C = tj * 32 + i;
+                const uint32_t cell = (uint32_t)R * (uint32_t)m.W + (uint32_t)C;
+                const float4 f = m.feat[cell];
+                const uint32_t fl = m.cfl[cell];
+                const bool forest = (fl & kFlagForest) != 0;
+                const uint32_t up = fl & 0xffu;
+                const ScreenCell sc = screen_cell(sh.sp, forest, f.x, f.y, f.z, f.w);
+                bool ign = false;
+                if (dm & 0x0fu) {
+                    const uint4 u = philox4x32_10(cell, t, 0u, 0u, key0, key1);
+                    ign = try_half<0>(dm, u, sc, up, sh.beta, forest, f);
+                }
+                if (!ign && (dm & 0xf0u)) {
+                    const uint4 u = philox4x32_10(cell, t, 1u, 0u, key0, key1);
+                    ign = try_half<4>(dm, u, sc, up, sh.beta, forest, f);
+                }
+                if (ign) atomicOr(&ws.Nsc[r], 1u << i);
+            }
+            __syncwarp();
+        }
+        nrow = ws.Nsc[lane];
+        ws.Nsc[lane] = 0;
+    }
+
+    // Commit: retire last step's burning cells, write the new ones with the
+    // next parity code.
+    const uint32_t stale = burning(x, y, par ^ 1u);
+    uint32_t nx = x | stale, ny = y | stale;
+    if (par) nx |= nrow;
+    else ny |= nrow;
+    if (nx != x) X[w] = nx;
+    if (ny != y) Y[w] = ny;
+
+    // Fused counts (Eq. 2) and status.
+    const int R = ti * 32 + lane;
+    uint32_t ic = 0;
+    bool border = false;
+    if (nrow) {
+        ic = __popc(nrow & m.tgt[w]);
+        if (R == 0 || R == m.H - 1) border = true;
+        if (tj == 0 && (nrow & 1u)) border = true;
+        if (tj == TW - 1 && ((nrow >> ((m.W - 1) & 31)) & 1u)) border = true;
+        if (a.burn_step) {
+            int32_t *bs = a.burn_step + (long long)s.sim * m.H * m.W +
+                          (long long)R * m.W + tj * 32;
+            uint32_t mm = nrow;
+            while (mm) {
+                const int i = __ffs(mm) - 1;
+                mm &= mm - 1;
+                bs[i] = (int32_t)(t + 1);
+            }
+        }
+    }
+    const uint32_t newc = __reduce_add_sync(kFull, __popc(nrow));
+    const uint32_t icw = __reduce_add_sync(kFull, ic);
+    const uint32_t trw = __reduce_add_sync(kFull, ntr);
+    const bool anyb = __any_sync(kFull, border);
+    if (lane == 0) {
+        if (newc) {
+            atomicAdd(&sh.burnt, newc);
+            if (icw) atomicAdd(&sh.inter, icw);
+            atomicMax(&sh.last_new, t + 1);
+            sh.newflag[(t + 1) % 3] = 1;
+        }
+        if (trw) atomicAdd(&sh.trials, trw);
+        if (anyb) atomicOr(&sh.status, FIRE_STATUS_BORDER);
+    }
+
+    // Worklist of step t + 1.
+    const uint32_t n0 = __shfl_sync(kFull, nrow, 0);
+    const uint32_t n31 = __shfl_sync(kFull, nrow, 31);
+    const bool anyN = __any_sync(kFull, nrow != 0);
+    const bool anyB = __any_sync(kFull, b != 0);
+    const bool anyL = __any_sync(kFull, (nrow & 1u) != 0);
+    const bool anyR = __any_sync(kFull, (nrow >> 31) != 0);
+    if (lane < 9) {
+        int dti = 0, dtj = 0;
+        bool want = false;
+        switch (lane) {
+        case 0: want = anyN || anyB; break;
+        case 1: dti = -1; want = n0 != 0; break;
+        case 2: dti = 1; want = n31 != 0; break;
+        case 3: dtj = -1; want = anyL; break;
+        case 4: dtj = 1; want = anyR; break;
+        case 5: dti = -1; dtj = -1; want = (n0 & 1u) != 0; break;
+        case 6: dti = -1; dtj = 1; want = (n0 >> 31) != 0; break;
+        case 7: dti = 1; dtj = -1; want = (n31 & 1u) != 0; break;
+        default: dti = 1; dtj = 1; want = (n31 >> 31) != 0; break;
+        }
+        const int nti = ti + dti, ntj = tj + dtj;
+        if (want && nti >= 0 && nti < TH && ntj >= 0 && ntj < TW)
+            mark_tile(s, nti * TW + ntj, t + 1);
+    }
+}
+
+template <bool kSmemState>
+__global__ void __launch_bounds__(512) k_simulate(SimLaunch a)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int nwarps = blockDim.x >> 5;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const MapDev &m = a.map;
+    const int ntiles = m.ntiles;
+    const SimLayout L = sim_layout(ntiles, nwarps, kSmemState);
+    SimShared &sh = *reinterpret_cast<SimShared *>(smem + L.header);
+    SimCtx s;
+    s.a = &a;
+    s.sh = &sh;
+    s.marks = reinterpret_cast<uint32_t *>(smem + L.marks);
+    s.lists = reinterpret_cast<uint16_t *>(smem + L.lists);
+    s.ntiles = ntiles;
+    WarpScratch &ws = reinterpret_cast<WarpScratch *>(smem + L.scratch)[warp];
+    if (kSmemState) {
+        s.X = reinterpret_cast<uint32_t *>(smem + L.planes);
+    } else {
+        s.X = a.gstate + (size_t)blockIdx.x * 2 * ntiles * 32;
+    }
+    s.Y = s.X + ntiles * 32;
+    const int nmark = (ntiles + 15) / 16;
+    const uint32_t plane_bytes = (uint32_t)ntiles * 128u;
+    const long long HW = (long long)m.H * m.W;
+    const uint32_t hard_cap = (uint32_t)min(HW + 2, (long long)0x7fffffff);
+
+    for (int i = threadIdx.x; i < 32 * nwarps; i += blockDim.x)
+        reinterpret_cast<WarpScratch *>(smem + L.scratch)[i >> 5].Nsc[i & 31] = 0;
+    if (kSmemState && threadIdx.x == 0) {
+        mbar_init(&sh.mbar, 1);
+        fence_proxy_async_smem();
+    }
+    uint32_t phase = 0;
+    __syncthreads();
+
+    for (;;) {
+        if (threadIdx.x == 0) sh.sim = (int)atomicAdd(a.work_counter, 1u);
+        __syncthreads();
+        const int sim = sh.sim;
+        if (sim >= a.n) break;
+        s.sim = sim;
+
+        // --- set-up of simulation `sim` ---
+        if (threadIdx.x == 0) {
+            const fire_params P = a.params[sim];
+            for (int j = 0; j < 5; ++j) sh.beta[j] = P.b[j];
+            sh.sp = screen_params(P.b);
+            const uint64_t seed = a.seeds[sim];
+            sh.key0 = (uint32_t)seed;
+            sh.key1 = (uint32_t)(seed >> 32);
+            const fire_cell g = a.ign[sim];
+            const bool ok = g.row >= 0 && g.row < m.H && g.col >= 0 &&
+                            g.col < m.W &&
+                            (m.cfl[(long long)g.row * m.W + g.col] &
+                             kFlagBurnable);
+            sh.skip = ok ? 0 : 1;
+            sh.timeout = 0;
+            sh.count[0] = sh.count[1] = sh.count[2] = 0;
+            sh.newflag[0] = 1;
+            sh.newflag[1] = sh.newflag[2] = 0;
+            sh.burnt = 1;
+            sh.inter = 0;
+            sh.trials = 0;
+            sh.status = 0;
+            sh.last_new = 0;
+        }
+        for (int i = threadIdx.x; i < nmark; i += blockDim.x) s.marks[i] = 0;
+        if (kSmemState) {
+            fence_proxy_async_smem();
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                mbar_arrive_expect_tx(&sh.mbar, 2u * plane_bytes);
+                bulk_g2s(s.X, m.blk, plane_bytes, &sh.mbar);
+                bulk_g2s(s.Y, m.blk, plane_bytes, &sh.mbar);
+            }
+        } else {
+            const uint4 *src = reinterpret_cast<const uint4 *>(m.blk);
+            uint4 *dx = reinterpret_cast<uint4 *>(s.X);
+            uint4 *dy = reinterpret_cast<uint4 *>(s.Y);
+            for (int i = threadIdx.x; i < ntiles * 8; i += blockDim.x) {
+                const uint4 v = src[i];
+                dx[i] = v;
+                dy[i] = v;
+            }
+        }
+        if (a.burn_step) {
+            int32_t *bs = a.burn_step + (long long)sim * HW;
+            for (long long i = threadIdx.x; i < HW; i += blockDim.x)
+                bs[i] = (m.cfl[i] & kFlagBurnable) ? -1 : -2;
+        }
+        if (kSmemState) {
+            const long long t0 = clock64();
+            bool done = mbar_try_wait(&sh.mbar, phase);
+            while (!done) {
+                if (clock64() - t0 > (1ll << 31)) break;
+                done = mbar_try_wait(&sh.mbar, phase);
+            }
+            if (!done) atomicOr((unsigned *)&sh.timeout, 1u);
+            phase ^= 1u;
+        }
+        __syncthreads();
+        if (sh.timeout) {
+            if (threadIdx.x == 0) {
+                atomicOr(a.error_word, 1u);
+                fire_result r{};
+                r.status = FIRE_STATUS_TIMEOUT;
+                a.out[sim] = r;
+            }
+            return;  // the copy never completed: leave this block
+        }
+        if (threadIdx.x == 0) {
+            const fire_cell g = a.ign[sim];
+            if (sh.skip) {
+                fire_result r{};
+                r.target = *m.tgt_count;
+                r.status = FIRE_STATUS_BAD_IGNITION;
+                a.out[sim] = r;
+            } else {
+                const int k0 = (g.row >> 5) * m.TW + (g.col >> 5);
+                const int r0 = g.row & 31, i0 = g.col & 31;
+                s.X[k0 * 32 + r0] |= 1u << i0;   // burning, parity 0
+                sh.inter = (m.tgt[k0 * 32 + r0] >> i0) & 1u;
+                if (g.row == 0 || g.row == m.H - 1 || g.col == 0 ||
+                    g.col == m.W - 1)
+                    sh.status |= FIRE_STATUS_BORDER;
+                if (a.burn_step)
+                    a.burn_step[(long long)sim * HW + (long long)g.row * m.W +
+                                g.col] = 0;
+                const int ti = k0 / m.TW, tj = k0 - ti * m.TW;
+                for (int dti = -1; dti <= 1; ++dti) {
+                    for (int dtj = -1; dtj <= 1; ++dtj) {
+                        const bool rowok = dti == 0 || (dti < 0 ? r0 == 0 : r0 == 31);
+                        const bool colok = dtj == 0 || (dtj < 0 ? i0 == 0 : i0 == 31);
+                        const int nti = ti + dti, ntj = tj + dtj;
+                        if (rowok && colok && nti >= 0 && nti < m.TH &&
+                            ntj >= 0 && ntj < m.TW)
+                            mark_tile(s, nti * m.TW + ntj, 0);
+                    }
+                }
+            }
+        }
+        if (sh.skip) {  // uniform: written before the last barrier
+            __syncthreads();
+            continue;
+        }
+
+        // --- steps ---
+        uint32_t t = 0;
+        bool capped = false;
+        for (;; ++t) {
+            __syncthreads();
+            const uint32_t nA = sh.count[t % 3];
+            if (nA == 0) break;
+            const bool burning_now = sh.newflag[t % 3] != 0;
+            if (burning_now && ((a.max_steps && t >= a.max_steps) || t >= hard_cap)) {
+                capped = true;
+                break;
+            }
+            if (threadIdx.x == 0) {
+                sh.count[(t + 2) % 3] = 0;
+                sh.newflag[(t + 2) % 3] = 0;
+            }
+            const uint16_t *list = s.lists + (t % 3) * ntiles;
+            for (uint32_t li = warp; li < nA; li += nwarps)
+                process_tile(s, ws, list[li], t, lane);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            fire_result r;
+            r.burnt = sh.burnt;
+            r.inter = sh.inter;
+            r.target = *m.tgt_count;
+            r.steps = capped ? t : sh.last_new + 1;
+            r.status = sh.status | (capped ? FIRE_STATUS_STEP_CAP : 0u);
+            r.trials = sh.trials;
+            a.out[sim] = r;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Fitness of Eq. 2 (kind 0) or Jaccard distance (kind 1).
+__global__ void k_fitness(const fire_result *__restrict__ r, int n, int kind,
+                          double *__restrict__ out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const fire_result q = r[i];
+    const double uni = __dsub_rn(__dadd_rn((double)q.target, (double)q.burnt),
+                                 (double)q.inter);
+    const double sym = __dsub_rn(uni, (double)q.inter);
+    const double den = kind == 0 ? (double)q.target : uni;
+    out[i] = den == 0.0 ? __longlong_as_double(0x7ff8000000000000ll)
+                        : __ddiv_rn(sym, den);
+}
+
+// Exact thresholds of every (direction, cell).
+__global__ void k_thresholds(MapDev m, const double *__restrict__ beta_dev,
+                             int64_t *__restrict__ out)
+{
+    const long long HW = (long long)m.H * m.W;
+    double b[5];
+    for (int j = 0; j < 5; ++j) b[j] = beta_dev[j];
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+         idx < 8 * HW; idx += (long long)gridDim.x * blockDim.x) {
+        const int d = (int)(idx / HW);
+        const long long i = idx - d * HW;
+        const float4 f = m.feat[i];
+        const uint32_t fl = m.cfl[i];
+        const double z = spec::z_of(b, fl & kFlagForest, f.x, f.y, f.z, f.w,
+                                    (fl >> d) & 1u, d);
+        out[idx] = (int64_t)spec::threshold_of_z(z);
+    }
+}
+
+__global__ void k_probabilities(MapDev m, const double *__restrict__ beta_dev,
+                                float *__restrict__ p32,
+                                double *__restrict__ p64)
+{
+    const long long HW = (long long)m.H * m.W;
+    double b[5];
+    for (int j = 0; j < 5; ++j) b[j] = beta_dev[j];
+    const ScreenParams sp = screen_params(b);
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+         idx < 8 * HW; idx += (long long)gridDim.x * blockDim.x) {
+        const int d = (int)(idx / HW);
+        const long long i = idx - d * HW;
+        const float4 f = m.feat[i];
+        const uint32_t fl = m.cfl[i];
+        const bool forest = fl & kFlagForest, up = (fl >> d) & 1u;
+        if (p32) {
+            const ScreenCell sc = screen_cell(sp, forest, f.x, f.y, f.z, f.w);
+            p32[idx] = screen_p(screen_z(sc, up, d));
+        }
+        if (p64)
+            p64[idx] = spec::logistic(
+                spec::z_of(b, forest, f.x, f.y, f.z, f.w, up, d));
+    }
+}
+
+__global__ void k_features_export(MapDev m, float *psi, float *sig, float *cw,
+                                  float *sw, uint16_t *cfl)
+{
+    const long long HW = (long long)m.H * m.W;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < HW;
+         i += (long long)gridDim.x * blockDim.x) {
+        const float4 f = m.feat[i];
+        if (psi) psi[i] = f.x;
+        if (sig) sig[i] = f.y;
+        if (cw) cw[i] = f.z;
+        if (sw) sw[i] = f.w;
+        if (cfl) cfl[i] = m.cfl[i];
+    }
+}
+
+// Randomised check of the single-precision screen against the exact
+// threshold: uniform and Gaussian parameters, random covariates, and draws
+// both uniform and placed next to the exact threshold.
+__global__ void k_screen_selftest(uint64_t n, uint64_t seed,
+                                  unsigned long long *counts,
+                                  unsigned long long *max_dp_bits)
+{
+    const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    unsigned long long local[3] = {0, 0, 0};
+    double local_max = 0.0;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint4 r1 = philox4x32_10((uint32_t)i, (uint32_t)(i >> 32), 1u, 0u, k0, k1);
+        const uint4 r2 = philox4x32_10((uint32_t)i, (uint32_t)(i >> 32), 2u, 0u, k0, k1);
+        const uint4 r3 = philox4x32_10((uint32_t)i, (uint32_t)(i >> 32), 3u, 0u, k0, k1);
+        const uint32_t rs[5] = {r1.x, r1.y, r1.z, r1.w, r2.x};
+        double b[5];
+        const bool gauss = (r2.y >> 31) & 1u;
+        for (int j = 0; j < 5; ++j) {
+            const double u = ((double)rs[j] + 0.5) * 0x1p-32;
+            // uniform on [-30, 30], or a Gaussian-looking sum (sd ~5)
+            b[j] = gauss ? (u - 0.5) * 17.32 + ((double)(rs[(j + 1) % 5] >> 16) /
+                                                     65536.0 - 0.5) * 17.32
+                         : -30.0 + 60.0 * u;
+        }
+        const bool forest = r2.y & 1u;
+        const int d = (int)((r2.y >> 1) & 7u);
+        const bool up = (r2.y >> 4) & 1u;
+        const float psi = (float)(((double)(r2.z >> 8) * 0x1p-24) * 2.0 - 1.0);
+        const float sig = (float)(0.9 * (double)(r2.w >> 8) * 0x1p-24);
+        const double ang = 360.0 * (double)(r3.x >> 8) * 0x1p-24;
+        const float cw = __double2float_rn(spec::cosd(ang));
+        const float sw = __double2float_rn(spec::sind(ang));
+        const double z = spec::z_of(b, forest, psi, sig, cw, sw, up, d);
+        const uint64_t T = spec::threshold_of_z(z);
+        uint32_t u;
+        if ((r3.y & 3u) == 0) {
+            u = r3.z;
+        } else {
+            const int64_t off = (int64_t)(r3.z % 200001u) - 100000;
+            int64_t v = (int64_t)T + off;
+            v = v < 0 ? 0 : (v > 0xffffffffll ? 0xffffffffll : v);
+            u = (uint32_t)v;
+        }
+        const ScreenParams sp = screen_params(b);
+        const ScreenCell sc = screen_cell(sp, forest, psi, sig, cw, sw);
+        const float p32 = screen_p(screen_z(sc, up, d));
+        int dec = screen_decide(p32, u);
+        const bool exact = (uint64_t)u < T;
+        local[0]++;
+        if (dec < 0) {
+            local[1]++;
+            dec = exact;
+        }
+        if ((dec != 0) != exact) local[2]++;
+        const double dp = fabs((double)p32 - spec::logistic(z));
+        local_max = fmax(local_max, dp);
+    }
+    for (int j = 0; j < 3; ++j) {
+        unsigned long long v = local[j];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
+        if ((threadIdx.x & 31) == 0 && v) atomicAdd(&counts[j], v);
+    }
+    for (int o = 16; o > 0; o >>= 1)
+        local_max = fmax(local_max, __shfl_down_sync(kFull, local_max, o));
+    if ((threadIdx.x & 31) == 0)
+        atomicMax(max_dp_bits, (unsigned long long)__double_as_longlong(local_max));
+}
+
+__global__ void k_philox_blocks(uint64_t n, uint4 ctr, uint2 key, uint32_t *out)
+{
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint4 r = philox4x32_10(ctr.x + (uint32_t)i, ctr.y, ctr.z, ctr.w,
+                                      key.x, key.y);
+        reinterpret_cast<uint4 *>(out)[i] = r;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Launchers.
+
+static int grid_for(long long n, int block)
+{
+    long long g = (n + block - 1) / block;
+    if (g < 1) g = 1;
+    if (g > 152 * 32) g = 152 * 32;
+    return (int)g;
+}
+
+cudaError_t launch_features(int H, int W, const uint8_t *veg, const float *elev,
+                            const float *slope, const float *aspect,
+                            const float *wind, float4 *feat, uint16_t *cfl,
+                            cudaStream_t st)
+{
+    const long long n = (long long)H * W;
+    k_features<<<grid_for(n, 256), 256, 0, st>>>(H, W, veg, elev, slope, aspect,
+                                                 wind, feat, cfl);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_blocked(const MapDev &m, const uint8_t *veg, uint32_t *blk,
+                           cudaStream_t st)
+{
+    const int nw = m.ntiles * 32;
+    k_pack_bits<false><<<(nw + 255) / 256, 256, 0, st>>>(m.H, m.W, m.TW, nw,
+                                                         veg, blk, nullptr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_target(const MapDev &m, const uint8_t *burnt, uint32_t *tgt,
+                          uint32_t *tgt_count, cudaStream_t st)
+{
+    const int nw = m.ntiles * 32;
+    cudaError_t e = cudaMemsetAsync(tgt_count, 0, sizeof(uint32_t), st);
+    if (e != cudaSuccess) return e;
+    k_pack_bits<true><<<(nw + 255) / 256, 256, 0, st>>>(m.H, m.W, m.TW, nw,
+                                                        burnt, tgt, tgt_count);
+    return cudaGetLastError();
+}
+
+const void *simulate_kernel_ptr(bool smem_state)
+{
+    return smem_state ? (const void *)k_simulate<true>
+                      : (const void *)k_simulate<false>;
+}
+
+cudaError_t launch_simulate(const SimLaunch &a, bool smem_state, int nwarps,
+                            int grid, size_t smem_bytes, cudaStream_t st)
+{
+    if (smem_state)
+        k_simulate<true><<<grid, nwarps * 32, smem_bytes, st>>>(a);
+    else
+        k_simulate<false><<<grid, nwarps * 32, smem_bytes, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fitness(const fire_result *r, int n, int kind, double *out,
+                           cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    k_fitness<<<(n + 255) / 256, 256, 0, st>>>(r, n, kind, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_thresholds(const MapDev &m, const double *beta_dev,
+                              int64_t *out, cudaStream_t st)
+{
+    k_thresholds<<<grid_for(8ll * m.H * m.W, 256), 256, 0, st>>>(m, beta_dev,
+                                                                 out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_probabilities(const MapDev &m, const double *beta_dev,
+                                 float *p32, double *p64, cudaStream_t st)
+{
+    k_probabilities<<<grid_for(8ll * m.H * m.W, 256), 256, 0, st>>>(
+        m, beta_dev, p32, p64);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_features_export(const MapDev &m, float *psi, float *sig,
+                                   float *cw, float *sw, uint16_t *cfl,
+                                   cudaStream_t st)
+{
+    k_features_export<<<grid_for((long long)m.H * m.W, 256), 256, 0, st>>>(
+        m, psi, sig, cw, sw, cfl);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_screen_selftest(uint64_t n, uint64_t seed,
+                                   unsigned long long *counts,
+                                   unsigned long long *max_dp_bits,
+                                   cudaStream_t st)
+{
+    k_screen_selftest<<<152 * 8, 256, 0, st>>>(n, seed, counts, max_dp_bits);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_philox_blocks(uint64_t n, uint4 ctr, uint2 key,
+                                 uint32_t *out, cudaStream_t st)
+{
+    k_philox_blocks<<<grid_for((long long)n, 256), 256, 0, st>>>(n, ctr, key,
+                                                                 out);
+    return cudaGetLastError();
+}
+
+}  // namespace fire

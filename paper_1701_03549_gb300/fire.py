@@ -1,0 +1,359 @@
+"""Thin Python binding of libfire's C ABI (include/fire.h).
+
+Argument marshalling only: every step of the simulation path runs in the
+CUDA library.  Functions keep the C names (``fire_create``,
+``fire_maps_upload``, ``fire_simulate_batch`` ...).  Host arrays are numpy
+arrays; device arrays are CUDA ``torch.Tensor`` objects, passed with
+``device=True`` (FIRE_DEVICE_PTRS).  PyTorch supplies device memory and the
+stream only.
+
+Loading fails loudly when libfire.so has not been built: there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libfire.so")
+
+FIRE_OK = 0
+FIRE_EINVAL = -1
+FIRE_ENOMEM = -2
+FIRE_ECUDA = -3
+FIRE_EIGNITION = -4
+FIRE_ETIMEOUT = -5
+FIRE_ESTEPS = -6
+
+FIRE_DEVICE_PTRS = 1
+FIRE_WANT_STEPS = 2
+FIRE_SYNC = 4
+
+STATUS_BORDER = 1
+STATUS_STEP_CAP = 2
+STATUS_BAD_IGNITION = 4
+STATUS_TIMEOUT = 8
+
+# cudaStreamLegacy: the legacy default stream of the current context
+CUDA_STREAM_LEGACY = 1
+
+FITNESS_PAPER_DELTA = 0
+FITNESS_JACCARD = 1
+
+RESULT_FIELDS = ("burnt", "inter", "target", "steps", "status", "trials")
+RESULT_DTYPE = np.dtype([(f, "<u4") for f in RESULT_FIELDS])
+
+EXPORTED = (
+    "fire_create", "fire_destroy", "fire_last_error", "fire_sync",
+    "fire_set_launch", "fire_maps_upload", "fire_map_free", "fire_map_shape",
+    "fire_target_upload", "fire_simulate_batch", "fire_fitness",
+    "fire_thresholds", "fire_probabilities", "fire_map_features",
+    "fire_screen_selftest", "fire_philox_blocks",
+)
+
+
+class FireError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"libfire error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libfire.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(
+            f"{path} is missing: build it with __graft_entry__.build() "
+            "(the CUDA library is required; there is no CPU fallback)")
+    L = C.CDLL(path)
+    vp, i32, u32, u64 = C.c_void_p, C.c_int, C.c_uint32, C.c_uint64
+    sig = {
+        "fire_create": (i32, [C.POINTER(vp), i32, vp]),
+        "fire_destroy": (None, [vp]),
+        "fire_last_error": (C.c_char_p, [vp]),
+        "fire_sync": (i32, [vp]),
+        "fire_set_launch": (i32, [vp, i32, i32]),
+        "fire_maps_upload": (i32, [vp, i32, i32, C.c_float, vp, vp, vp, vp, vp,
+                                   u32, C.POINTER(vp)]),
+        "fire_map_free": (None, [vp]),
+        "fire_map_shape": (i32, [vp, C.POINTER(i32), C.POINTER(i32)]),
+        "fire_target_upload": (i32, [vp, vp, vp, u32]),
+        "fire_simulate_batch": (i32, [vp, vp, i32, vp, vp, vp, u32, u32, vp,
+                                      vp]),
+        "fire_fitness": (i32, [vp, vp, i32, i32, u32, vp]),
+        "fire_thresholds": (i32, [vp, vp, vp, u32, vp]),
+        "fire_probabilities": (i32, [vp, vp, vp, u32, vp, vp]),
+        "fire_map_features": (i32, [vp, vp, u32, vp, vp, vp, vp, vp]),
+        "fire_screen_selftest": (i32, [vp, u64, u64, vp, vp]),
+        "fire_philox_blocks": (i32, [vp, u64, vp, vp, u32, vp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+# ---------------------------------------------------------------------------
+# marshalling helpers
+
+def _is_tensor(a) -> bool:
+    try:
+        import torch
+    except ImportError:  # pragma: no cover
+        return False
+    return isinstance(a, torch.Tensor)
+
+
+def _ptr(a):
+    """Address of a numpy array or torch tensor (None passes NULL)."""
+    if a is None:
+        return None
+    if _is_tensor(a):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr()
+    if not a.flags["C_CONTIGUOUS"]:
+        raise ValueError("array must be C-contiguous")
+    return a.ctypes.data
+
+
+def _host(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+class Context:
+    """A libfire context (fire_create) bound to one device and stream."""
+
+    def __init__(self, device: int = 0, stream=None):
+        self.lib = load()
+        h = C.c_void_p()
+        s = None
+        if stream is not None:
+            s = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(
+                stream)
+            if s == 0:
+                # torch's default stream is the legacy default stream; NULL
+                # would ask the library for a stream of its own
+                s = CUDA_STREAM_LEGACY
+        rc = self.lib.fire_create(C.byref(h), int(device), s)
+        if rc != FIRE_OK:
+            raise FireError(rc, "fire_create failed")
+        self.h = h
+        self.device = device
+
+    # -- errors
+    def check(self, rc):
+        if rc != FIRE_OK:
+            msg = self.lib.fire_last_error(self.h)
+            raise FireError(rc, msg.decode() if msg else "")
+        return rc
+
+    def close(self):
+        if self.h:
+            self.lib.fire_destroy(self.h)
+            self.h = None
+
+    def __del__(self):  # pragma: no cover - best effort
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def sync(self):
+        return self.check(self.lib.fire_sync(self.h))
+
+    def set_launch(self, warps_per_block: int = 0, blocks_per_sm: int = 0):
+        return self.check(self.lib.fire_set_launch(self.h, warps_per_block,
+                                                   blocks_per_sm))
+
+    # -- maps
+    def maps_upload(self, veg, elev, slope, aspect, wind, cell_m=30.0,
+                    device=False):
+        if device:
+            arrs = (veg, elev, slope, aspect, wind)
+            H, W = veg.shape
+            flags = FIRE_DEVICE_PTRS
+        else:
+            arrs = (_host(veg, np.uint8), _host(elev, np.float32),
+                    _host(slope, np.float32), _host(aspect, np.float32),
+                    _host(wind, np.float32))
+            H, W = arrs[0].shape
+            flags = 0
+        h = C.c_void_p()
+        self.check(self.lib.fire_maps_upload(
+            self.h, H, W, float(cell_m), *[_ptr(a) for a in arrs], flags,
+            C.byref(h)))
+        return Map(self, h, H, W)
+
+    def landscape_upload(self, land):
+        return self.maps_upload(land.veg, land.elev, land.slope, land.aspect,
+                                land.wind, cell_m=land.cell_m)
+
+
+class Map:
+    """A device-resident landscape (fire_maps_upload)."""
+
+    def __init__(self, ctx: Context, h, H: int, W: int):
+        self.ctx, self.h, self.H, self.W = ctx, h, H, W
+
+    def free(self):
+        if self.h:
+            self.ctx.lib.fire_map_free(self.h)
+            self.h = None
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def target_upload(self, burnt, device=False):
+        if device:
+            self.ctx.check(self.ctx.lib.fire_target_upload(
+                self.ctx.h, self.h, _ptr(burnt), FIRE_DEVICE_PTRS))
+        else:
+            b = _host(np.asarray(burnt) != 0, np.uint8)
+            self.ctx.check(self.ctx.lib.fire_target_upload(
+                self.ctx.h, self.h, _ptr(b), 0))
+
+    def simulate_batch(self, params, ignitions, seeds, want_steps=False,
+                       max_steps=0, device=False, out=None, burn_step=None,
+                       sync=False):
+        """fire_simulate_batch.
+
+        Host mode: params (n, 5) float64, ignitions (n, 2) int32 (row, col),
+        seeds (n,) uint64; returns (results structured array, burn_step or
+        None).  Device mode: torch CUDA tensors params (n, 5) float64,
+        ignitions (n, 2) int32, seeds (n,) int64 (bit pattern of the uint64
+        seeds), out (n, 6) int32 (bit pattern of the uint32 results), optional
+        burn_step (n, H, W) int32; returns (out, burn_step).
+        """
+        lib = self.ctx.lib
+        flags = FIRE_WANT_STEPS if want_steps else 0
+        if device:
+            n = int(params.shape[0])
+            flags |= FIRE_DEVICE_PTRS | (FIRE_SYNC if sync else 0)
+            self.ctx.check(lib.fire_simulate_batch(
+                self.ctx.h, self.h, n, _ptr(params), _ptr(ignitions),
+                _ptr(seeds), int(max_steps), flags, _ptr(out),
+                _ptr(burn_step)))
+            return out, burn_step
+        p = _host(params, np.float64).reshape(-1, 5)
+        n = p.shape[0]
+        g = _host(ignitions, np.int32).reshape(n, 2)
+        s = _host(seeds, np.uint64).reshape(n)
+        res = np.zeros(n, RESULT_DTYPE)
+        bs = np.zeros((n, self.H, self.W), np.int32) if want_steps else None
+        self.ctx.check(lib.fire_simulate_batch(
+            self.ctx.h, self.h, n, _ptr(p), _ptr(g), _ptr(s), int(max_steps),
+            flags, _ptr(res), _ptr(bs)))
+        return res, bs
+
+    def thresholds(self, beta):
+        b = _host(beta, np.float64).reshape(5)
+        out = np.zeros((8, self.H, self.W), np.int64)
+        self.ctx.check(self.ctx.lib.fire_thresholds(
+            self.ctx.h, self.h, _ptr(b), 0, _ptr(out)))
+        return out
+
+    def probabilities(self, beta):
+        b = _host(beta, np.float64).reshape(5)
+        p32 = np.zeros((8, self.H, self.W), np.float32)
+        p64 = np.zeros((8, self.H, self.W), np.float64)
+        self.ctx.check(self.ctx.lib.fire_probabilities(
+            self.ctx.h, self.h, _ptr(b), 0, _ptr(p32), _ptr(p64)))
+        return p32, p64
+
+    def features(self):
+        H, W = self.H, self.W
+        psi = np.zeros((H, W), np.float32)
+        sig = np.zeros((H, W), np.float32)
+        cw = np.zeros((H, W), np.float32)
+        sw = np.zeros((H, W), np.float32)
+        fl = np.zeros((H, W), np.uint16)
+        self.ctx.check(self.ctx.lib.fire_map_features(
+            self.ctx.h, self.h, 0, _ptr(psi), _ptr(sig), _ptr(cw), _ptr(sw),
+            _ptr(fl)))
+        return dict(psi=psi, sig=sig, cw=cw, sw=sw, flags=fl)
+
+
+# ---------------------------------------------------------------------------
+# functions with the C names
+
+def fire_create(device: int = 0, stream=None) -> Context:
+    return Context(device, stream)
+
+
+def fire_maps_upload(ctx: Context, veg, elev, slope, aspect, wind,
+                     cell_m=30.0, device=False) -> Map:
+    return ctx.maps_upload(veg, elev, slope, aspect, wind, cell_m, device)
+
+
+def fire_target_upload(ctx: Context, m: Map, burnt, device=False):
+    return m.target_upload(burnt, device)
+
+
+def fire_simulate_batch(ctx: Context, m: Map, params, ignitions, seeds,
+                        **kw):
+    return m.simulate_batch(params, ignitions, seeds, **kw)
+
+
+def fire_fitness(ctx: Context, results, kind=FITNESS_PAPER_DELTA,
+                 device=False, out=None):
+    lib = ctx.lib
+    if device:
+        n = int(results.shape[0])
+        ctx.check(lib.fire_fitness(ctx.h, _ptr(results), n, int(kind),
+                                   FIRE_DEVICE_PTRS, _ptr(out)))
+        return out
+    r = np.ascontiguousarray(results, RESULT_DTYPE)
+    o = np.zeros(r.shape[0], np.float64)
+    ctx.check(lib.fire_fitness(ctx.h, _ptr(r), r.shape[0], int(kind), 0,
+                               _ptr(o)))
+    return o
+
+
+def fire_thresholds(ctx: Context, m: Map, beta):
+    return m.thresholds(beta)
+
+
+def fire_probabilities(ctx: Context, m: Map, beta):
+    return m.probabilities(beta)
+
+
+def fire_map_features(ctx: Context, m: Map):
+    return m.features()
+
+
+def fire_screen_selftest(ctx: Context, n: int, seed: int):
+    counts = np.zeros(3, np.uint64)
+    mx = np.zeros(1, np.float64)
+    ctx.check(ctx.lib.fire_screen_selftest(ctx.h, int(n), int(seed),
+                                           _ptr(counts), _ptr(mx)))
+    return dict(cases=int(counts[0]), fallbacks=int(counts[1]),
+                flips=int(counts[2]), max_abs_dp=float(mx[0]))
+
+
+def fire_philox_blocks(ctx: Context, n: int, ctr, key):
+    c = _host(ctr, np.uint32).reshape(4)
+    k = _host(key, np.uint32).reshape(2)
+    out = np.zeros((n, 4), np.uint32)
+    ctx.check(ctx.lib.fire_philox_blocks(ctx.h, int(n), _ptr(c), _ptr(k), 0,
+                                         _ptr(out)))
+    return out
+
+
+def results_view(out_tensor) -> np.ndarray:
+    """Device results tensor (n, 6) int32 -> host structured array."""
+    a = out_tensor.detach().cpu().numpy().astype(np.int32, copy=False)
+    return a.view(np.uint32).reshape(-1, 6).copy().view(RESULT_DTYPE).reshape(-1)

@@ -1,0 +1,82 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every entry point
+include/fire.h declares (no GPU needed: nothing is called)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "fire.h")
+
+
+def _declared():
+    txt = open(HEADER).read()
+    return sorted(set(re.findall(r"^FIRE_API\s+[\w\s\*]*?\b(fire_\w+)\s*\(",
+                                 txt, flags=re.M)))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    from paper_1701_03549_gb300 import build
+
+    return build.build_library()
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for required in ("fire_create", "fire_maps_upload", "fire_target_upload",
+                     "fire_simulate_batch", "fire_fitness"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    lib = ctypes.CDLL(libpath)
+    for name in _declared():
+        assert hasattr(lib, name), name
+
+
+def test_only_abi_symbols_are_exported(libpath):
+    out = subprocess.run(["nm", "-D", "--defined-only", libpath],
+                         capture_output=True, text=True, check=True).stdout
+    text_syms = [l.split()[-1] for l in out.splitlines() if " T " in l]
+    assert sorted(text_syms) == _declared()
+
+
+def test_binding_covers_the_header():
+    from paper_1701_03549_gb300 import fire
+
+    assert sorted(fire.EXPORTED) == _declared()
+
+
+def test_binding_loads_without_a_gpu(libpath):
+    from paper_1701_03549_gb300 import fire
+
+    L = fire.load()
+    assert L.fire_simulate_batch.restype is ctypes.c_int
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    from paper_1701_03549_gb300 import fire
+
+    saved = fire._lib
+    fire._lib = None
+    try:
+        with pytest.raises(RuntimeError, match="no CPU fallback"):
+            fire.load(str(tmp_path / "libfire.so"))
+    finally:
+        fire._lib = saved
+
+
+def test_kernels_compile_for_sm103a_without_spills():
+    from paper_1701_03549_gb300 import build
+
+    src = os.path.join(build.CSRC, "fire_kernels.cu")
+    r = subprocess.run([build._nvcc(), *build.ARCH, *build.NVCC_FLAGS,
+                        "-Xptxas=-v", "-c", src, "-o", os.devnull],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    for block in r.stderr.split("Compiling entry function")[1:]:
+        if "k_simulate" in block.split("\n")[0]:
+            assert "0 bytes spill stores" in block

@@ -1,0 +1,304 @@
+"""GPU parity: the CUDA library (through its C ABI) against the CPU oracle.
+
+Covariates, thresholds and trajectories must match bit for bit; the
+single-precision screen's probabilities must agree with double precision to
+1e-6 absolute and never change a decision.
+"""
+import numpy as np
+import pytest
+
+from paper_1701_03549_gb300 import synth, workloads
+
+pytestmark = pytest.mark.gpu
+
+TRUTH = np.asarray(synth.TRUTH_BETA)
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_1701_03549_gb300 import fire
+
+    c = fire.Context(0)
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def orc():
+    import oracle
+
+    oracle.build()
+    return oracle
+
+
+def _maps(shape_seed_list):
+    for (H, W), seed, wind_seed in shape_seed_list:
+        yield synth.landscape(H, W, seed=seed, wind_seed=wind_seed)
+
+
+SHAPES = [((1, 1), 1, None), ((1, 2), 2, None), ((3, 3), 3, 3),
+          ((37, 61), 4, 4), ((64, 64), 5, None), ((100, 33), 6, 6),
+          ((128, 128), 1, None)]
+
+
+def _compare_features(ctx, orc, land):
+    F = orc.Features(land)
+    m = ctx.landscape_upload(land)
+    g = m.features()
+    assert np.array_equal(g["psi"].view(np.uint32), F.psi.view(np.uint32))
+    assert np.array_equal(g["sig"].view(np.uint32), F.sig.view(np.uint32))
+    assert np.array_equal(g["cw"].view(np.uint32), F.cw.view(np.uint32))
+    assert np.array_equal(g["sw"].view(np.uint32), F.sw.view(np.uint32))
+    want = (F.up.astype(np.uint16) | (F.forest.astype(np.uint16) << 8)
+            | (F.burnable.astype(np.uint16) << 9))
+    assert np.array_equal(g["flags"], want)
+    return F, m
+
+
+def test_covariates_match_oracle(ctx, orc):
+    for land in _maps(SHAPES):
+        _compare_features(ctx, orc, land)
+
+
+def test_thresholds_match_oracle_exactly(ctx, orc):
+    rng = np.random.default_rng(1)
+    betas = [TRUTH, np.zeros(5), [1000.0, 0, 0, 0, 0], [-1000.0, 0, 0, 0, 0]]
+    betas += list(rng.normal(0, 5, (4, 5))) + list(rng.uniform(-30, 30, (4, 5)))
+    for land in _maps([((37, 61), 4, 4), ((128, 128), 1, None)]):
+        F, m = _compare_features(ctx, orc, land)
+        for b in betas:
+            assert np.array_equal(m.thresholds(b).astype(np.uint64),
+                                  F.thresholds(b))
+
+
+def test_single_precision_probabilities_within_1e6(ctx, orc):
+    rng = np.random.default_rng(2)
+    worst = 0.0
+    for land in _maps([((64, 64), 5, 5), ((128, 128), 1, None)]):
+        m = ctx.landscape_upload(land)
+        for b in [TRUTH] + list(rng.uniform(-30, 30, (8, 5))):
+            p32, p64 = m.probabilities(b)
+            worst = max(worst, float(np.abs(p32.astype(np.float64) - p64).max()))
+            # the double-precision values are the oracle's
+            F = orc.Features(land)
+            T = F.thresholds(b).astype(np.float64)
+            assert np.all(np.floor(p64 * 2.0 ** 32) == T)
+    assert worst <= 1e-6, worst
+
+
+def test_screen_never_flips_a_decision(ctx):
+    from paper_1701_03549_gb300 import fire
+
+    r = fire.fire_screen_selftest(ctx, 1 << 26, 12345)
+    assert r["cases"] == 1 << 26
+    assert r["flips"] == 0
+    assert r["max_abs_dp"] <= 1e-6
+    # the double-precision fallback stays rare for uniform draws
+    assert r["fallbacks"] < r["cases"]
+
+
+def test_philox_blocks_match_oracle(ctx, orc):
+    from paper_1701_03549_gb300 import fire
+
+    rng = np.random.default_rng(3)
+    for _ in range(8):
+        ctr = rng.integers(0, 2 ** 32, 4, dtype=np.uint64).astype(np.uint32)
+        key = rng.integers(0, 2 ** 32, 2, dtype=np.uint64).astype(np.uint32)
+        ctr[0] = min(int(ctr[0]), 2 ** 32 - 300)
+        got = fire.fire_philox_blocks(ctx, 256, ctr, key)
+        for i in range(0, 256, 17):
+            c = ctr.copy()
+            c[0] += i
+            assert np.array_equal(got[i], orc.philox4x32_10(c, key))
+
+
+def _check_batch(ctx, orc, land, params, ignitions, seeds, target=None,
+                 max_steps=0, warps=0, bps=0):
+    F = orc.Features(land)
+    m = ctx.landscape_upload(land)
+    if target is not None:
+        m.target_upload(target)
+    ctx.set_launch(warps, bps)
+    try:
+        res, bs = m.simulate_batch(params, ignitions, seeds, want_steps=True,
+                                   max_steps=max_steps)
+    finally:
+        ctx.set_launch(0, 0)
+    for i in range(len(seeds)):
+        o, obs = F.simulate(params[i], tuple(ignitions[i]), int(seeds[i]),
+                            target=target, max_steps=max_steps)
+        assert np.array_equal(bs[i], obs), f"trajectory {i}"
+        for k in ("burnt", "inter", "target", "steps", "status", "trials"):
+            assert int(res[k][i]) == o[k], (i, k, int(res[k][i]), o[k])
+    return res, bs
+
+
+def test_trajectories_single_fire_128(ctx, orc):
+    wl = workloads.single_fire_128(replicates=64)
+    F = orc.Features(wl.land)
+    _, target = workloads.pick_target(
+        lambda s: F.simulate(synth.TRUTH_BETA, wl.ignition, s)[1] >= 0,
+        int(F.burnable.sum()))
+    _check_batch(ctx, orc, wl.land, wl.params, wl.ignitions, wl.seeds,
+                 target=target)
+
+
+@pytest.mark.parametrize("shape,seed", [((1, 1), 1), ((1, 2), 2), ((3, 3), 3),
+                                        ((37, 61), 4), ((100, 33), 6),
+                                        ((33, 97), 7), ((96, 160), 8)])
+def test_trajectories_ragged_grids(ctx, orc, shape, seed):
+    land = synth.landscape(*shape, seed=seed, wind_seed=seed)
+    rng = np.random.default_rng(seed)
+    n = 24
+    params = np.concatenate([rng.normal(0, 3, (n - 4, 5)),
+                             [TRUTH, [1000.0, 0, 0, 0, 0],
+                              [-1000.0, 0, 0, 0, 0], [2.0, 0, 0, 0, 0]]])
+    burnable = np.argwhere(land.veg != 0)
+    ign = burnable[rng.integers(0, len(burnable), n)].astype(np.int32)
+    seeds = rng.integers(1, 2 ** 63, n, dtype=np.uint64)
+    target = rng.random(shape) < 0.3
+    _check_batch(ctx, orc, land, params, ign, seeds, target=target)
+
+
+def test_ignitions_on_edges_and_corners(ctx, orc):
+    H, W = 65, 70
+    land = synth.landscape(H, W, seed=11, wind_seed=11)
+    land.veg[:] = np.maximum(land.veg, 1)
+    pts = [(0, 0), (0, W - 1), (H - 1, 0), (H - 1, W - 1), (31, 31), (32, 32),
+           (31, 32), (32, 31), (0, 33), (64, 63)]
+    n = len(pts)
+    params = np.tile([1.0, -0.5, 0.5, 1.5, -1.0], (n, 1))
+    _check_batch(ctx, orc, land, params, np.asarray(pts, np.int32),
+                 np.arange(1, n + 1, dtype=np.uint64))
+
+
+def test_p_one_and_p_zero(ctx, orc):
+    land = synth.uniform_landscape(70, 75)
+    res, bs = _check_batch(ctx, orc, land, np.array([[1000.0, 0, 0, 0, 0],
+                                                     [-1000.0, 0, 0, 0, 0]]),
+                           np.array([[20, 50], [3, 4]], np.int32),
+                           np.array([5, 6], np.uint64))
+    rr, cc = np.mgrid[0:70, 0:75]
+    assert np.array_equal(bs[0], np.maximum(abs(rr - 20), abs(cc - 50)))
+    assert res["burnt"][1] == 1 and res["steps"][1] == 1
+
+
+def test_step_cap(ctx, orc):
+    land = synth.uniform_landscape(40, 40)
+    _check_batch(ctx, orc, land, np.array([[1000.0, 0, 0, 0, 0]] * 3),
+                 np.array([[20, 20]] * 3, np.int32),
+                 np.array([1, 2, 3], np.uint64), max_steps=5)
+
+
+def test_launch_shape_and_batch_position_do_not_change_results(ctx, orc):
+    wl = workloads.single_fire_128(replicates=48)
+    m = ctx.landscape_upload(wl.land)
+    ref, refbs = m.simulate_batch(wl.params, wl.ignitions, wl.seeds,
+                                  want_steps=True)
+    for warps, bps in ((1, 1), (2, 0), (8, 3), (16, 1)):
+        ctx.set_launch(warps, bps)
+        r, b = m.simulate_batch(wl.params, wl.ignitions, wl.seeds,
+                                want_steps=True)
+        assert np.array_equal(r, ref) and np.array_equal(b, refbs)
+    ctx.set_launch(0, 0)
+    perm = np.random.default_rng(0).permutation(wl.n)
+    r, b = m.simulate_batch(wl.params[perm], wl.ignitions[perm],
+                            wl.seeds[perm], want_steps=True)
+    assert np.array_equal(r, ref[perm]) and np.array_equal(b, refbs[perm])
+    one, oneb = m.simulate_batch(wl.params[7:8], wl.ignitions[7:8],
+                                 wl.seeds[7:8], want_steps=True)
+    assert np.array_equal(one[0], ref[7]) and np.array_equal(oneb[0], refbs[7])
+
+
+def test_ga_generation_512_sample(ctx, orc):
+    wl = workloads.ga_generation_512(population=256, replicates=16)
+    idx = np.array([0, 1, 2, 17, 100, 2001, 4095])
+    F = orc.Features(wl.land)
+    _, target = workloads.pick_target(
+        lambda s: F.simulate(synth.TRUTH_BETA, wl.ignition, s)[1] >= 0,
+        int(F.burnable.sum()))
+    m = ctx.landscape_upload(wl.land)
+    m.target_upload(target)
+    res, _ = m.simulate_batch(wl.params, wl.ignitions, wl.seeds)
+    for i in idx:
+        o, _ = F.simulate(wl.params[i], wl.ignition, int(wl.seeds[i]),
+                          target=target, want_steps=False)
+        for k in ("burnt", "inter", "target", "steps", "status", "trials"):
+            assert int(res[k][i]) == o[k], (i, k)
+
+
+def test_global_state_variant_1024(ctx, orc):
+    """1024 x 1024 state does not fit in shared memory: the per-block global
+    state buffer path must give the same trajectories."""
+    land = synth.landscape(1024, 1024, seed=3, wind_seed=3)
+    ign = synth.centre_ignition(land.veg)
+    params = np.array([TRUTH, [-1.0, 0.5, 0.5, 3.0, -1.0]])
+    _check_batch(ctx, orc, land, params, np.array([ign, ign], np.int32),
+                 np.array([3, 4], np.uint64))
+
+
+def test_fitness_matches_oracle(ctx, orc):
+    from paper_1701_03549_gb300 import fire
+
+    rng = np.random.default_rng(4)
+    r = np.zeros(500, fire.RESULT_DTYPE)
+    r["target"] = rng.integers(1, 5000, 500)
+    r["burnt"] = rng.integers(1, 5000, 500)
+    r["inter"] = np.minimum(r["target"], r["burnt"]) * rng.random(500)
+    for kind in (0, 1):
+        got = fire.fire_fitness(ctx, r, kind)
+        want = [orc.fitness(int(a), int(b), int(c), kind)
+                for a, b, c in zip(r["burnt"], r["inter"], r["target"])]
+        assert np.array_equal(got, np.asarray(want))
+
+
+def test_bad_host_ignition_is_rejected(ctx):
+    from paper_1701_03549_gb300 import fire
+
+    land = synth.landscape(40, 40, seed=1)
+    land.veg[5, 5] = 0
+    m = ctx.landscape_upload(land)
+    for ign in ([5, 5], [40, 0], [-1, 3]):
+        with pytest.raises(fire.FireError) as e:
+            m.simulate_batch([[0.0] * 5], [ign], [1])
+        assert e.value.code == fire.FIRE_EIGNITION
+    with pytest.raises(fire.FireError) as e:
+        m.simulate_batch([[np.nan, 0, 0, 0, 0]], [[1, 1]], [1])
+    assert e.value.code == fire.FIRE_EINVAL
+    r, _ = m.simulate_batch(np.zeros((0, 5)), np.zeros((0, 2)), np.zeros(0))
+    assert r.shape == (0,)
+
+
+def test_device_pointer_path_matches_host_path(ctx, orc):
+    import torch
+
+    from paper_1701_03549_gb300 import fire
+
+    wl = workloads.single_fire_128(replicates=32)
+    m = ctx.landscape_upload(wl.land)
+    href, hbs = m.simulate_batch(wl.params, wl.ignitions, wl.seeds,
+                                 want_steps=True)
+    dev = torch.device("cuda", 0)
+    p = torch.tensor(wl.params, dtype=torch.float64, device=dev)
+    g = torch.tensor(wl.ignitions, dtype=torch.int32, device=dev)
+    s = torch.tensor(wl.seeds.view(np.int64), dtype=torch.int64, device=dev)
+    out = torch.zeros((wl.n, 6), dtype=torch.int32, device=dev)
+    bs = torch.zeros((wl.n, 128, 128), dtype=torch.int32, device=dev)
+    torch.cuda.synchronize()  # the context issues work on its own stream
+    m.simulate_batch(p, g, s, want_steps=True, device=True, out=out,
+                     burn_step=bs, sync=True)
+    assert np.array_equal(fire.results_view(out), href)
+    assert np.array_equal(bs.cpu().numpy(), hbs)
+    # device-side ignition check: an out-of-grid ignition is flagged per sim
+    g[3, 0] = 500
+    torch.cuda.synchronize()
+    m.simulate_batch(p, g, s, device=True, out=out, sync=True)
+    r = fire.results_view(out)
+    assert r["status"][3] & fire.STATUS_BAD_IGNITION
+    assert np.array_equal(np.delete(r, 3), np.delete(href, 3))
