@@ -99,7 +99,7 @@ enum {
     FIRE_ESTEPS = -6      /* a simulation reached the step cap               */
 };
 
-#define FIRE_MAX_TILES 24576
+#define FIRE_MAX_TILES 16384
 
 /* call flags */
 #define FIRE_DEVICE_PTRS 1u  /* array arguments are device pointers          */

@@ -387,13 +387,23 @@ int fire_simulate_batch(fire_ctx *ctx, const fire_map *m, int n,
         }
     }
 
-    // launch shape
+    // launch shape: warps per block, candidate-queue capacity, state in
+    // shared memory when it fits (else a per-block global buffer)
     const int ntiles = m->dev.ntiles;
     int nwarps = ctx->warps_per_block;
-    if (nwarps <= 0) nwarps = ntiles <= 64 ? 4 : 8;
-    const SimLayout Ls = sim_layout(ntiles, nwarps, true);
-    const bool smem_state = Ls.total <= ctx->max_smem_optin;
-    const SimLayout L = smem_state ? Ls : sim_layout(ntiles, nwarps, false);
+    if (nwarps <= 0) nwarps = ntiles <= 16 ? 4 : (ntiles <= 64 ? 8 : 16);
+    nwarps = std::min(nwarps, kSimMaxThreads / 32);
+    int qcap = 4096;
+    SimLayout L = sim_layout(ntiles, qcap, true);
+    const bool smem_state = L.total <= ctx->max_smem_optin;
+    if (!smem_state) {
+        qcap = 16384;
+        L = sim_layout(ntiles, qcap, false);
+        if (L.total > ctx->max_smem_optin) {
+            qcap = 4096;
+            L = sim_layout(ntiles, qcap, false);
+        }
+    }
     const void *kfn = simulate_kernel_ptr(smem_state);
     CUDA_TRY(ctx, cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)L.total),
@@ -468,6 +478,7 @@ int fire_simulate_batch(fire_ctx *ctx, const fire_map *m, int n,
     a.gstate = ctx->gstate;
     a.error_word = ctx->counter + 1;
     a.max_steps = max_steps;
+    a.qcap = qcap;
     cudaError_t e = cudaMemsetAsync(ctx->counter, 0, 4, ctx->stream);
     if (e == cudaSuccess)
         e = launch_simulate(a, smem_state, nwarps, (int)grid, L.total, ctx->stream);

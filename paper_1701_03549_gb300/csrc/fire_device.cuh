@@ -293,11 +293,13 @@ __device__ __forceinline__ ScreenParams screen_params(const double b[5])
     return s;
 }
 
-// Per-target-cell partial sums of z.
+// Per-target-cell partial sums of z: the direction-independent part with and
+// without the slope term, and the wind term b3 * omega_d for d = 0..3
+// (directions 4..7 are their negatives).
 struct ScreenCell {
-    ff base;   // b0 + b1 If + b2 psi
-    ff A, B;   // b3 cos(phi_w), b3 sin(phi_w)
-    ff G;      // b4 sig
+    ff base;    // b0 + b1 If + b2 psi
+    ff baseG;   // base + b4 sig
+    ff w0, w1, w2, w3;
 };
 
 __device__ __forceinline__ ScreenCell screen_cell(const ScreenParams &sp,
@@ -307,38 +309,33 @@ __device__ __forceinline__ ScreenCell screen_cell(const ScreenParams &sp,
 {
     ScreenCell c;
     c.base = ff_add(sp.K[forest ? 1 : 0], ff_mul_f(sp.b2, psi));
-    c.A = ff_mul_f(sp.b3, cw);
-    c.B = ff_mul_f(sp.b3, sw);
-    c.G = ff_mul_f(sp.b4, sig);
+    c.baseG = ff_add(c.base, ff_mul_f(sp.b4, sig));
+    const ff A = ff_mul_f(sp.b3, cw);
+    const ff B = ff_mul_f(sp.b3, sw);
+    c.w0 = A;
+    c.w1 = ff_mul_r2(ff_add(A, B));
+    c.w2 = B;
+    c.w3 = ff_mul_r2(ff_add(B, ff_neg(A)));
     return c;
 }
 
-// b3 * omega_d as a float pair.
-__device__ __forceinline__ ff screen_wind(const ScreenCell &c, int d)
-{
-    switch (d & 7) {
-    case 0: return c.A;
-    case 1: return ff_mul_r2(ff_add(c.A, c.B));
-    case 2: return c.B;
-    case 3: return ff_mul_r2(ff_add(c.B, ff_neg(c.A)));
-    case 4: return ff_neg(c.A);
-    case 5: return ff_neg(ff_mul_r2(ff_add(c.A, c.B)));
-    case 6: return ff_neg(c.B);
-    default: return ff_mul_r2(ff_add(c.A, ff_neg(c.B)));
-    }
-}
-
+// z of direction d (up: target above the source), rounded to float.
 __device__ __forceinline__ float screen_z(const ScreenCell &c, bool up, int d)
 {
-    ff z = ff_add(c.base, screen_wind(c, d));
-    if (up) z = ff_add(z, c.G);
-    return z.h;
+    const int j = d & 3;
+    ff wt = j == 0 ? c.w0 : (j == 1 ? c.w1 : (j == 2 ? c.w2 : c.w3));
+    if (d & 4) wt = ff_neg(wt);
+    return ff_add(up ? c.baseG : c.base, wt).h;
 }
 
+// p = 1 / (1 + e^-z) with the hardware exponential and reciprocal (each
+// within a few ulp; the margin above covers them with a factor 10).
 __device__ __forceinline__ float screen_p(float z)
 {
     const float e = __expf(-z);
-    return __frcp_rn(__fadd_rn(1.0f, e));
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(__fadd_rn(1.0f, e)));
+    return r;
 }
 
 // Decision of the trial with draw u.  Returns 1 success, 0 failure, -1 when

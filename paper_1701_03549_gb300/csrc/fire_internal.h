@@ -38,14 +38,12 @@ struct SimLaunch {
     uint32_t *gstate;          // global-state variant: 2 * ntiles * 32 words per block
     uint32_t *error_word;      // set nonzero when a bounded wait runs out
     uint32_t max_steps;        // 0 = no cap
+    int qcap;                  // candidate-queue capacity (entries)
 };
 
 // Cell-flag bits.
 constexpr uint16_t kFlagForest = 1u << 8;
 constexpr uint16_t kFlagBurnable = 1u << 9;
-
-// Capacity of a warp's candidate queue (entries processed per pass).
-constexpr int kQueueCap = 256;
 
 // Per-simulation shared state of the simulation kernel's block.
 struct SimShared {
@@ -57,23 +55,20 @@ struct SimShared {
     int timeout;
     uint32_t count[3];    // worklist lengths, slot t % 3 for step t
     uint32_t newflag[3];  // some cell burning at step t (slot t % 3)
-    uint32_t burnt, inter, trials, status, last_new;
+    uint32_t qcount[2];   // candidate-queue reservations of step t (t & 1)
+    uint32_t qvalid[2];   // end of the valid queue prefix of step t (t & 1)
+    uint32_t trials, status, last_new;
+    uint32_t burnt, inter;
+    unsigned long long tw_magic;  // floor(2^40 / TW) + 1: k / TW = k * m >> 40
     unsigned long long mbar;
-};
-
-// Per-warp scratch: direction masks of the tile rows, new-cell words and the
-// candidate queue (row << 5 | column).
-struct WarpScratch {
-    uint32_t Md[8][32];
-    uint32_t Nsc[32];
-    uint16_t q[kQueueCap];
 };
 
 // Shared-memory layout of the simulation kernel (identical on host/device):
 // header, worklist mark bits (2 per tile), three worklists of uint16 tile
-// indices, warp scratch, then (shared-state variant) the X and Y planes.
+// indices, the block's candidate queue (qcap uint32 entries), then, in the
+// shared-state variant, the X and Y planes.
 struct SimLayout {
-    size_t header, marks, lists, scratch, planes, total;
+    size_t header, marks, lists, queue, planes, total;
 };
 
 __host__ __device__ inline size_t align_up(size_t x, size_t a)
@@ -81,15 +76,15 @@ __host__ __device__ inline size_t align_up(size_t x, size_t a)
     return (x + a - 1) / a * a;
 }
 
-__host__ __device__ inline SimLayout sim_layout(int ntiles, int nwarps,
+__host__ __device__ inline SimLayout sim_layout(int ntiles, int qcap,
                                                 bool smem_state)
 {
     SimLayout L;
     L.header = 0;
     L.marks = align_up(sizeof(SimShared), 16);
     L.lists = align_up(L.marks + 4 * (size_t)((ntiles + 15) / 16), 16);
-    L.scratch = align_up(L.lists + 3 * 2 * (size_t)ntiles, 16);
-    L.planes = align_up(L.scratch + (size_t)nwarps * sizeof(WarpScratch), 128);
+    L.queue = align_up(L.lists + 3 * 2 * (size_t)ntiles, 16);
+    L.planes = align_up(L.queue + 4 * (size_t)qcap, 128);
     L.total = smem_state ? L.planes + 2 * (size_t)ntiles * 128 : L.planes;
     return L;
 }
@@ -105,6 +100,8 @@ cudaError_t launch_target(const MapDev &m, const uint8_t *burnt, uint32_t *tgt,
                           uint32_t *tgt_count, cudaStream_t st);
 cudaError_t launch_simulate(const SimLaunch &a, bool smem_state, int nwarps,
                             int grid, size_t smem_bytes, cudaStream_t st);
+// Threads per block the simulation kernel is compiled for (upper bound).
+constexpr int kSimMaxThreads = 512;
 const void *simulate_kernel_ptr(bool smem_state);
 cudaError_t launch_fitness(const fire_result *r, int n, int kind, double *out,
                            cudaStream_t st);

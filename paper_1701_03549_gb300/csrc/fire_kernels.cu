@@ -180,15 +180,25 @@ struct SimCtx {
     SimShared *sh;
     uint32_t *marks;
     uint16_t *lists;
+    uint32_t *queue;
     uint32_t *X, *Y;
     int ntiles;
     int sim;
 };
 
-// Append tile kk to the worklist of step tn unless it is already there.
+__device__ __forceinline__ int tile_row(const SimShared &sh, int k)
+{
+    return (int)(((unsigned long long)k * sh.tw_magic) >> 40);
+}
+
+// Append tile kk to the worklist of step tn unless it is already there.  A
+// set mark bit of parity tn & 1 can only come from step tn - 1 (every tile of
+// a worklist is popped, clearing its bit, during its step), so a plain read
+// that sees the bit set may skip the atomic.
 __device__ __forceinline__ void mark_tile(const SimCtx &s, int kk, uint32_t tn)
 {
     const uint32_t bit = 1u << (2 * (kk & 15) + (tn & 1));
+    if (*((volatile uint32_t *)&s.marks[kk >> 4]) & bit) return;
     const uint32_t old = atomicOr(&s.marks[kk >> 4], bit);
     if (!(old & bit)) {
         const uint32_t slot = tn % 3;
@@ -197,40 +207,101 @@ __device__ __forceinline__ void mark_tile(const SimCtx &s, int kk, uint32_t tn)
     }
 }
 
-// Decide trials of directions base..base+3 of one candidate cell.
-template <int kBase>
-__device__ __forceinline__ bool try_half(uint32_t dm, uint4 u4,
-                                         const ScreenCell &sc, uint32_t up,
-                                         const double *beta, bool forest,
-                                         const float4 &f)
+// Exact decision of one trial through the double-precision threshold.
+static __device__ __noinline__ int exact_decide(const double *beta,
+                                                bool forest, float4 f,
+                                                bool upd, int d, uint32_t u)
 {
-    const uint32_t us[4] = {u4.x, u4.y, u4.z, u4.w};
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const int d = kBase + j;
-        if (!((dm >> d) & 1u)) continue;
+    const uint64_t T = spec::threshold_of_z(
+        spec::z_of(beta, forest, f.x, f.y, f.z, f.w, upd, d));
+    return (uint64_t)u < T ? 1 : 0;
+}
+
+// Trials of the directions in m4 (bit j: direction base + j) drawn from one
+// Philox block; stops at the first success.
+__device__ __forceinline__ bool test_dirs(uint32_t m4, int base, uint4 u4,
+                                          const ScreenCell &sc, uint32_t up,
+                                          const double *beta, bool forest,
+                                          const float4 &f)
+{
+    while (m4) {
+        const int j = __ffs(m4) - 1;
+        m4 &= m4 - 1;
+        const int d = base + j;
+        const uint32_t u = j == 0 ? u4.x : (j == 1 ? u4.y : (j == 2 ? u4.z : u4.w));
         const bool upd = (up >> d) & 1u;
         const float p32 = screen_p(screen_z(sc, upd, d));
-        int dec = screen_decide(p32, us[j]);
-        if (dec < 0) {
-            const uint64_t T = spec::threshold_of_z(
-                spec::z_of(beta, forest, f.x, f.y, f.z, f.w, upd, d));
-            dec = (uint64_t)us[j] < T;
-        }
+        int dec = screen_decide(p32, u);
+        if (dec < 0) dec = exact_decide(beta, forest, f, upd, d, u);
         if (dec) return true;
     }
     return false;
 }
 
-// One active tile of step t, processed by one warp (lane = tile row).
-__device__ __forceinline__ void process_tile(const SimCtx &s, WarpScratch &ws,
-                                             int k, uint32_t t, int lane)
+// All trials of one candidate cell (dm: directions with a burning source).
+__device__ __forceinline__ bool trial_cell(const SimCtx &s, uint32_t cell,
+                                           uint32_t dm, uint32_t t)
+{
+    const MapDev &m = s.a->map;
+    const SimShared &sh = *s.sh;
+    const float4 f = __ldg(&m.feat[cell]);
+    const uint32_t fl = __ldg(&m.cfl[cell]);
+    const bool forest = (fl & kFlagForest) != 0;
+    const uint32_t up = fl & 0xffu;
+    const ScreenCell sc = screen_cell(sh.sp, forest, f.x, f.y, f.z, f.w);
+    bool ign = false;
+    if (dm & 0x0fu) {
+        const uint4 u = philox4x32_10(cell, t, 0u, 0u, sh.key0, sh.key1);
+        ign = test_dirs(dm & 0x0fu, 0, u, sc, up, sh.beta, forest, f);
+    }
+    if (!ign && (dm & 0xf0u)) {
+        const uint4 u = philox4x32_10(cell, t, 1u, 0u, sh.key0, sh.key1);
+        ign = test_dirs(dm >> 4, 4, u, sc, up, sh.beta, forest, f);
+    }
+    return ign;
+}
+
+// Cell (row r, column i of tile k = (ti, tj)) ignites at step t: write it with
+// the "burning, parity t + 1" code and put its tile, and the neighbour tiles
+// across the edges it lies on, on the worklist of step t + 1.
+__device__ __forceinline__ void ignite(const SimCtx &s, int k, int ti, int tj,
+                                       int r, int i, uint32_t cell, uint32_t t)
+{
+    const MapDev &m = s.a->map;
+    uint32_t *P = (t & 1u) ? s.X : s.Y;
+    atomicOr(&P[k * 32 + r], 1u << i);
+    if (s.a->burn_step)
+        s.a->burn_step[(long long)s.sim * m.H * m.W + cell] = (int32_t)(t + 1);
+    const uint32_t tn = t + 1;
+    mark_tile(s, k, tn);
+    const int dr = r == 0 ? -1 : (r == 31 ? 1 : 0);
+    const int dc = i == 0 ? -1 : (i == 31 ? 1 : 0);
+    const bool rok = dr != 0 && ti + dr >= 0 && ti + dr < m.TH;
+    const bool cok = dc != 0 && tj + dc >= 0 && tj + dc < m.TW;
+    if (rok) mark_tile(s, k + dr * m.TW, tn);
+    if (cok) mark_tile(s, k + dc, tn);
+    if (rok && cok) mark_tile(s, k + dr * m.TW + dc, tn);
+}
+
+__device__ __forceinline__ uint32_t dir_bits(const uint32_t md[8], int i)
+{
+    uint32_t dm = 0;
+#pragma unroll
+    for (int d = 0; d < 8; ++d) dm |= ((md[d] >> i) & 1u) << d;
+    return dm;
+}
+
+// Phase A of step t for active tile k, one warp (lane = tile row): retire the
+// previous step's burning cells, find the targets with a burning source in
+// each direction, count the trials and queue the candidates for phase B.
+__device__ __forceinline__ void phase_a(const SimCtx &s, int k, uint32_t t,
+                                        int lane)
 {
     const SimLaunch &a = *s.a;
     const MapDev &m = a.map;
     SimShared &sh = *s.sh;
     const int TW = m.TW, TH = m.TH;
-    const int ti = k / TW, tj = k - ti * TW;
+    const int ti = tile_row(sh, k), tj = k - ti * TW;
     const uint32_t par = t & 1u;
     uint32_t *X = s.X, *Y = s.Y;
 
@@ -266,6 +337,16 @@ __device__ __forceinline__ void process_tile(const SimCtx &s, WarpScratch &ws,
             if (tj < TW - 1) brd = burning(X[wb + 32], Y[wb + 32], par);
         }
     }
+    // Retire last step's burning cells (code of parity t + 1) to "burnt";
+    // readers of other tiles only look for the parity-t code.
+    const uint32_t stale = burning(x, y, par ^ 1u);
+    if (stale) {
+        X[w] = x | stale;
+        Y[w] = y | stale;
+    }
+    if (__any_sync(kFull, b != 0) && lane == 0) mark_tile(s, k, t + 1);
+    __syncwarp();
+
     // Targets of row `lane` with a burning source in direction d (the source
     // of direction d lies at target - off(d)).
     const uint32_t avail = ~(x | y);
@@ -285,6 +366,8 @@ __device__ __forceinline__ void process_tile(const SimCtx &s, WarpScratch &ws,
         cand |= md[d];
         ntr += __popc(md[d]);
     }
+    const uint32_t trw = __reduce_add_sync(kFull, ntr);
+    if (lane == 0 && trw) atomicAdd(&sh.trials, trw);
     const uint32_t c = __popc(cand);
     uint32_t incl = c;
 #pragma unroll
@@ -293,145 +376,55 @@ __device__ __forceinline__ void process_tile(const SimCtx &s, WarpScratch &ws,
         if (lane >= o) incl += v;
     }
     const uint32_t total = __shfl_sync(kFull, incl, 31);
+    if (total == 0) return;
     const uint32_t excl = incl - c;
-
-    uint32_t nrow = 0;
-    if (total) {
-#pragma unroll
-        for (int d = 0; d < 8; ++d) ws.Md[d][lane] = md[d];
-        const uint32_t key0 = sh.key0, key1 = sh.key1;
-        for (uint32_t base = 0; base < total; base += kQueueCap) {
-            const uint32_t lo = max(excl, base);
-            const uint32_t hi = min(excl + c, base + (uint32_t)kQueueCap);
-            if (lo < hi) {
-                uint32_t mm = cand;
-                for (uint32_t q = excl; q < lo; ++q) mm &= mm - 1;
-                for (uint32_t pos = lo; pos < hi; ++pos) {
-                    const int i = __ffs(mm) - 1;
-                    mm &= mm - 1;
-                    ws.q[pos - base] = (uint16_t)((lane << 5) | i);
-                }
-            }
-            __syncwarp();
-            const uint32_t cnt = min(total - base, (uint32_t)kQueueCap);
-            for (uint32_t qi = lane; qi < cnt; qi += 32) {
-                const uint32_t e = ws.q[qi];
-                const int r = (int)(e >> 5), i = (int)(e & 31);
-                uint32_t dm = 0;
-#pragma unroll
-                for (int d = 0; d < 8; ++d) dm |= ((ws.Md[d][r] >> i) & 1u) << d;
-                const int R = ti * 32 + r, C = tj * 32 + i;
-                const uint32_t cell = (uint32_t)R * (uint32_t)m.W + (uint32_t)C;
-                const float4 f = m.feat[cell];
-                const uint32_t fl = m.cfl[cell];
-                const bool forest = (fl & kFlagForest) != 0;
-                const uint32_t up = fl & 0xffu;
-                const ScreenCell sc = screen_cell(sh.sp, forest, f.x, f.y, f.z, f.w);
-                bool ign = false;
-                if (dm & 0x0fu) {
-                    const uint4 u = philox4x32_10(cell, t, 0u, 0u, key0, key1);
-                    ign = try_half<0>(dm, u, sc, up, sh.beta, forest, f);
-                }
-                if (!ign && (dm & 0xf0u)) {
-                    const uint4 u = philox4x32_10(cell, t, 1u, 0u, key0, key1);
-                    ign = try_half<4>(dm, u, sc, up, sh.beta, forest, f);
-                }
-                if (ign) atomicOr(&ws.Nsc[r], 1u << i);
-            }
-            __syncwarp();
-        }
-        nrow = ws.Nsc[lane];
-        ws.Nsc[lane] = 0;
-    }
-
-    // Commit: retire last step's burning cells, write the new ones with the
-    // next parity code.
-    const uint32_t stale = burning(x, y, par ^ 1u);
-    uint32_t nx = x | stale, ny = y | stale;
-    if (par) nx |= nrow;
-    else ny |= nrow;
-    if (nx != x) X[w] = nx;
-    if (ny != y) Y[w] = ny;
-
-    // Fused counts (Eq. 2) and status.
-    const int R = ti * 32 + lane;
-    uint32_t ic = 0;
-    bool border = false;
-    if (nrow) {
-        ic = __popc(nrow & m.tgt[w]);
-        if (R == 0 || R == m.H - 1) border = true;
-        if (tj == 0 && (nrow & 1u)) border = true;
-        if (tj == TW - 1 && ((nrow >> ((m.W - 1) & 31)) & 1u)) border = true;
-        if (a.burn_step) {
-            int32_t *bs = a.burn_step + (long long)s.sim * m.H * m.W +
-                          (long long)R * m.W + tj * 32;
-            uint32_t mm = nrow;
-            while (mm) {
-                const int i = __ffs(mm) - 1;
-                mm &= mm - 1;
-                bs[i] = (int32_t)(t + 1);
-            }
-        }
-    }
-    const uint32_t newc = __reduce_add_sync(kFull, __popc(nrow));
-    const uint32_t icw = __reduce_add_sync(kFull, ic);
-    const uint32_t trw = __reduce_add_sync(kFull, ntr);
-    const bool anyb = __any_sync(kFull, border);
+    uint32_t base = 0, ok = 0;
     if (lane == 0) {
-        if (newc) {
-            atomicAdd(&sh.burnt, newc);
-            if (icw) atomicAdd(&sh.inter, icw);
-            atomicMax(&sh.last_new, t + 1);
-            sh.newflag[(t + 1) % 3] = 1;
-        }
-        if (trw) atomicAdd(&sh.trials, trw);
-        if (anyb) atomicOr(&sh.status, FIRE_STATUS_BORDER);
+        base = atomicAdd(&sh.qcount[par], total);
+        ok = base + total <= (uint32_t)a.qcap;
+        if (!ok) atomicMin(&sh.qvalid[par], base);
     }
-
-    // Worklist of step t + 1.
-    const uint32_t n0 = __shfl_sync(kFull, nrow, 0);
-    const uint32_t n31 = __shfl_sync(kFull, nrow, 31);
-    const bool anyN = __any_sync(kFull, nrow != 0);
-    const bool anyB = __any_sync(kFull, b != 0);
-    const bool anyL = __any_sync(kFull, (nrow & 1u) != 0);
-    const bool anyR = __any_sync(kFull, (nrow >> 31) != 0);
-    if (lane < 9) {
-        int dti = 0, dtj = 0;
-        bool want = false;
-        switch (lane) {
-        case 0: want = anyN || anyB; break;
-        case 1: dti = -1; want = n0 != 0; break;
-        case 2: dti = 1; want = n31 != 0; break;
-        case 3: dtj = -1; want = anyL; break;
-        case 4: dtj = 1; want = anyR; break;
-        case 5: dti = -1; dtj = -1; want = (n0 & 1u) != 0; break;
-        case 6: dti = -1; dtj = 1; want = (n0 >> 31) != 0; break;
-        case 7: dti = 1; dtj = -1; want = (n31 & 1u) != 0; break;
-        default: dti = 1; dtj = 1; want = (n31 >> 31) != 0; break;
+    base = __shfl_sync(kFull, base, 0);
+    ok = __shfl_sync(kFull, ok, 0);
+    uint32_t mm = cand;
+    if (ok) {
+        uint32_t pos = base + excl;
+        while (mm) {
+            const int i = __ffs(mm) - 1;
+            mm &= mm - 1;
+            s.queue[pos++] = ((uint32_t)w << 13) | ((uint32_t)i << 8) |
+                             dir_bits(md, i);
         }
-        const int nti = ti + dti, ntj = tj + dtj;
-        if (want && nti >= 0 && nti < TH && ntj >= 0 && ntj < TW)
-            mark_tile(s, nti * TW + ntj, t + 1);
+    } else {
+        // queue full: this warp decides its own candidates now
+        const uint32_t R = (uint32_t)(ti * 32 + lane);
+        while (mm) {
+            const int i = __ffs(mm) - 1;
+            mm &= mm - 1;
+            const uint32_t cell = R * (uint32_t)m.W + (uint32_t)(tj * 32 + i);
+            if (trial_cell(s, cell, dir_bits(md, i), t))
+                ignite(s, k, ti, tj, lane, i, cell, t);
+        }
     }
 }
 
 template <bool kSmemState>
-__global__ void __launch_bounds__(512) k_simulate(SimLaunch a)
+__global__ void __launch_bounds__(kSimMaxThreads, 2) k_simulate(SimLaunch a)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     const int nwarps = blockDim.x >> 5;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const MapDev &m = a.map;
     const int ntiles = m.ntiles;
-    const SimLayout L = sim_layout(ntiles, nwarps, kSmemState);
+    const SimLayout L = sim_layout(ntiles, a.qcap, kSmemState);
     SimShared &sh = *reinterpret_cast<SimShared *>(smem + L.header);
     SimCtx s;
     s.a = &a;
     s.sh = &sh;
     s.marks = reinterpret_cast<uint32_t *>(smem + L.marks);
     s.lists = reinterpret_cast<uint16_t *>(smem + L.lists);
+    s.queue = reinterpret_cast<uint32_t *>(smem + L.queue);
     s.ntiles = ntiles;
-    WarpScratch &ws = reinterpret_cast<WarpScratch *>(smem + L.scratch)[warp];
     if (kSmemState) {
         s.X = reinterpret_cast<uint32_t *>(smem + L.planes);
     } else {
@@ -443,11 +436,12 @@ __global__ void __launch_bounds__(512) k_simulate(SimLaunch a)
     const long long HW = (long long)m.H * m.W;
     const uint32_t hard_cap = (uint32_t)min(HW + 2, (long long)0x7fffffff);
 
-    for (int i = threadIdx.x; i < 32 * nwarps; i += blockDim.x)
-        reinterpret_cast<WarpScratch *>(smem + L.scratch)[i >> 5].Nsc[i & 31] = 0;
-    if (kSmemState && threadIdx.x == 0) {
-        mbar_init(&sh.mbar, 1);
-        fence_proxy_async_smem();
+    if (threadIdx.x == 0) {
+        sh.tw_magic = (1ull << 40) / (unsigned long long)m.TW + 1ull;
+        if (kSmemState) {
+            mbar_init(&sh.mbar, 1);
+            fence_proxy_async_smem();
+        }
     }
     uint32_t phase = 0;
     __syncthreads();
@@ -477,11 +471,13 @@ __global__ void __launch_bounds__(512) k_simulate(SimLaunch a)
             sh.count[0] = sh.count[1] = sh.count[2] = 0;
             sh.newflag[0] = 1;
             sh.newflag[1] = sh.newflag[2] = 0;
-            sh.burnt = 1;
-            sh.inter = 0;
+            sh.qcount[0] = sh.qcount[1] = 0;
+            sh.qvalid[0] = sh.qvalid[1] = (uint32_t)a.qcap;
             sh.trials = 0;
             sh.status = 0;
             sh.last_new = 0;
+            sh.burnt = 0;
+            sh.inter = 0;
         }
         for (int i = threadIdx.x; i < nmark; i += blockDim.x) s.marks[i] = 0;
         if (kSmemState) {
@@ -538,10 +534,6 @@ __global__ void __launch_bounds__(512) k_simulate(SimLaunch a)
                 const int k0 = (g.row >> 5) * m.TW + (g.col >> 5);
                 const int r0 = g.row & 31, i0 = g.col & 31;
                 s.X[k0 * 32 + r0] |= 1u << i0;   // burning, parity 0
-                sh.inter = (m.tgt[k0 * 32 + r0] >> i0) & 1u;
-                if (g.row == 0 || g.row == m.H - 1 || g.col == 0 ||
-                    g.col == m.W - 1)
-                    sh.status |= FIRE_STATUS_BORDER;
                 if (a.burn_step)
                     a.burn_step[(long long)sim * HW + (long long)g.row * m.W +
                                 g.col] = 0;
@@ -563,7 +555,7 @@ __global__ void __launch_bounds__(512) k_simulate(SimLaunch a)
             continue;
         }
 
-        // --- steps ---
+        // --- steps: phase A (tiles) | barrier | phase B (trials) | barrier
         uint32_t t = 0;
         bool capped = false;
         for (;; ++t) {
@@ -581,7 +573,57 @@ __global__ void __launch_bounds__(512) k_simulate(SimLaunch a)
             }
             const uint16_t *list = s.lists + (t % 3) * ntiles;
             for (uint32_t li = warp; li < nA; li += nwarps)
-                process_tile(s, ws, list[li], t, lane);
+                phase_a(s, list[li], t, lane);
+            __syncthreads();
+            const uint32_t par = t & 1u;
+            const uint32_t nq = min(sh.qcount[par], sh.qvalid[par]);
+            if (threadIdx.x == 0) {
+                sh.qcount[par ^ 1u] = 0;
+                sh.qvalid[par ^ 1u] = (uint32_t)a.qcap;
+            }
+            bool any = false;
+            for (uint32_t q = threadIdx.x; q < nq; q += blockDim.x) {
+                const uint32_t e = s.queue[q];
+                const uint32_t w = e >> 13;
+                const int i = (int)((e >> 8) & 31u);
+                const int k = (int)(w >> 5), r = (int)(w & 31u);
+                const int ti = tile_row(sh, k), tj = k - ti * m.TW;
+                const uint32_t cell = (uint32_t)(ti * 32 + r) * (uint32_t)m.W +
+                                      (uint32_t)(tj * 32 + i);
+                if (trial_cell(s, cell, e & 0xffu, t)) {
+                    ignite(s, k, ti, tj, r, i, cell, t);
+                    any = true;
+                }
+            }
+            if (__any_sync(kFull, any) && lane == 0) {
+                sh.newflag[(t + 1) % 3] = 1;
+                sh.last_new = t + 1;
+            }
+        }
+
+        // --- final sweep: Eq. 2 counts and border status from the state ---
+        __syncthreads();
+        uint32_t nb = 0, ni = 0;
+        bool border = false;
+        for (int w = threadIdx.x; w < ntiles * 32; w += blockDim.x) {
+            const uint32_t bw = (s.X[w] | s.Y[w]) & ~__ldg(&m.blk[w]);
+            if (!bw) continue;
+            nb += __popc(bw);
+            ni += __popc(bw & __ldg(&m.tgt[w]));
+            const int k = w >> 5;
+            const int ti = tile_row(sh, k), tj = k - ti * m.TW;
+            const int R = ti * 32 + (w & 31);
+            if (R == 0 || R == m.H - 1 || (tj == 0 && (bw & 1u)) ||
+                (tj == m.TW - 1 && ((bw >> ((m.W - 1) & 31)) & 1u)))
+                border = true;
+        }
+        nb = __reduce_add_sync(kFull, nb);
+        ni = __reduce_add_sync(kFull, ni);
+        border = __any_sync(kFull, border);
+        if (lane == 0) {
+            if (nb) atomicAdd(&sh.burnt, nb);
+            if (ni) atomicAdd(&sh.inter, ni);
+            if (border) atomicOr(&sh.status, FIRE_STATUS_BORDER);
         }
         __syncthreads();
         if (threadIdx.x == 0) {
