@@ -283,6 +283,22 @@ __device__ __forceinline__ void ignite(const SimCtx &s, int k, int ti, int tj,
     if (rok && cok) mark_tile(s, k + dr * m.TW + dc, tn);
 }
 
+// Position of the n-th (0-based) set bit of m (n < popc(m)).
+__device__ __forceinline__ int nth_set_bit(uint32_t m, uint32_t n)
+{
+    int pos = 0;
+    uint32_t c = __popc(m & 0xffffu);
+    if (n >= c) { n -= c; m >>= 16; pos += 16; }
+    c = __popc(m & 0xffu);
+    if (n >= c) { n -= c; m >>= 8; pos += 8; }
+    c = __popc(m & 0xfu);
+    if (n >= c) { n -= c; m >>= 4; pos += 4; }
+    c = __popc(m & 0x3u);
+    if (n >= c) { n -= c; m >>= 2; pos += 2; }
+    if (n >= (m & 1u)) pos += 1;
+    return pos;
+}
+
 __device__ __forceinline__ uint32_t dir_bits(const uint32_t md[8], int i)
 {
     uint32_t dm = 0;
@@ -313,29 +329,39 @@ __device__ __forceinline__ void phase_a(const SimCtx &s, int k, uint32_t t,
     uint32_t bl = 0, br = 0;
     if (tj > 0) bl = burning(X[w - 32], Y[w - 32], par);
     if (tj < TW - 1) br = burning(X[w + 32], Y[w + 32], par);
+    // Edge rows of the tiles above (row 31) and below (row 0), including the
+    // diagonal neighbours: lanes 0..5 fetch one word each.
+    uint32_t edge = 0;
+    if (lane < 6) {
+        const int dti = lane < 3 ? -1 : 1;
+        const int dtj = (lane % 3) - 1;   // -1, 0, +1
+        const int nti = ti + dti, ntj = tj + dtj;
+        if (nti >= 0 && nti < TH && ntj >= 0 && ntj < TW) {
+            const int we = (nti * TW + ntj) * 32 + (dti < 0 ? 31 : 0);
+            edge = burning(X[we], Y[we], par);
+        }
+    }
     uint32_t bu = __shfl_up_sync(kFull, b, 1);
     uint32_t blu = __shfl_up_sync(kFull, bl, 1);
     uint32_t bru = __shfl_up_sync(kFull, br, 1);
     uint32_t bd = __shfl_down_sync(kFull, b, 1);
     uint32_t bld = __shfl_down_sync(kFull, bl, 1);
     uint32_t brd = __shfl_down_sync(kFull, br, 1);
+    const uint32_t e_ul = __shfl_sync(kFull, edge, 0);
+    const uint32_t e_u = __shfl_sync(kFull, edge, 1);
+    const uint32_t e_ur = __shfl_sync(kFull, edge, 2);
+    const uint32_t e_dl = __shfl_sync(kFull, edge, 3);
+    const uint32_t e_d = __shfl_sync(kFull, edge, 4);
+    const uint32_t e_dr = __shfl_sync(kFull, edge, 5);
     if (lane == 0) {
-        bu = blu = bru = 0;
-        if (ti > 0) {
-            const int wa = (k - TW) * 32 + 31;
-            bu = burning(X[wa], Y[wa], par);
-            if (tj > 0) blu = burning(X[wa - 32], Y[wa - 32], par);
-            if (tj < TW - 1) bru = burning(X[wa + 32], Y[wa + 32], par);
-        }
+        bu = e_u;
+        blu = e_ul;
+        bru = e_ur;
     }
     if (lane == 31) {
-        bd = bld = brd = 0;
-        if (ti < TH - 1) {
-            const int wb = (k + TW) * 32;
-            bd = burning(X[wb], Y[wb], par);
-            if (tj > 0) bld = burning(X[wb - 32], Y[wb - 32], par);
-            if (tj < TW - 1) brd = burning(X[wb + 32], Y[wb + 32], par);
-        }
+        bd = e_d;
+        bld = e_dl;
+        brd = e_dr;
     }
     // Retire last step's burning cells (code of parity t + 1) to "burnt";
     // readers of other tiles only look for the parity-t code.
@@ -386,17 +412,34 @@ __device__ __forceinline__ void phase_a(const SimCtx &s, int k, uint32_t t,
     }
     base = __shfl_sync(kFull, base, 0);
     ok = __shfl_sync(kFull, ok, 0);
-    uint32_t mm = cand;
     if (ok) {
-        uint32_t pos = base + excl;
-        while (mm) {
-            const int i = __ffs(mm) - 1;
-            mm &= mm - 1;
-            s.queue[pos++] = ((uint32_t)w << 13) | ((uint32_t)i << 8) |
-                             dir_bits(md, i);
+        // Candidate q (in row-major order within the tile) goes to lane
+        // q mod 32: its row is the first with inclusive prefix > q, its
+        // column the (q - excl)-th set bit of that row's candidate mask.
+        // The trip count is the same for every lane (all lanes take part in
+        // the shuffles); lanes past the last candidate write nothing.
+        for (uint32_t q0 = 0; q0 < total; q0 += 32) {
+            const uint32_t q = q0 + lane;
+            int r = 0;
+            if (__shfl_sync(kFull, incl, 15) <= q) r = 16;
+            if (__shfl_sync(kFull, incl, r + 7) <= q) r += 8;
+            if (__shfl_sync(kFull, incl, r + 3) <= q) r += 4;
+            if (__shfl_sync(kFull, incl, r + 1) <= q) r += 2;
+            if (__shfl_sync(kFull, incl, r) <= q) r += 1;
+            const uint32_t cr = __shfl_sync(kFull, cand, r);
+            const uint32_t ir = __shfl_sync(kFull, incl, r);
+            const int i = nth_set_bit(cr, q - (ir - (uint32_t)__popc(cr)));
+            uint32_t dm = 0;
+#pragma unroll
+            for (int d = 0; d < 8; ++d)
+                dm |= ((__shfl_sync(kFull, md[d], r) >> i) & 1u) << d;
+            if (q < total)
+                s.queue[base + q] = ((uint32_t)(k * 32 + r) << 13) |
+                                    ((uint32_t)i << 8) | dm;
         }
     } else {
         // queue full: this warp decides its own candidates now
+        uint32_t mm = cand;
         const uint32_t R = (uint32_t)(ti * 32 + lane);
         while (mm) {
             const int i = __ffs(mm) - 1;
