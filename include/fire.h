@@ -178,6 +178,31 @@ FIRE_API int fire_simulate_batch(fire_ctx *ctx, const fire_map *map, int n,
                         const uint64_t *seeds, uint32_t max_steps,
                         uint32_t flags, fire_result *out, int32_t *burn_step);
 
+/* The same simulations as fire_simulate_batch for callers that cannot let
+ * the library allocate device memory: for example code running under a fixed
+ * device-memory budget owned by another allocator, or a latency-bound loop
+ * in which cudaMalloc's implicit device synchronisation is not acceptable.
+ * (The paper has no counterpart; this is an integration convenience.)
+ * Every array argument is a device pointer supplied by the caller
+ * (FIRE_DEVICE_PTRS is implied); results are identical to
+ * fire_simulate_batch's.  The call allocates nothing: its scratch (work
+ * counter, error word, per-block state buffers) lives in one fixed device
+ * array of 2 MiB that every GPU loading the library holds until the process
+ * exits.  A map whose per-block state buffer does not fit in it (grids of
+ * more than about 8191 tiles whose state also exceeds shared memory) is
+ * rejected with FIRE_EINVAL before any work is issued.  The first call on a
+ * device looks up the array's address once; make that first call before any
+ * stream capture begins on the device.  All calls on a device share the
+ * array and each clears its counter area before launching, so calls whose
+ * work overlaps on the GPU race: serialise them.  Asynchronous unless
+ * FIRE_SYNC is set (then a timed-out device wait returns FIRE_ETIMEOUT). */
+FIRE_API int fire_simulate_batch_noalloc(fire_ctx *ctx, const fire_map *map,
+                                         int n, const fire_params *params,
+                                         const fire_cell *ignitions,
+                                         const uint64_t *seeds,
+                                         uint32_t max_steps, uint32_t flags,
+                                         fire_result *out, int32_t *burn_step);
+
 /* Fitness of n results (Eq. 2 or the Jaccard distance), double precision,
  * computed on the device.  A zero denominator gives NaN. */
 FIRE_API int fire_fitness(fire_ctx *ctx, const fire_result *results, int n, int kind,

@@ -6,43 +6,9 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
-#include <string>
-#include <vector>
-
 #include "fire_internal.h"
 
 using namespace fire;
-
-struct fire_ctx {
-    int device = 0;
-    int num_sms = 0;
-    size_t max_smem_optin = 0;
-    cudaStream_t stream = nullptr;
-    bool own_stream = false;
-    int warps_per_block = 0;   // 0: heuristic
-    int blocks_per_sm = 0;     // 0: as many as fit
-    std::string err;
-    // device scratch
-    uint32_t *counter = nullptr;     // work counter + error word
-    void *staging = nullptr;         // inputs / outputs of host-pointer calls
-    size_t staging_bytes = 0;
-    uint32_t *gstate = nullptr;      // global-state simulation buffers
-    size_t gstate_bytes = 0;
-    void *host_pinned = nullptr;     // pinned bounce buffer
-    size_t host_pinned_bytes = 0;
-};
-
-struct fire_map {
-    fire_ctx *ctx = nullptr;
-    MapDev dev{};
-    float cell_m = 0.f;
-    float4 *feat = nullptr;
-    uint16_t *cfl = nullptr;
-    uint32_t *blk = nullptr;
-    uint32_t *tgt = nullptr;
-    uint32_t *tgt_count = nullptr;
-    std::vector<uint8_t> burnable_host;
-};
 
 namespace {
 

@@ -52,6 +52,7 @@ EXPORTED = (
     "fire_target_upload", "fire_simulate_batch", "fire_fitness",
     "fire_thresholds", "fire_probabilities", "fire_map_features",
     "fire_screen_selftest", "fire_philox_blocks",
+    "fire_simulate_batch_noalloc",
 )
 
 
@@ -94,6 +95,8 @@ def load(path: str = LIB_PATH):
         "fire_map_features": (i32, [vp, vp, u32, vp, vp, vp, vp, vp]),
         "fire_screen_selftest": (i32, [vp, u64, u64, vp, vp]),
         "fire_philox_blocks": (i32, [vp, u64, vp, vp, u32, vp]),
+        "fire_simulate_batch_noalloc": (i32, [vp, vp, i32, vp, vp, vp, u32,
+                                              u32, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -258,6 +261,19 @@ class Map:
             self.ctx.h, self.h, n, _ptr(p), _ptr(g), _ptr(s), int(max_steps),
             flags, _ptr(res), _ptr(bs)))
         return res, bs
+
+    def simulate_batch_noalloc(self, params, ignitions, seeds, out,
+                               burn_step=None, want_steps=False, max_steps=0,
+                               sync=True):
+        """fire_simulate_batch_noalloc: device tensors only (as the device
+        mode of simulate_batch); the library allocates nothing."""
+        flags = (FIRE_WANT_STEPS if want_steps else 0) | FIRE_DEVICE_PTRS
+        flags |= FIRE_SYNC if sync else 0
+        self.ctx.check(self.ctx.lib.fire_simulate_batch_noalloc(
+            self.ctx.h, self.h, int(params.shape[0]), _ptr(params),
+            _ptr(ignitions), _ptr(seeds), int(max_steps), flags, _ptr(out),
+            _ptr(burn_step)))
+        return out, burn_step
 
     def thresholds(self, beta):
         b = _host(beta, np.float64).reshape(5)
