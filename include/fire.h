@@ -105,12 +105,15 @@ enum {
 #define FIRE_DEVICE_PTRS 1u  /* array arguments are device pointers          */
 #define FIRE_WANT_STEPS 2u   /* fill burn_step (see fire_simulate_batch)     */
 #define FIRE_SYNC 4u         /* block until the work has finished            */
+#define FIRE_GRAPH 8u        /* capture the call's device work as a CUDA graph
+                                once and replay it on later identical calls  */
 
 /* fire_result.status bits */
 #define FIRE_STATUS_BORDER 1u        /* a burnt cell lies on the grid edge   */
 #define FIRE_STATUS_STEP_CAP 2u      /* stopped at the step cap              */
 #define FIRE_STATUS_BAD_IGNITION 4u  /* ignition outside grid/non-burnable   */
 #define FIRE_STATUS_TIMEOUT 8u       /* a bounded device wait ran out        */
+#define FIRE_STATUS_BAD_MAP 16u      /* map index outside the map table      */
 
 /* fitness kinds */
 #define FIRE_FITNESS_PAPER_DELTA 0  /* Eq. 2: (|AuA*| - |AnA*|) / |A|          */
@@ -130,9 +133,18 @@ FIRE_API const char *fire_last_error(const fire_ctx *ctx);
 /* Block until all work issued on the context's stream has finished. */
 FIRE_API int fire_sync(fire_ctx *ctx);
 
-/* Launch shape used by later calls: warps per block (1..32) and blocks per
- * SM (0: as many as fit).  Results do not depend on it (see Trials above). */
-FIRE_API int fire_set_launch(fire_ctx *ctx, int warps_per_block, int blocks_per_sm);
+/* Launch shape used by later simulation calls: warps per block (1..16),
+ * blocks per SM (0: as many as fit), candidate-queue entries per block
+ * (0: default; at least 64) and state placement (FIRE_STATE_AUTO: shared
+ * memory when the grid's state fits, else a per-block global buffer;
+ * FIRE_STATE_SHARED; FIRE_STATE_GLOBAL).  Results do not depend on any of
+ * them (see Trials above); a shape that does not fit the device makes the
+ * next simulation call fail with FIRE_EINVAL. */
+#define FIRE_STATE_AUTO 0
+#define FIRE_STATE_SHARED 1
+#define FIRE_STATE_GLOBAL 2
+FIRE_API int fire_set_launch(fire_ctx *ctx, int warps_per_block, int blocks_per_sm,
+                             int queue_entries, int state_mode);
 
 /* Upload the raster maps of one landscape (Sec. 2.1, Fig. 1) and precompute
  * the per-cell covariates of Eq. 1 on the device:
@@ -202,6 +214,50 @@ FIRE_API int fire_simulate_batch_noalloc(fire_ctx *ctx, const fire_map *map,
                                          const uint64_t *seeds,
                                          uint32_t max_steps, uint32_t flags,
                                          fire_result *out, int32_t *burn_step);
+
+/* Uneven batch: n simulations over nmaps landscapes of different sizes in one
+ * persistent launch.  maps[nmaps] is a host array of map handles (all on the
+ * context's device); map_of_sim[n] gives each simulation's map index; the
+ * other arguments are as in fire_simulate_batch (out[i] belongs to
+ * simulation i; burn-step maps are not produced).  Simulations run largest
+ * map first (a device-side counting sort), which shortens the tail of the
+ * launch; results do not depend on the order.  With host pointers, map
+ * indices, parameters and ignitions are checked before any work is issued
+ * (FIRE_EINVAL / FIRE_EIGNITION); with FIRE_DEVICE_PTRS a bad map index or
+ * ignition is reported per simulation (FIRE_STATUS_BAD_MAP /
+ * FIRE_STATUS_BAD_IGNITION).
+ * FIRE_GRAPH (with FIRE_DEVICE_PTRS, on a context created with a
+ * non-default stream): the first call captures the ordering, counter reset
+ * and simulation launch into a CUDA graph kept by the context; a later call
+ * with the same maps, n, pointers, step cap and launch shape replays it, so
+ * new inputs must be written into the same device buffers.  Graphs are
+ * dropped when the context has to move one of its device buffers. */
+FIRE_API int fire_simulate_multi(fire_ctx *ctx, int nmaps,
+                                 const fire_map *const *maps,
+                                 const int32_t *map_of_sim, int n,
+                                 const fire_params *params,
+                                 const fire_cell *ignitions,
+                                 const uint64_t *seeds, uint32_t max_steps,
+                                 uint32_t flags, fire_result *out);
+
+/* Launch shape chosen by the autotuner. */
+typedef struct {
+    int32_t warps_per_block, blocks_per_sm, queue_entries, state_mode;
+    float ms;   /* time of the best shape on the probe batch */
+} fire_launch;
+
+/* Time the simulation kernel on the given batch (as fire_simulate_multi;
+ * map_of_sim may be NULL with host pointers, meaning map 0) with each of a
+ * fixed list of launch shapes (warps per block, blocks per SM, queue
+ * capacity, state placement), record the fastest for this largest-map tile
+ * count in the context, and return it.  Later calls without an explicit
+ * fire_set_launch override use it; results never depend on it.  Runs the
+ * batch about twenty times. */
+FIRE_API int fire_autotune(fire_ctx *ctx, int nmaps, const fire_map *const *maps,
+                           const int32_t *map_of_sim, int n,
+                           const fire_params *params, const fire_cell *ignitions,
+                           const uint64_t *seeds, uint32_t flags,
+                           fire_launch *best);
 
 /* Fitness of n results (Eq. 2 or the Jaccard distance), double precision,
  * computed on the device.  A zero denominator gives NaN. */

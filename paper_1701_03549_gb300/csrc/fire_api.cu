@@ -10,7 +10,7 @@
 
 using namespace fire;
 
-namespace {
+namespace fire {
 
 int set_err(fire_ctx *ctx, int code, const char *fmt, ...)
 {
@@ -30,12 +30,6 @@ int cuda_err(fire_ctx *ctx, cudaError_t e, const char *what)
     return set_err(ctx, FIRE_ECUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
-#define CUDA_TRY(ctx, expr, what)                         \
-    do {                                                  \
-        cudaError_t e_ = (expr);                          \
-        if (e_ != cudaSuccess) return cuda_err(ctx, e_, what); \
-    } while (0)
-
 int ensure_device(fire_ctx *ctx)
 {
     int cur = -1;
@@ -52,6 +46,7 @@ int grow_device(fire_ctx *ctx, void **buf, size_t *cap, size_t need,
                 const char *what)
 {
     if (need <= *cap) return FIRE_OK;
+    ctx->epoch++;   // cached graphs may reference the old buffer
     if (*buf) cudaFree(*buf);
     *buf = nullptr;
     *cap = 0;
@@ -85,7 +80,70 @@ size_t round16(size_t x) { return (x + 15) & ~(size_t)15; }
 
 bool valid_map(const fire_map *m) { return m && m->ctx && m->feat; }
 
-}  // namespace
+// Launch shape of the simulation kernel for maps of up to `ntiles` tiles:
+// an explicit fire_set_launch override, else the autotuned shape recorded for
+// this tile count, else a heuristic.
+int plan_launch(fire_ctx *ctx, int ntiles, long long n, LaunchPlan *p)
+{
+    int warps = 0, bps = 0, queue = 0, state = FIRE_STATE_AUTO;
+    const bool override = ctx->warps_per_block || ctx->blocks_per_sm ||
+                          ctx->queue_entries || ctx->state_mode;
+    if (override) {
+        warps = ctx->warps_per_block;
+        bps = ctx->blocks_per_sm;
+        queue = ctx->queue_entries;
+        state = ctx->state_mode;
+    } else {
+        for (const TuneEntry &t : ctx->tuned) {
+            if (t.ntiles == ntiles) {
+                warps = t.warps;
+                bps = t.bps;
+                queue = t.queue;
+                state = t.state;
+            }
+        }
+    }
+    int nwarps = warps > 0 ? warps : (ntiles <= 16 ? 4 : (ntiles <= 64 ? 8 : 16));
+    nwarps = std::min(nwarps, kSimMaxThreads / 32);
+    int qcap = queue > 0 ? queue : 4096;
+    SimLayout L = sim_layout(ntiles, qcap, true);
+    bool smem_state = state == FIRE_STATE_SHARED ||
+                      (state == FIRE_STATE_AUTO && L.total <= ctx->max_smem_optin);
+    if (smem_state && L.total > ctx->max_smem_optin)
+        return set_err(ctx, FIRE_EINVAL, "state of %d tiles does not fit in "
+                       "shared memory", ntiles);
+    if (!smem_state) {
+        if (queue <= 0) {
+            qcap = 16384;
+            if (sim_layout(ntiles, qcap, false).total > ctx->max_smem_optin)
+                qcap = 4096;
+        }
+        L = sim_layout(ntiles, qcap, false);
+        if (L.total > ctx->max_smem_optin)
+            return set_err(ctx, FIRE_EINVAL, "worklists of %d tiles do not fit in "
+                           "shared memory", ntiles);
+    }
+    const void *kfn = simulate_kernel_ptr(smem_state);
+    cudaError_t e = cudaFuncSetAttribute(
+        kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "cudaFuncSetAttribute");
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kfn, nwarps * 32,
+                                                      L.total);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "occupancy");
+    if (occ < 1)
+        return set_err(ctx, FIRE_EINVAL, "kernel does not fit (%zu B smem, %d "
+                       "warps)", L.total, nwarps);
+    const int use = bps > 0 ? std::min(bps, occ) : occ;
+    p->nwarps = nwarps;
+    p->qcap = qcap;
+    p->smem_state = smem_state;
+    p->L = L;
+    p->grid = (int)std::min((long long)use * ctx->num_sms, std::max(n, 1ll));
+    return FIRE_OK;
+}
+
+}  // namespace fire
 
 extern "C" {
 
@@ -132,6 +190,9 @@ void fire_destroy(fire_ctx *ctx)
     if (!ctx) return;
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
+    for (GraphEntry &g : ctx->graphs) cudaGraphExecDestroy(g.exec);
+    if (ctx->table) cudaFree(ctx->table);
+    if (ctx->order) cudaFree(ctx->order);
     if (ctx->counter) cudaFree(ctx->counter);
     if (ctx->staging) cudaFree(ctx->staging);
     if (ctx->gstate) cudaFree(ctx->gstate);
@@ -161,14 +222,21 @@ int fire_sync(fire_ctx *ctx)
     return FIRE_OK;
 }
 
-int fire_set_launch(fire_ctx *ctx, int warps_per_block, int blocks_per_sm)
+int fire_set_launch(fire_ctx *ctx, int warps_per_block, int blocks_per_sm,
+                    int queue_entries, int state_mode)
 {
     if (!ctx) return FIRE_EINVAL;
-    if (warps_per_block < 0 || warps_per_block > 16 || blocks_per_sm < 0)
-        return set_err(ctx, FIRE_EINVAL, "bad launch shape %d x %d",
-                       warps_per_block, blocks_per_sm);
+    if (warps_per_block < 0 || warps_per_block > kSimMaxThreads / 32 ||
+        blocks_per_sm < 0 || queue_entries < 0 ||
+        (queue_entries > 0 && queue_entries < 64) || state_mode < 0 ||
+        state_mode > FIRE_STATE_GLOBAL)
+        return set_err(ctx, FIRE_EINVAL, "bad launch shape %d x %d, queue %d, "
+                       "state %d", warps_per_block, blocks_per_sm,
+                       queue_entries, state_mode);
     ctx->warps_per_block = warps_per_block;
     ctx->blocks_per_sm = blocks_per_sm;
+    ctx->queue_entries = queue_entries;
+    ctx->state_mode = state_mode;
     return FIRE_OK;
 }
 
@@ -204,6 +272,7 @@ int fire_maps_upload(fire_ctx *ctx, int H, int W, float cell_m,
     const size_t words = (size_t)m->dev.ntiles * 32;
     cudaError_t e = cudaSuccess;
     if ((e = cudaMalloc(&m->feat, HW * sizeof(float4))) != cudaSuccess ||
+        (e = cudaMalloc(&m->wdiag, HW * sizeof(float2))) != cudaSuccess ||
         (e = cudaMalloc(&m->cfl, HW * sizeof(uint16_t))) != cudaSuccess ||
         (e = cudaMalloc(&m->blk, words * 4)) != cudaSuccess ||
         (e = cudaMalloc(&m->tgt, words * 4)) != cudaSuccess ||
@@ -213,6 +282,7 @@ int fire_maps_upload(fire_ctx *ctx, int H, int W, float cell_m,
                        cudaGetErrorString(e));
     }
     m->dev.feat = m->feat;
+    m->dev.wdiag = m->wdiag;
     m->dev.cfl = m->cfl;
     m->dev.blk = m->blk;
     m->dev.tgt = m->tgt;
@@ -250,7 +320,7 @@ int fire_maps_upload(fire_ctx *ctx, int H, int W, float cell_m,
         dwind = f[3];
     }
     e = launch_features(H, W, dveg, delev, dslope, daspect, dwind, m->feat,
-                        m->cfl, ctx->stream);
+                        m->wdiag, m->cfl, ctx->stream);
     if (e == cudaSuccess) e = launch_blocked(m->dev, dveg, m->blk, ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(m->tgt, 0, words * 4, ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(m->tgt_count, 0, 16, ctx->stream);
@@ -279,6 +349,7 @@ void fire_map_free(fire_map *m)
     if (!m) return;
     if (m->ctx) cudaSetDevice(m->ctx->device);
     if (m->feat) cudaFree(m->feat);
+    if (m->wdiag) cudaFree(m->wdiag);
     if (m->cfl) cudaFree(m->cfl);
     if (m->blk) cudaFree(m->blk);
     if (m->tgt) cudaFree(m->tgt);
@@ -353,36 +424,12 @@ int fire_simulate_batch(fire_ctx *ctx, const fire_map *m, int n,
         }
     }
 
-    // launch shape: warps per block, candidate-queue capacity, state in
-    // shared memory when it fits (else a per-block global buffer)
     const int ntiles = m->dev.ntiles;
-    int nwarps = ctx->warps_per_block;
-    if (nwarps <= 0) nwarps = ntiles <= 16 ? 4 : (ntiles <= 64 ? 8 : 16);
-    nwarps = std::min(nwarps, kSimMaxThreads / 32);
-    int qcap = 4096;
-    SimLayout L = sim_layout(ntiles, qcap, true);
-    const bool smem_state = L.total <= ctx->max_smem_optin;
-    if (!smem_state) {
-        qcap = 16384;
-        L = sim_layout(ntiles, qcap, false);
-        if (L.total > ctx->max_smem_optin) {
-            qcap = 4096;
-            L = sim_layout(ntiles, qcap, false);
-        }
-    }
-    const void *kfn = simulate_kernel_ptr(smem_state);
-    CUDA_TRY(ctx, cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)L.total),
-             "cudaFuncSetAttribute");
-    int occ = 0;
-    CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kfn, nwarps * 32,
-                                                                L.total),
-             "occupancy");
-    if (occ < 1) return set_err(ctx, FIRE_EINVAL, "kernel does not fit (%zu B smem)",
-                                L.total);
-    int bps = ctx->blocks_per_sm > 0 ? std::min(ctx->blocks_per_sm, occ) : occ;
-    long long grid = (long long)bps * ctx->num_sms;
-    if (grid > n) grid = n;
+    LaunchPlan plan;
+    rc = plan_launch(ctx, ntiles, n, &plan);
+    if (rc) return rc;
+    const bool smem_state = plan.smem_state;
+    const long long grid = plan.grid;
 
     // staging of host arguments
     const fire_params *dparams = params;
@@ -434,6 +481,11 @@ int fire_simulate_batch(fire_ctx *ctx, const fire_map *m, int n,
 
     SimLaunch a;
     a.map = m->dev;
+    a.maps = nullptr;
+    a.nmaps = 1;
+    a.map_of_sim = nullptr;
+    a.order = nullptr;
+    a.ntiles_max = ntiles;
     a.n = n;
     a.params = dparams;
     a.ign = dign;
@@ -444,10 +496,11 @@ int fire_simulate_batch(fire_ctx *ctx, const fire_map *m, int n,
     a.gstate = ctx->gstate;
     a.error_word = ctx->counter + 1;
     a.max_steps = max_steps;
-    a.qcap = qcap;
+    a.qcap = plan.qcap;
     cudaError_t e = cudaMemsetAsync(ctx->counter, 0, 4, ctx->stream);
     if (e == cudaSuccess)
-        e = launch_simulate(a, smem_state, nwarps, (int)grid, L.total, ctx->stream);
+        e = launch_simulate(a, smem_state, plan.nwarps, (int)grid, plan.L.total,
+                            ctx->stream);
     if (e != cudaSuccess) {
         if (steps_tmp) cudaFree(steps_tmp);
         return cuda_err(ctx, e, "simulate launch");

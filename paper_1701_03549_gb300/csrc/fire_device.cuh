@@ -224,10 +224,11 @@ __device__ __forceinline__ double z_of(const double b[5], bool forest,
 
 // ---------------------------------------------------------------------------
 // Single-precision screen.  z is accumulated as an unevaluated float pair
-// (hi + lo, error-free products by FMA and two-sums), so the only roundings
-// left are that of z to float (relative 2^-24), of the exponential and of
-// the reciprocal.  With p(1-p) <= 1/4 and max_z z p(1-p) < 0.23 this keeps
-// |p32 - p64| below 4e-7; a trial is decided in single precision when
+// (hi + lo, error-free products by FMA and two-sums), so the roundings left
+// are that of the diagonal wind cosines (|b3| 2^-25 in z), of z to float
+// (relative 2^-24), of the exponential and of the reciprocal.  With
+// p(1-p) <= 1/4 and max_z z p(1-p) < 0.23 this keeps |p32 - p64| below
+// 6e-7 for |b3| <= 30; a trial is decided in single precision when
 // |p32 - (u + 1) 2^-32| > kScreenMargin and otherwise re-decided through the
 // exact double-precision threshold (success <=> u < floor(p 2^32) <=>
 // (u + 1) 2^-32 <= p64).
@@ -294,38 +295,40 @@ __device__ __forceinline__ ScreenParams screen_params(const double b[5])
 }
 
 // Per-target-cell partial sums of z: the direction-independent part with and
-// without the slope term, and the wind term b3 * omega_d for d = 0..3
-// (directions 4..7 are their negatives).
+// without the slope term, and cos(phi_w - 45 j) for j = 0..3 (directions
+// 4..7 use their negatives).  The diagonal cosines are the double-precision
+// omega of the threshold definition rounded to float at upload, which adds at
+// most |b3| 2^-25 to z.
 struct ScreenCell {
     ff base;    // b0 + b1 If + b2 psi
     ff baseG;   // base + b4 sig
-    ff w0, w1, w2, w3;
+    float om0, om1, om2, om3;
 };
 
 __device__ __forceinline__ ScreenCell screen_cell(const ScreenParams &sp,
                                                   bool forest, float psi,
                                                   float sig, float cw,
-                                                  float sw)
+                                                  float om1, float sw,
+                                                  float om3)
 {
     ScreenCell c;
     c.base = ff_add(sp.K[forest ? 1 : 0], ff_mul_f(sp.b2, psi));
     c.baseG = ff_add(c.base, ff_mul_f(sp.b4, sig));
-    const ff A = ff_mul_f(sp.b3, cw);
-    const ff B = ff_mul_f(sp.b3, sw);
-    c.w0 = A;
-    c.w1 = ff_mul_r2(ff_add(A, B));
-    c.w2 = B;
-    c.w3 = ff_mul_r2(ff_add(B, ff_neg(A)));
+    c.om0 = cw;
+    c.om1 = om1;
+    c.om2 = sw;
+    c.om3 = om3;
     return c;
 }
 
 // z of direction d (up: target above the source), rounded to float.
-__device__ __forceinline__ float screen_z(const ScreenCell &c, bool up, int d)
+__device__ __forceinline__ float screen_z(const ScreenCell &c, const ff &b3,
+                                         bool up, int d)
 {
     const int j = d & 3;
-    ff wt = j == 0 ? c.w0 : (j == 1 ? c.w1 : (j == 2 ? c.w2 : c.w3));
-    if (d & 4) wt = ff_neg(wt);
-    return ff_add(up ? c.baseG : c.base, wt).h;
+    float om = j == 0 ? c.om0 : (j == 1 ? c.om1 : (j == 2 ? c.om2 : c.om3));
+    if (d & 4) om = -om;
+    return ff_add(up ? c.baseG : c.base, ff_mul_f(b3, om)).h;
 }
 
 // p = 1 / (1 + e^-z) with the hardware exponential and reciprocal (each

@@ -22,6 +22,7 @@ namespace fire {
 struct MapDev {
     int H, W, TH, TW, ntiles;
     const float4 *feat;         // (psi, sig, cos wind, sin wind) per cell
+    const float2 *wdiag;        // cos(wind - 45 deg), cos(wind - 135 deg) per cell
     const uint16_t *cfl;        // bit d<8 uphill from source d, 8 forest, 9 burnable
     const uint32_t *blk;        // non-burnable bitmap, ntiles * 32 words
     const uint32_t *tgt;        // target bitmap, ntiles * 32 words
@@ -29,7 +30,12 @@ struct MapDev {
 };
 
 struct SimLaunch {
-    MapDev map;
+    MapDev map;                // the map when `maps` is NULL
+    const MapDev *maps;        // device map table (multi-map launches)
+    int nmaps;
+    const int32_t *map_of_sim; // map index per simulation (NULL: map 0)
+    const uint32_t *order;     // processing order of the simulations (NULL: 0..n-1)
+    int ntiles_max;            // largest map of the launch (sizes buffers)
     int n;
     const fire_params *params;
     const fire_cell *ign;
@@ -61,7 +67,10 @@ struct SimShared {
     uint32_t qvalid[2];   // end of the valid queue prefix of step t (t & 1)
     uint32_t trials, status, last_new;
     uint32_t burnt, inter;
+    uint32_t hard_cap;
+    int nmark;
     unsigned long long tw_magic;  // floor(2^40 / TW) + 1: k / TW = k * m >> 40
+    MapDev map;                   // map of the current simulation
     unsigned long long mbar;
 };
 
@@ -94,8 +103,8 @@ __host__ __device__ inline SimLayout sim_layout(int ntiles, int qcap,
 // Launchers (fire_kernels.cu).  All are asynchronous on `st`.
 cudaError_t launch_features(int H, int W, const uint8_t *veg, const float *elev,
                             const float *slope, const float *aspect,
-                            const float *wind, float4 *feat, uint16_t *cfl,
-                            cudaStream_t st);
+                            const float *wind, float4 *feat, float2 *wdiag,
+                            uint16_t *cfl, cudaStream_t st);
 cudaError_t launch_blocked(const MapDev &m, const uint8_t *veg, uint32_t *blk,
                            cudaStream_t st);
 cudaError_t launch_target(const MapDev &m, const uint8_t *burnt, uint32_t *tgt,
@@ -107,6 +116,10 @@ constexpr int kSimMaxThreads = 512;
 const void *simulate_kernel_ptr(bool smem_state);
 cudaError_t launch_fitness(const fire_result *r, int n, int kind, double *out,
                            cudaStream_t st);
+// Counting sort of simulations by rank[map_of_sim[i]] (counts: nmaps + 1).
+cudaError_t launch_order(int n, const int32_t *map_of_sim, int nmaps,
+                         const int32_t *rank, uint32_t *counts, uint32_t *order,
+                         cudaStream_t st);
 cudaError_t launch_thresholds(const MapDev &m, const double *beta_dev,
                               int64_t *out, cudaStream_t st);
 cudaError_t launch_probabilities(const MapDev &m, const double *beta_dev,
@@ -121,7 +134,27 @@ cudaError_t launch_screen_selftest(uint64_t n, uint64_t seed,
 cudaError_t launch_philox_blocks(uint64_t n, uint4 ctr, uint2 key,
                                  uint32_t *out, cudaStream_t st);
 
+struct LaunchPlan {
+    int nwarps, qcap;
+    bool smem_state;
+    SimLayout L;
+    int grid;
+};
+
 }  // namespace fire
+
+// Launch-shape record of the autotuner (per map tile count).
+struct TuneEntry {
+    int ntiles, warps, bps, queue, state;
+    float ms;
+};
+
+// A captured CUDA graph and the call it replays.
+struct GraphEntry {
+    std::vector<unsigned long long> key;
+    cudaGraphExec_t exec;
+    unsigned epoch;
+};
 
 // Opaque handles of the C ABI (definitions shared by the host sources).
 struct fire_ctx {
@@ -132,6 +165,8 @@ struct fire_ctx {
     bool own_stream = false;
     int warps_per_block = 0;   // 0: heuristic
     int blocks_per_sm = 0;     // 0: as many as fit
+    int queue_entries = 0;     // 0: default
+    int state_mode = 0;        // FIRE_STATE_*
     std::string err;
     // device scratch
     uint32_t *counter = nullptr;     // work counter + error word
@@ -141,6 +176,13 @@ struct fire_ctx {
     size_t gstate_bytes = 0;
     void *host_pinned = nullptr;     // pinned bounce buffer
     size_t host_pinned_bytes = 0;
+    void *table = nullptr;           // map table + map ranks (multi-map calls)
+    size_t table_bytes = 0;
+    void *order = nullptr;           // bucket counts + processing order
+    size_t order_bytes = 0;
+    std::vector<TuneEntry> tuned;    // autotuned launch shapes
+    std::vector<GraphEntry> graphs;  // captured calls
+    unsigned epoch = 0;              // bumped when a device buffer moves
 };
 
 struct fire_map {
@@ -148,6 +190,7 @@ struct fire_map {
     fire::MapDev dev{};
     float cell_m = 0.f;
     float4 *feat = nullptr;
+    float2 *wdiag = nullptr;
     uint16_t *cfl = nullptr;
     uint32_t *blk = nullptr;
     uint32_t *tgt = nullptr;
@@ -155,3 +198,21 @@ struct fire_map {
     std::vector<uint8_t> burnable_host;
 };
 
+
+namespace fire {
+// Host helpers shared by the C ABI sources (fire_api.cu).
+int set_err(fire_ctx *ctx, int code, const char *fmt, ...);
+int cuda_err(fire_ctx *ctx, cudaError_t e, const char *what);
+int ensure_device(fire_ctx *ctx);
+int grow_device(fire_ctx *ctx, void **buf, size_t *cap, size_t need,
+                const char *what);
+size_t round16(size_t x);
+bool valid_map(const fire_map *m);
+int plan_launch(fire_ctx *ctx, int ntiles, long long n, LaunchPlan *p);
+}  // namespace fire
+
+#define CUDA_TRY(ctx, expr, what)                                   \
+    do {                                                            \
+        cudaError_t e_ = (expr);                                    \
+        if (e_ != cudaSuccess) return fire::cuda_err(ctx, e_, what); \
+    } while (0)

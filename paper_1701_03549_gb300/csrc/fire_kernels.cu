@@ -53,6 +53,7 @@ __global__ void k_features(int H, int W, const uint8_t *__restrict__ veg,
                            const float *__restrict__ aspect,
                            const float *__restrict__ wind,
                            float4 *__restrict__ feat,
+                           float2 *__restrict__ wdiag,
                            uint16_t *__restrict__ cfl)
 {
     const long long n = (long long)H * W;
@@ -80,6 +81,8 @@ __global__ void k_features(int H, int W, const uint8_t *__restrict__ veg,
         if (v == 1) f |= kFlagForest;
         if (v != 0) f |= kFlagBurnable;
         feat[i] = make_float4(psi, sig, cw, sw);
+        wdiag[i] = make_float2(__double2float_rn(spec::omega(cw, sw, 1)),
+                               __double2float_rn(spec::omega(cw, sw, 3)));
         cfl[i] = f;
     }
 }
@@ -178,6 +181,7 @@ __device__ __forceinline__ uint32_t burning(uint32_t x, uint32_t y,
 struct SimCtx {
     const SimLaunch *a;
     SimShared *sh;
+    const MapDev *map;   // the current simulation's map (shared memory)
     uint32_t *marks;
     uint16_t *lists;
     uint32_t *queue;
@@ -220,9 +224,9 @@ static __device__ __noinline__ int exact_decide(const double *beta,
 // Trials of the directions in m4 (bit j: direction base + j) drawn from one
 // Philox block; stops at the first success.
 __device__ __forceinline__ bool test_dirs(uint32_t m4, int base, uint4 u4,
-                                          const ScreenCell &sc, uint32_t up,
-                                          const double *beta, bool forest,
-                                          const float4 &f)
+                                          const ScreenCell &sc, const ff &b3,
+                                          uint32_t up, const double *beta,
+                                          bool forest, const float4 &f)
 {
     while (m4) {
         const int j = __ffs(m4) - 1;
@@ -230,7 +234,7 @@ __device__ __forceinline__ bool test_dirs(uint32_t m4, int base, uint4 u4,
         const int d = base + j;
         const uint32_t u = j == 0 ? u4.x : (j == 1 ? u4.y : (j == 2 ? u4.z : u4.w));
         const bool upd = (up >> d) & 1u;
-        const float p32 = screen_p(screen_z(sc, upd, d));
+        const float p32 = screen_p(screen_z(sc, b3, upd, d));
         int dec = screen_decide(p32, u);
         if (dec < 0) dec = exact_decide(beta, forest, f, upd, d, u);
         if (dec) return true;
@@ -242,21 +246,24 @@ __device__ __forceinline__ bool test_dirs(uint32_t m4, int base, uint4 u4,
 __device__ __forceinline__ bool trial_cell(const SimCtx &s, uint32_t cell,
                                            uint32_t dm, uint32_t t)
 {
-    const MapDev &m = s.a->map;
+    const MapDev &m = *s.map;
     const SimShared &sh = *s.sh;
     const float4 f = __ldg(&m.feat[cell]);
+    const float2 wd = __ldg(&m.wdiag[cell]);
     const uint32_t fl = __ldg(&m.cfl[cell]);
     const bool forest = (fl & kFlagForest) != 0;
     const uint32_t up = fl & 0xffu;
-    const ScreenCell sc = screen_cell(sh.sp, forest, f.x, f.y, f.z, f.w);
+    const ScreenCell sc = screen_cell(sh.sp, forest, f.x, f.y, f.z, wd.x, f.w,
+                                      wd.y);
+    const ff b3 = sh.sp.b3;
     bool ign = false;
     if (dm & 0x0fu) {
         const uint4 u = philox4x32_10(cell, t, 0u, 0u, sh.key0, sh.key1);
-        ign = test_dirs(dm & 0x0fu, 0, u, sc, up, sh.beta, forest, f);
+        ign = test_dirs(dm & 0x0fu, 0, u, sc, b3, up, sh.beta, forest, f);
     }
     if (!ign && (dm & 0xf0u)) {
         const uint4 u = philox4x32_10(cell, t, 1u, 0u, sh.key0, sh.key1);
-        ign = test_dirs(dm >> 4, 4, u, sc, up, sh.beta, forest, f);
+        ign = test_dirs(dm >> 4, 4, u, sc, b3, up, sh.beta, forest, f);
     }
     return ign;
 }
@@ -267,7 +274,7 @@ __device__ __forceinline__ bool trial_cell(const SimCtx &s, uint32_t cell,
 __device__ __forceinline__ void ignite(const SimCtx &s, int k, int ti, int tj,
                                        int r, int i, uint32_t cell, uint32_t t)
 {
-    const MapDev &m = s.a->map;
+    const MapDev &m = *s.map;
     uint32_t *P = (t & 1u) ? s.X : s.Y;
     atomicOr(&P[k * 32 + r], 1u << i);
     if (s.a->burn_step)
@@ -314,7 +321,7 @@ __device__ __forceinline__ void phase_a(const SimCtx &s, int k, uint32_t t,
                                         int lane)
 {
     const SimLaunch &a = *s.a;
-    const MapDev &m = a.map;
+    const MapDev &m = *s.map;
     SimShared &sh = *s.sh;
     const int TW = m.TW, TH = m.TH;
     const int ti = tile_row(sh, k), tj = k - ti * TW;
@@ -403,50 +410,44 @@ __device__ __forceinline__ void phase_a(const SimCtx &s, int k, uint32_t t,
     }
     const uint32_t total = __shfl_sync(kFull, incl, 31);
     if (total == 0) return;
-    const uint32_t excl = incl - c;
-    uint32_t base = 0, ok = 0;
+    // Reserve queue space for the tile's candidates; a full queue makes this
+    // warp decide them here instead (same decisions, in phase A).
+    uint32_t base = 0;
     if (lane == 0) {
         base = atomicAdd(&sh.qcount[par], total);
-        ok = base + total <= (uint32_t)a.qcap;
-        if (!ok) atomicMin(&sh.qvalid[par], base);
+        if (base + total > (uint32_t)a.qcap) {
+            atomicMin(&sh.qvalid[par], base);
+            base = 0xffffffffu;
+        }
     }
     base = __shfl_sync(kFull, base, 0);
-    ok = __shfl_sync(kFull, ok, 0);
-    if (ok) {
-        // Candidate q (in row-major order within the tile) goes to lane
-        // q mod 32: its row is the first with inclusive prefix > q, its
-        // column the (q - excl)-th set bit of that row's candidate mask.
-        // The trip count is the same for every lane (all lanes take part in
-        // the shuffles); lanes past the last candidate write nothing.
-        for (uint32_t q0 = 0; q0 < total; q0 += 32) {
-            const uint32_t q = q0 + lane;
-            int r = 0;
-            if (__shfl_sync(kFull, incl, 15) <= q) r = 16;
-            if (__shfl_sync(kFull, incl, r + 7) <= q) r += 8;
-            if (__shfl_sync(kFull, incl, r + 3) <= q) r += 4;
-            if (__shfl_sync(kFull, incl, r + 1) <= q) r += 2;
-            if (__shfl_sync(kFull, incl, r) <= q) r += 1;
-            const uint32_t cr = __shfl_sync(kFull, cand, r);
-            const uint32_t ir = __shfl_sync(kFull, incl, r);
-            const int i = nth_set_bit(cr, q - (ir - (uint32_t)__popc(cr)));
-            uint32_t dm = 0;
+    // Candidate q (in row-major order within the tile) goes to lane q mod 32:
+    // its row is the first with inclusive prefix > q, its column the
+    // (q - excl)-th set bit of that row's candidate mask.  The trip count is
+    // the same for every lane (all lanes take part in the shuffles).
+    for (uint32_t q0 = 0; q0 < total; q0 += 32) {
+        const uint32_t q = q0 + lane;
+        int r = 0;
+        if (__shfl_sync(kFull, incl, 15) <= q) r = 16;
+        if (__shfl_sync(kFull, incl, r + 7) <= q) r += 8;
+        if (__shfl_sync(kFull, incl, r + 3) <= q) r += 4;
+        if (__shfl_sync(kFull, incl, r + 1) <= q) r += 2;
+        if (__shfl_sync(kFull, incl, r) <= q) r += 1;
+        const uint32_t cr = __shfl_sync(kFull, cand, r);
+        const uint32_t ir = __shfl_sync(kFull, incl, r);
+        const int i = nth_set_bit(cr, q - (ir - (uint32_t)__popc(cr)));
+        uint32_t dm = 0;
 #pragma unroll
-            for (int d = 0; d < 8; ++d)
-                dm |= ((__shfl_sync(kFull, md[d], r) >> i) & 1u) << d;
-            if (q < total)
-                s.queue[base + q] = ((uint32_t)(k * 32 + r) << 13) |
-                                    ((uint32_t)i << 8) | dm;
-        }
-    } else {
-        // queue full: this warp decides its own candidates now
-        uint32_t mm = cand;
-        const uint32_t R = (uint32_t)(ti * 32 + lane);
-        while (mm) {
-            const int i = __ffs(mm) - 1;
-            mm &= mm - 1;
-            const uint32_t cell = R * (uint32_t)m.W + (uint32_t)(tj * 32 + i);
-            if (trial_cell(s, cell, dir_bits(md, i), t))
-                ignite(s, k, ti, tj, lane, i, cell, t);
+        for (int d = 0; d < 8; ++d)
+            dm |= ((__shfl_sync(kFull, md[d], r) >> i) & 1u) << d;
+        if (q >= total) continue;
+        if (base != 0xffffffffu) {
+            s.queue[base + q] = ((uint32_t)(k * 32 + r) << 13) |
+                                ((uint32_t)i << 8) | dm;
+        } else {
+            const uint32_t cell = (uint32_t)(ti * 32 + r) * (uint32_t)m.W +
+                                  (uint32_t)(tj * 32 + i);
+            if (trial_cell(s, cell, dm, t)) ignite(s, k, ti, tj, r, i, cell, t);
         }
     }
 }
@@ -457,40 +458,38 @@ __global__ void __launch_bounds__(kSimMaxThreads, 2) k_simulate(SimLaunch a)
     extern __shared__ __align__(128) unsigned char smem[];
     const int nwarps = blockDim.x >> 5;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const MapDev &m = a.map;
-    const int ntiles = m.ntiles;
-    const SimLayout L = sim_layout(ntiles, a.qcap, kSmemState);
+    const int ntiles_max = a.ntiles_max;
+    const SimLayout L = sim_layout(ntiles_max, a.qcap, kSmemState);
     SimShared &sh = *reinterpret_cast<SimShared *>(smem + L.header);
+    const MapDev &m = sh.map;
     SimCtx s;
     s.a = &a;
     s.sh = &sh;
+    s.map = &sh.map;
     s.marks = reinterpret_cast<uint32_t *>(smem + L.marks);
     s.lists = reinterpret_cast<uint16_t *>(smem + L.lists);
     s.queue = reinterpret_cast<uint32_t *>(smem + L.queue);
-    s.ntiles = ntiles;
+    s.ntiles = ntiles_max;
     if (kSmemState) {
         s.X = reinterpret_cast<uint32_t *>(smem + L.planes);
     } else {
-        s.X = a.gstate + (size_t)blockIdx.x * 2 * ntiles * 32;
+        s.X = a.gstate + (size_t)blockIdx.x * 2 * ntiles_max * 32;
     }
-    s.Y = s.X + ntiles * 32;
-    const int nmark = (ntiles + 15) / 16;
-    const uint32_t plane_bytes = (uint32_t)ntiles * 128u;
-    const long long HW = (long long)m.H * m.W;
-    const uint32_t hard_cap = (uint32_t)min(HW + 2, (long long)0x7fffffff);
+    s.Y = s.X + ntiles_max * 32;
 
-    if (threadIdx.x == 0) {
-        sh.tw_magic = (1ull << 40) / (unsigned long long)m.TW + 1ull;
-        if (kSmemState) {
-            mbar_init(&sh.mbar, 1);
-            fence_proxy_async_smem();
-        }
+    if (kSmemState && threadIdx.x == 0) {
+        mbar_init(&sh.mbar, 1);
+        fence_proxy_async_smem();
     }
     uint32_t phase = 0;
     __syncthreads();
 
     for (;;) {
-        if (threadIdx.x == 0) sh.sim = (int)atomicAdd(a.work_counter, 1u);
+        if (threadIdx.x == 0) {
+            const uint32_t w = atomicAdd(a.work_counter, 1u);
+            sh.sim = w < (uint32_t)a.n ? (a.order ? (int)a.order[w] : (int)w)
+                                       : a.n;
+        }
         __syncthreads();
         const int sim = sh.sim;
         if (sim >= a.n) break;
@@ -498,6 +497,19 @@ __global__ void __launch_bounds__(kSimMaxThreads, 2) k_simulate(SimLaunch a)
 
         // --- set-up of simulation `sim` ---
         if (threadIdx.x == 0) {
+            bool map_ok = true;
+            if (a.maps) {
+                const int mi = a.map_of_sim ? a.map_of_sim[sim] : 0;
+                map_ok = mi >= 0 && mi < a.nmaps;
+                sh.map = a.maps[map_ok ? mi : 0];
+            } else {
+                sh.map = a.map;
+            }
+            const long long hw = (long long)sh.map.H * sh.map.W;
+            sh.hard_cap = (uint32_t)min(hw + 2, (long long)0x7fffffff);
+            sh.nmark = (sh.map.ntiles + 15) / 16;
+            sh.tw_magic = (1ull << 40) / (unsigned long long)sh.map.TW + 1ull;
+            sh.status = map_ok ? 0u : FIRE_STATUS_BAD_MAP;
             const fire_params P = a.params[sim];
             for (int j = 0; j < 5; ++j) sh.beta[j] = P.b[j];
             sh.sp = screen_params(P.b);
@@ -505,8 +517,8 @@ __global__ void __launch_bounds__(kSimMaxThreads, 2) k_simulate(SimLaunch a)
             sh.key0 = (uint32_t)seed;
             sh.key1 = (uint32_t)(seed >> 32);
             const fire_cell g = a.ign[sim];
-            const bool ok = g.row >= 0 && g.row < m.H && g.col >= 0 &&
-                            g.col < m.W &&
+            const bool ok = map_ok && g.row >= 0 && g.row < m.H &&
+                            g.col >= 0 && g.col < m.W &&
                             (m.cfl[(long long)g.row * m.W + g.col] &
                              kFlagBurnable);
             sh.skip = ok ? 0 : 1;
@@ -517,12 +529,14 @@ __global__ void __launch_bounds__(kSimMaxThreads, 2) k_simulate(SimLaunch a)
             sh.qcount[0] = sh.qcount[1] = 0;
             sh.qvalid[0] = sh.qvalid[1] = (uint32_t)a.qcap;
             sh.trials = 0;
-            sh.status = 0;
             sh.last_new = 0;
             sh.burnt = 0;
             sh.inter = 0;
         }
-        for (int i = threadIdx.x; i < nmark; i += blockDim.x) s.marks[i] = 0;
+        __syncthreads();   // the map descriptor is read by every thread below
+        const uint32_t plane_bytes = (uint32_t)m.ntiles * 128u;
+        const long long HW = (long long)m.H * m.W;
+        for (int i = threadIdx.x; i < sh.nmark; i += blockDim.x) s.marks[i] = 0;
         if (kSmemState) {
             fence_proxy_async_smem();
             __syncthreads();
@@ -535,7 +549,7 @@ __global__ void __launch_bounds__(kSimMaxThreads, 2) k_simulate(SimLaunch a)
             const uint4 *src = reinterpret_cast<const uint4 *>(m.blk);
             uint4 *dx = reinterpret_cast<uint4 *>(s.X);
             uint4 *dy = reinterpret_cast<uint4 *>(s.Y);
-            for (int i = threadIdx.x; i < ntiles * 8; i += blockDim.x) {
+            for (int i = threadIdx.x; i < m.ntiles * 8; i += blockDim.x) {
                 const uint4 v = src[i];
                 dx[i] = v;
                 dy[i] = v;
@@ -571,7 +585,9 @@ __global__ void __launch_bounds__(kSimMaxThreads, 2) k_simulate(SimLaunch a)
             if (sh.skip) {
                 fire_result r{};
                 r.target = *m.tgt_count;
-                r.status = FIRE_STATUS_BAD_IGNITION;
+                r.status = (sh.status & FIRE_STATUS_BAD_MAP)
+                               ? FIRE_STATUS_BAD_MAP
+                               : FIRE_STATUS_BAD_IGNITION;
                 a.out[sim] = r;
             } else {
                 const int k0 = (g.row >> 5) * m.TW + (g.col >> 5);
@@ -606,7 +622,7 @@ __global__ void __launch_bounds__(kSimMaxThreads, 2) k_simulate(SimLaunch a)
             const uint32_t nA = sh.count[t % 3];
             if (nA == 0) break;
             const bool burning_now = sh.newflag[t % 3] != 0;
-            if (burning_now && ((a.max_steps && t >= a.max_steps) || t >= hard_cap)) {
+            if (burning_now && ((a.max_steps && t >= a.max_steps) || t >= sh.hard_cap)) {
                 capped = true;
                 break;
             }
@@ -614,7 +630,7 @@ __global__ void __launch_bounds__(kSimMaxThreads, 2) k_simulate(SimLaunch a)
                 sh.count[(t + 2) % 3] = 0;
                 sh.newflag[(t + 2) % 3] = 0;
             }
-            const uint16_t *list = s.lists + (t % 3) * ntiles;
+            const uint16_t *list = s.lists + (t % 3) * ntiles_max;
             for (uint32_t li = warp; li < nA; li += nwarps)
                 phase_a(s, list[li], t, lane);
             __syncthreads();
@@ -648,7 +664,7 @@ __global__ void __launch_bounds__(kSimMaxThreads, 2) k_simulate(SimLaunch a)
         __syncthreads();
         uint32_t nb = 0, ni = 0;
         bool border = false;
-        for (int w = threadIdx.x; w < ntiles * 32; w += blockDim.x) {
+        for (int w = threadIdx.x; w < m.ntiles * 32; w += blockDim.x) {
             const uint32_t bw = (s.X[w] | s.Y[w]) & ~__ldg(&m.blk[w]);
             if (!bw) continue;
             nb += __popc(bw);
@@ -733,8 +749,10 @@ __global__ void k_probabilities(MapDev m, const double *__restrict__ beta_dev,
         const uint32_t fl = m.cfl[i];
         const bool forest = fl & kFlagForest, up = (fl >> d) & 1u;
         if (p32) {
-            const ScreenCell sc = screen_cell(sp, forest, f.x, f.y, f.z, f.w);
-            p32[idx] = screen_p(screen_z(sc, up, d));
+            const float2 wd = m.wdiag[i];
+            const ScreenCell sc =
+                screen_cell(sp, forest, f.x, f.y, f.z, wd.x, f.w, wd.y);
+            p32[idx] = screen_p(screen_z(sc, sp.b3, up, d));
         }
         if (p64)
             p64[idx] = spec::logistic(
@@ -802,8 +820,10 @@ __global__ void k_screen_selftest(uint64_t n, uint64_t seed,
             u = (uint32_t)v;
         }
         const ScreenParams sp = screen_params(b);
-        const ScreenCell sc = screen_cell(sp, forest, psi, sig, cw, sw);
-        const float p32 = screen_p(screen_z(sc, up, d));
+        const float om1 = __double2float_rn(spec::omega(cw, sw, 1));
+        const float om3 = __double2float_rn(spec::omega(cw, sw, 3));
+        const ScreenCell sc = screen_cell(sp, forest, psi, sig, cw, om1, sw, om3);
+        const float p32 = screen_p(screen_z(sc, sp.b3, up, d));
         int dec = screen_decide(p32, u);
         const bool exact = (uint64_t)u < T;
         local[0]++;
@@ -837,6 +857,48 @@ __global__ void k_philox_blocks(uint64_t n, uint4 ctr, uint2 key, uint32_t *out)
 }
 
 // ---------------------------------------------------------------------------
+// Processing order of a multi-map batch: simulations grouped by map, largest
+// map first (rank 0 = most tiles), by a counting sort.  The order inside a
+// group is arbitrary; results do not depend on it.
+
+__global__ void k_order_count(int n, const int32_t *__restrict__ map_of_sim,
+                              int nmaps, const int32_t *__restrict__ rank,
+                              uint32_t *__restrict__ counts)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += gridDim.x * blockDim.x) {
+        const int mi = map_of_sim[i];
+        const int b = (mi >= 0 && mi < nmaps) ? rank[mi] : nmaps;
+        atomicAdd(&counts[b], 1u);
+    }
+}
+
+__global__ void k_order_scan(int nb, uint32_t *counts)
+{
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        uint32_t acc = 0;
+        for (int b = 0; b < nb; ++b) {
+            const uint32_t c = counts[b];
+            counts[b] = acc;
+            acc += c;
+        }
+    }
+}
+
+__global__ void k_order_scatter(int n, const int32_t *__restrict__ map_of_sim,
+                                int nmaps, const int32_t *__restrict__ rank,
+                                uint32_t *__restrict__ cursor,
+                                uint32_t *__restrict__ order)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += gridDim.x * blockDim.x) {
+        const int mi = map_of_sim[i];
+        const int b = (mi >= 0 && mi < nmaps) ? rank[mi] : nmaps;
+        order[atomicAdd(&cursor[b], 1u)] = (uint32_t)i;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Launchers.
 
 static int grid_for(long long n, int block)
@@ -849,12 +911,12 @@ static int grid_for(long long n, int block)
 
 cudaError_t launch_features(int H, int W, const uint8_t *veg, const float *elev,
                             const float *slope, const float *aspect,
-                            const float *wind, float4 *feat, uint16_t *cfl,
-                            cudaStream_t st)
+                            const float *wind, float4 *feat, float2 *wdiag,
+                            uint16_t *cfl, cudaStream_t st)
 {
     const long long n = (long long)H * W;
     k_features<<<grid_for(n, 256), 256, 0, st>>>(H, W, veg, elev, slope, aspect,
-                                                 wind, feat, cfl);
+                                                 wind, feat, wdiag, cfl);
     return cudaGetLastError();
 }
 
@@ -891,6 +953,19 @@ cudaError_t launch_simulate(const SimLaunch &a, bool smem_state, int nwarps,
         k_simulate<true><<<grid, nwarps * 32, smem_bytes, st>>>(a);
     else
         k_simulate<false><<<grid, nwarps * 32, smem_bytes, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_order(int n, const int32_t *map_of_sim, int nmaps,
+                         const int32_t *rank, uint32_t *counts, uint32_t *order,
+                         cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(counts, 0, (nmaps + 1) * sizeof(uint32_t), st);
+    if (e != cudaSuccess) return e;
+    const int g = grid_for(n, 256);
+    k_order_count<<<g, 256, 0, st>>>(n, map_of_sim, nmaps, rank, counts);
+    k_order_scan<<<1, 32, 0, st>>>(nmaps + 1, counts);
+    k_order_scatter<<<g, 256, 0, st>>>(n, map_of_sim, nmaps, rank, counts, order);
     return cudaGetLastError();
 }
 

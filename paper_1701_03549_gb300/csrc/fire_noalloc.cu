@@ -105,31 +105,11 @@ extern "C" int fire_simulate_batch_noalloc(fire_ctx *ctx, const fire_map *m,
 
     // launch shape, as fire_simulate_batch chooses it
     const int ntiles = m->dev.ntiles;
-    int nwarps = ctx->warps_per_block;
-    if (nwarps <= 0) nwarps = ntiles <= 16 ? 4 : (ntiles <= 64 ? 8 : 16);
-    nwarps = std::min(nwarps, kSimMaxThreads / 32);
-    int qcap = 4096;
-    SimLayout L = sim_layout(ntiles, qcap, true);
-    const bool smem_state = L.total <= ctx->max_smem_optin;
-    if (!smem_state) {
-        qcap = 16384;
-        L = sim_layout(ntiles, qcap, false);
-        if (L.total > ctx->max_smem_optin) {
-            qcap = 4096;
-            L = sim_layout(ntiles, qcap, false);
-        }
-    }
-    const void *kfn = simulate_kernel_ptr(smem_state);
-    e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)L.total);
-    if (e != cudaSuccess) return na_cuda(ctx, e, "cudaFuncSetAttribute");
-    int occ = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kfn, nwarps * 32,
-                                                      L.total);
-    if (e != cudaSuccess) return na_cuda(ctx, e, "occupancy");
-    if (occ < 1) return na_err(ctx, FIRE_EINVAL, "kernel does not fit");
-    const int bps = ctx->blocks_per_sm > 0 ? std::min(ctx->blocks_per_sm, occ) : occ;
-    long long grid = std::min((long long)bps * ctx->num_sms, (long long)n);
+    LaunchPlan plan;
+    rc = plan_launch(ctx, ntiles, n, &plan);
+    if (rc) return rc;
+    const bool smem_state = plan.smem_state;
+    long long grid = plan.grid;
     if (!smem_state) {
         // each resident block needs its own state buffer inside the array
         const size_t per_block = 2 * (size_t)ntiles * 128;
@@ -149,6 +129,11 @@ extern "C" int fire_simulate_batch_noalloc(fire_ctx *ctx, const fire_map *m,
     uint32_t *counters = static_cast<uint32_t *>(scratch);
     SimLaunch a;
     a.map = m->dev;
+    a.maps = nullptr;
+    a.nmaps = 1;
+    a.map_of_sim = nullptr;
+    a.order = nullptr;
+    a.ntiles_max = ntiles;
     a.n = n;
     a.params = params;
     a.ign = ignitions;
@@ -160,10 +145,11 @@ extern "C" int fire_simulate_batch_noalloc(fire_ctx *ctx, const fire_map *m,
     a.gstate = reinterpret_cast<uint32_t *>(static_cast<char *>(scratch) +
                                             kCounterBytes);
     a.max_steps = max_steps;
-    a.qcap = qcap;
+    a.qcap = plan.qcap;
     e = cudaMemsetAsync(counters, 0, 2 * sizeof(uint32_t), ctx->stream);
     if (e == cudaSuccess)
-        e = launch_simulate(a, smem_state, nwarps, (int)grid, L.total, ctx->stream);
+        e = launch_simulate(a, smem_state, plan.nwarps, (int)grid, plan.L.total,
+                            ctx->stream);
     if (e != cudaSuccess) return na_cuda(ctx, e, "no-alloc simulate launch");
     if (flags & FIRE_SYNC) {
         e = cudaStreamSynchronize(ctx->stream);

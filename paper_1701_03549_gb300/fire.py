@@ -31,11 +31,17 @@ FIRE_ESTEPS = -6
 FIRE_DEVICE_PTRS = 1
 FIRE_WANT_STEPS = 2
 FIRE_SYNC = 4
+FIRE_GRAPH = 8
 
 STATUS_BORDER = 1
 STATUS_STEP_CAP = 2
 STATUS_BAD_IGNITION = 4
 STATUS_TIMEOUT = 8
+STATUS_BAD_MAP = 16
+
+STATE_AUTO = 0
+STATE_SHARED = 1
+STATE_GLOBAL = 2
 
 # cudaStreamLegacy: the legacy default stream of the current context
 CUDA_STREAM_LEGACY = 1
@@ -52,7 +58,7 @@ EXPORTED = (
     "fire_target_upload", "fire_simulate_batch", "fire_fitness",
     "fire_thresholds", "fire_probabilities", "fire_map_features",
     "fire_screen_selftest", "fire_philox_blocks",
-    "fire_simulate_batch_noalloc",
+    "fire_simulate_batch_noalloc", "fire_simulate_multi", "fire_autotune",
 )
 
 
@@ -81,7 +87,7 @@ def load(path: str = LIB_PATH):
         "fire_destroy": (None, [vp]),
         "fire_last_error": (C.c_char_p, [vp]),
         "fire_sync": (i32, [vp]),
-        "fire_set_launch": (i32, [vp, i32, i32]),
+        "fire_set_launch": (i32, [vp, i32, i32, i32, i32]),
         "fire_maps_upload": (i32, [vp, i32, i32, C.c_float, vp, vp, vp, vp, vp,
                                    u32, C.POINTER(vp)]),
         "fire_map_free": (None, [vp]),
@@ -97,6 +103,9 @@ def load(path: str = LIB_PATH):
         "fire_philox_blocks": (i32, [vp, u64, vp, vp, u32, vp]),
         "fire_simulate_batch_noalloc": (i32, [vp, vp, i32, vp, vp, vp, u32,
                                               u32, vp, vp]),
+        "fire_simulate_multi": (i32, [vp, i32, vp, vp, i32, vp, vp, vp, u32,
+                                      u32, vp]),
+        "fire_autotune": (i32, [vp, i32, vp, vp, i32, vp, vp, vp, u32, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -175,9 +184,10 @@ class Context:
     def sync(self):
         return self.check(self.lib.fire_sync(self.h))
 
-    def set_launch(self, warps_per_block: int = 0, blocks_per_sm: int = 0):
-        return self.check(self.lib.fire_set_launch(self.h, warps_per_block,
-                                                   blocks_per_sm))
+    def set_launch(self, warps_per_block: int = 0, blocks_per_sm: int = 0,
+                   queue_entries: int = 0, state_mode: int = 0):
+        return self.check(self.lib.fire_set_launch(
+            self.h, warps_per_block, blocks_per_sm, queue_entries, state_mode))
 
     # -- maps
     def maps_upload(self, veg, elev, slope, aspect, wind, cell_m=30.0,
@@ -322,6 +332,72 @@ def fire_target_upload(ctx: Context, m: Map, burnt, device=False):
 def fire_simulate_batch(ctx: Context, m: Map, params, ignitions, seeds,
                         **kw):
     return m.simulate_batch(params, ignitions, seeds, **kw)
+
+
+class FireLaunch(C.Structure):
+    _fields_ = [("warps_per_block", C.c_int32), ("blocks_per_sm", C.c_int32),
+                ("queue_entries", C.c_int32), ("state_mode", C.c_int32),
+                ("ms", C.c_float)]
+
+
+def _map_handles(maps):
+    arr = (C.c_void_p * len(maps))(*[m.h.value if hasattr(m.h, "value")
+                                     else m.h for m in maps])
+    return arr
+
+
+def fire_simulate_multi(ctx: Context, maps, map_of_sim, params, ignitions,
+                        seeds, max_steps=0, device=False, out=None,
+                        graph=False, sync=False):
+    """Uneven batch over several maps (see fire_simulate_multi in fire.h).
+
+    Host mode: numpy inputs, returns the structured results.  Device mode:
+    torch CUDA tensors (map_of_sim int32, others as in simulate_batch) and a
+    preallocated `out` (n, 6) int32; returns `out`."""
+    lib = ctx.lib
+    handles = _map_handles(maps)
+    if device:
+        n = int(params.shape[0])
+        flags = FIRE_DEVICE_PTRS | (FIRE_GRAPH if graph else 0)
+        flags |= FIRE_SYNC if sync else 0
+        ctx.check(lib.fire_simulate_multi(
+            ctx.h, len(maps), handles, _ptr(map_of_sim), n, _ptr(params),
+            _ptr(ignitions), _ptr(seeds), int(max_steps), flags, _ptr(out)))
+        return out
+    p = _host(params, np.float64).reshape(-1, 5)
+    n = p.shape[0]
+    mi = _host(map_of_sim, np.int32).reshape(n)
+    g = _host(ignitions, np.int32).reshape(n, 2)
+    s = _host(seeds, np.uint64).reshape(n)
+    res = np.zeros(n, RESULT_DTYPE)
+    ctx.check(lib.fire_simulate_multi(
+        ctx.h, len(maps), handles, _ptr(mi), n, _ptr(p), _ptr(g), _ptr(s),
+        int(max_steps), 0, _ptr(res)))
+    return res
+
+
+def fire_autotune(ctx: Context, maps, map_of_sim, params, ignitions, seeds,
+                  device=False):
+    """Pick and record the fastest launch shape for this batch; returns it as
+    a dict (warps_per_block, blocks_per_sm, queue_entries, state_mode, ms)."""
+    lib = ctx.lib
+    handles = _map_handles(maps)
+    best = FireLaunch()
+    if device:
+        n = int(params.shape[0])
+        ctx.check(lib.fire_autotune(
+            ctx.h, len(maps), handles, _ptr(map_of_sim), n, _ptr(params),
+            _ptr(ignitions), _ptr(seeds), FIRE_DEVICE_PTRS, C.byref(best)))
+    else:
+        p = _host(params, np.float64).reshape(-1, 5)
+        n = p.shape[0]
+        mi = None if map_of_sim is None else _host(map_of_sim, np.int32)
+        g = _host(ignitions, np.int32).reshape(n, 2)
+        s = _host(seeds, np.uint64).reshape(n)
+        ctx.check(lib.fire_autotune(
+            ctx.h, len(maps), handles, _ptr(mi), n, _ptr(p), _ptr(g), _ptr(s),
+            0, C.byref(best)))
+    return {f: getattr(best, f) for f, _ in FireLaunch._fields_}
 
 
 def fire_fitness(ctx: Context, results, kind=FITNESS_PAPER_DELTA,
