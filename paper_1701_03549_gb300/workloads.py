@@ -74,3 +74,37 @@ def ga_generation_512(population: int = 256, replicates: int = 16,
     return Workload("ga_generation_512", land, ign, params,
                     np.tile(np.asarray(ign, np.int32), (n, 1)),
                     synth.replicate_seeds(n, first_seed))
+
+
+@dataclass
+class MultiWorkload:
+    name: str
+    lands: list
+    map_of_sim: np.ndarray   # (n,) int32
+    params: np.ndarray       # (n, 5)
+    ignitions: np.ndarray    # (n, 2) int32
+    seeds: np.ndarray        # (n,) uint64
+
+    @property
+    def n(self):
+        return self.params.shape[0]
+
+
+def uneven_fires(n_total: int = 100_000, param_seed: int = 0,
+                 first_seed: int = 1) -> MultiWorkload:
+    """Nine fires on grids 200x300 ... 2000x1500 (fire i: 200 + 225 i rows,
+    300 + 150 i columns, map seed 100 + i, constant 45 degree wind), each with
+    its centre ignition; n_total simulations spread as evenly as possible
+    over the fires (the first fires take the remainder), parameters drawn
+    from the Uniform[-30, 30] initial distribution of Table 1."""
+    shapes = synth.uneven_fire_shapes()
+    lands = [synth.landscape(H, W, seed=100 + i)
+             for i, (H, W) in enumerate(shapes)]
+    k = len(lands)
+    counts = [n_total // k + (1 if i < n_total % k else 0) for i in range(k)]
+    map_of_sim = np.repeat(np.arange(k, dtype=np.int32), counts)
+    ign = np.array([synth.centre_ignition(L.veg) for L in lands], np.int32)
+    params = synth.uniform_population(n_total, 2000 + param_seed)
+    return MultiWorkload("uneven_fires", lands, map_of_sim, params,
+                         ign[map_of_sim], synth.replicate_seeds(n_total,
+                                                               first_seed))
