@@ -259,6 +259,34 @@ FIRE_API int fire_autotune(fire_ctx *ctx, int nmaps, const fire_map *const *maps
                            const uint64_t *seeds, uint32_t flags,
                            fire_launch *best);
 
+/* One generation of the genetic algorithm of the paper's Appendix B on the
+ * device: elitism (the two best individuals carried over unchanged),
+ * tournament selection between two individuals drawn at random (one draw per
+ * new individual), one-point crossover of consecutive pairs, and per-gene
+ * mutation whose probability decreases as the generations advance.
+ *   genes_in[pop*genes], genes_out[pop*genes]  row-major individuals
+ *   fitness[pop]   lower is better; NaN ranks last; ties go to the lower index
+ *   generation / total_gens   g and NG of the schedule below
+ *   ga_seed        Philox key of this GA run
+ *   lo[genes], hi[genes]      bounds of each gene
+ * The paper leaves the constants open; this library uses: contestants
+ * a = (w0 pop) >> 32 and b = (w1 pop) >> 32 from Philox block (j, g, 0, 0) for
+ * new slot j; cut c = 1 + ((w0 (genes - 1)) >> 32) from block (j, g, 1, 0)
+ * for the pair (j, j + 1); gene k of child j mutates when w0 < floor(pm 2^32)
+ * of block (j, g, 2, k), pm = 0.2 (1 - g/NG) + 0.01, by
+ * (2 w1 2^-32 - 1) 0.1 (hi_k - lo_k) (1 - g/NG), clamped to [lo_k, hi_k].
+ * The result depends only on the arguments (bit-reproducible). */
+FIRE_API int ga_step(fire_ctx *ctx, int pop, int genes, const double *genes_in,
+                     const double *fitness, int generation, int total_gens,
+                     uint64_t ga_seed, const double *lo, const double *hi,
+                     uint32_t flags, double *genes_out);
+
+/* Mean of each of `groups` runs of per_group consecutive values (the fitness
+ * of a GA individual over its replicate simulations), summed in index order
+ * in double precision: out[groups]. */
+FIRE_API int fire_group_mean(fire_ctx *ctx, const double *values, int groups,
+                             int per_group, uint32_t flags, double *out);
+
 /* Fitness of n results (Eq. 2 or the Jaccard distance), double precision,
  * computed on the device.  A zero denominator gives NaN. */
 FIRE_API int fire_fitness(fire_ctx *ctx, const fire_result *results, int n, int kind,

@@ -90,6 +90,11 @@ def lib():
                                          C.c_void_p]
         L.orc_fitness.restype = C.c_double
         L.orc_fitness.argtypes = [C.c_uint32, C.c_uint32, C.c_uint32, C.c_int]
+        L.orc_ga_step.restype = C.c_int
+        L.orc_ga_step.argtypes = [C.c_int, C.c_int, C.c_void_p, C.c_void_p,
+                                  C.c_int, C.c_int, C.c_uint64, C.c_void_p,
+                                  C.c_void_p, C.c_void_p]
+        L.orc_group_mean.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_void_p]
         _lib = L
     return _lib
 
@@ -145,6 +150,30 @@ def omega(cw: float, sw: float, d: int) -> float:
 
 def fitness(burnt: int, inter: int, target: int, kind: int = 0) -> float:
     return lib().orc_fitness(burnt, inter, target, kind)
+
+
+def ga_step(genes, fitness, generation, total_gens, seed, lo, hi):
+    """One generation of the Appendix B genetic algorithm (see
+    fire_oracle.c for the reading of its unspecified constants)."""
+    g = np.ascontiguousarray(genes, np.float64)
+    P, G = g.shape
+    f = np.ascontiguousarray(fitness, np.float64).reshape(P)
+    lo = np.ascontiguousarray(lo, np.float64).reshape(G)
+    hi = np.ascontiguousarray(hi, np.float64).reshape(G)
+    out = np.zeros_like(g)
+    rc = lib().orc_ga_step(P, G, _p(g), _p(f), int(generation),
+                           int(total_gens), int(seed), _p(lo), _p(hi), _p(out))
+    if rc:
+        raise ValueError(f"orc_ga_step failed ({rc})")
+    return out
+
+
+def group_mean(values, per_group):
+    v = np.ascontiguousarray(values, np.float64)
+    groups = v.size // per_group
+    out = np.zeros(groups, np.float64)
+    lib().orc_group_mean(_p(v), groups, per_group, _p(out))
+    return out
 
 
 # ---------------------------------------------------------------------------

@@ -455,3 +455,124 @@ double orc_fitness(uint32_t burnt, uint32_t inter, uint32_t target, int kind)
     if (kind == 0) return sym / (double)target;
     return sym / uni;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Genetic algorithm of the paper's Appendix B: elitism, tournament selection
+ * between two individuals drawn at random, one-point crossover of pairs, and
+ * per-gene mutation whose probability decreases as the GA advances.  The
+ * paper leaves the constants open; the reading used here (the same one the
+ * CUDA library implements independently):
+ *   - order of individuals: lower fitness is better, NaN is worst, ties go
+ *     to the lower index;
+ *   - E = min(2, P) elites (best first) fill slots 0..E-1 unchanged;
+ *   - slot j >= E: Philox counter (j, g, 0, 0), contestants
+ *     a = (w0 * P) >> 32 and b = (w1 * P) >> 32, parent = the better one;
+ *   - pairs (j, j + 1), j = E, E + 2, ...: counter (j, g, 1, 0), cut
+ *     c = 1 + ((w0 * (G - 1)) >> 32) in [1, G - 1]; child j takes genes
+ *     [0, c) from its own parent and [c, G) from the partner's, child j + 1
+ *     the reverse; an unpaired last slot copies its parent; G = 1 never
+ *     crosses;
+ *   - gene k of child j: counter (j, g, 2, k); with s = 1 - g / NG,
+ *     pm = 0.2 s + 0.01 and T = floor(pm 2^32), the gene mutates iff w0 < T,
+ *     by delta = (2 u - 1) (0.1 (hi_k - lo_k)) s with u = w1 2^-32, and the
+ *     result is clamped to [lo_k, hi_k].
+ * Every step is a single IEEE-754 double operation in the written order. */
+static int orc_better(const double *f, int a, int b)
+{
+    const int na = f[a] != f[a], nb = f[b] != f[b];
+    if (na != nb) return nb;          /* the non-NaN one is better */
+    if (!na && f[a] != f[b]) return f[a] < f[b];
+    return a < b;
+}
+
+static void orc_block(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2,
+                      uint32_t c3, uint32_t out[4])
+{
+    uint32_t ctr[4] = {c0, c1, c2, c3};
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    orc_philox4x32_10(ctr, key, out);
+}
+
+int orc_ga_step(int P, int G, const double *genes_in, const double *fitness,
+                int g, int NG, uint64_t seed, const double *lo,
+                const double *hi, double *genes_out)
+{
+    if (P <= 0 || G <= 0 || NG <= 0) return -1;
+    const int E = P < 2 ? P : 2;
+    /* elites */
+    int best = 0;
+    for (int i = 1; i < P; ++i) if (orc_better(fitness, i, best)) best = i;
+    int second = -1;
+    for (int i = 0; i < P; ++i) {
+        if (i == best) continue;
+        if (second < 0 || orc_better(fitness, i, second)) second = i;
+    }
+    const int elite[2] = {best, second};
+    for (int e = 0; e < E; ++e)
+        for (int k = 0; k < G; ++k)
+            genes_out[(long)e * G + k] = genes_in[(long)elite[e] * G + k];
+    /* tournament parents */
+    int *parent = (int *)malloc(sizeof(int) * (size_t)P);
+    if (!parent) return -2;
+    for (int j = E; j < P; ++j) {
+        uint32_t w[4];
+        orc_block(seed, (uint32_t)j, (uint32_t)g, 0u, 0u, w);
+        const int a = (int)(((uint64_t)w[0] * (uint64_t)P) >> 32);
+        const int b = (int)(((uint64_t)w[1] * (uint64_t)P) >> 32);
+        parent[j] = orc_better(fitness, a, b) ? a : b;
+    }
+    /* crossover */
+    for (int j = E; j < P; j += 2) {
+        const double *pa = genes_in + (long)parent[j] * G;
+        double *ca = genes_out + (long)j * G;
+        if (j + 1 >= P || G < 2) {
+            for (int k = 0; k < G; ++k) ca[k] = pa[k];
+            if (j + 1 < P) {
+                const double *pb = genes_in + (long)parent[j + 1] * G;
+                double *cb = genes_out + (long)(j + 1) * G;
+                for (int k = 0; k < G; ++k) cb[k] = pb[k];
+            }
+            continue;
+        }
+        const double *pb = genes_in + (long)parent[j + 1] * G;
+        double *cb = genes_out + (long)(j + 1) * G;
+        uint32_t w[4];
+        orc_block(seed, (uint32_t)j, (uint32_t)g, 1u, 0u, w);
+        const int cut = 1 + (int)(((uint64_t)w[0] * (uint64_t)(G - 1)) >> 32);
+        for (int k = 0; k < G; ++k) {
+            ca[k] = k < cut ? pa[k] : pb[k];
+            cb[k] = k < cut ? pb[k] : pa[k];
+        }
+    }
+    free(parent);
+    /* mutation */
+    const double s = 1.0 - (double)g / (double)NG;
+    const double pm = 0.2 * s + 0.01;
+    const uint64_t T = (uint64_t)floor(pm * 4294967296.0);
+    for (int j = E; j < P; ++j) {
+        for (int k = 0; k < G; ++k) {
+            uint32_t w[4];
+            orc_block(seed, (uint32_t)j, (uint32_t)g, 2u, (uint32_t)k, w);
+            if ((uint64_t)w[0] >= T) continue;
+            const double u = (double)w[1] * 0x1p-32;
+            const double scale = (0.1 * (hi[k] - lo[k])) * s;
+            const double delta = (2.0 * u - 1.0) * scale;
+            double x = genes_out[(long)j * G + k] + delta;
+            if (x < lo[k]) x = lo[k];
+            if (x > hi[k]) x = hi[k];
+            genes_out[(long)j * G + k] = x;
+        }
+    }
+    return 0;
+}
+
+/* Mean of each group of per_group consecutive values (the fitness of a GA
+ * individual over its replicate simulations), summed in index order. */
+void orc_group_mean(const double *v, int groups, int per_group, double *out)
+{
+    for (int i = 0; i < groups; ++i) {
+        double s = 0.0;
+        for (int r = 0; r < per_group; ++r) s = s + v[(long)i * per_group + r];
+        out[i] = s / (double)per_group;
+    }
+}

@@ -1,0 +1,119 @@
+"""Parameter calibration on top of the CUDA library: the paper's genetic
+algorithm (Sec. 2.2, Appendix B), its brute-force Monte Carlo alternative
+(Appendix C) and the ensemble estimate (Sec. 2.1 rules: rank the simulations
+by fitness and keep those below a cutoff; the estimate is the ensemble's mean
+and standard deviation, the best set the one of least fitness).
+
+All simulation, fitness, replicate averaging and GA arithmetic runs in the
+library's kernels on device-resident torch tensors; this module only sequences
+the calls and keeps the per-generation history.  The context may issue work
+on a stream other than torch's, so tensors are synchronised at each hand-off
+between torch and the library.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import fire, synth
+
+
+@dataclass
+class History:
+    params: list = field(default_factory=list)     # per generation (P, 5)
+    fitness: list = field(default_factory=list)    # per generation (P,)
+
+    def all(self):
+        return np.concatenate(self.params), np.concatenate(self.fitness)
+
+
+def sim_seeds(base: int, generation: int, pop: int, reps: int) -> np.ndarray:
+    """Seeds of generation g: base + (g P + i) R + r for individual i,
+    replicate r."""
+    first = base + (generation * pop) * reps
+    return np.arange(first, first + pop * reps, dtype=np.uint64)
+
+
+def evaluate(ctx, m, params_dev, ignition, seeds, reps, kind, torch):
+    """Mean fitness over `reps` replicates of each parameter vector (device
+    tensors in, device tensor out)."""
+    dev = params_dev.device
+    P = params_dev.shape[0]
+    n = P * reps
+    p_sims = params_dev.repeat_interleave(reps, dim=0).contiguous()
+    ign = torch.tensor(np.tile(np.asarray(ignition, np.int32), (n, 1)),
+                       device=dev)
+    s = torch.tensor(np.asarray(seeds, np.uint64).view(np.int64), device=dev)
+    out = torch.zeros((n, 6), dtype=torch.int32, device=dev)
+    fit = torch.zeros(n, dtype=torch.float64, device=dev)
+    mean = torch.zeros(P, dtype=torch.float64, device=dev)
+    torch.cuda.synchronize(dev)
+    m.simulate_batch(p_sims, ign, s, device=True, out=out)
+    fire.fire_fitness(ctx, out, kind, device=True, out=fit)
+    fire.fire_group_mean(ctx, fit, reps, device=True, out=mean)
+    ctx.sync()
+    return mean
+
+
+def run_ga(ctx, m, ignition, pop=256, reps=16, generations=50,
+           prior="gauss", lo=-30.0, hi=30.0, ga_seed=1, sim_seed=1,
+           kind=fire.FITNESS_JACCARD, init=None):
+    """The Appendix B genetic algorithm on map `m` (which holds the target).
+    Returns the History of every generation's population and fitness."""
+    import torch
+
+    dev = torch.device("cuda", ctx.device)
+    G = 5
+    if init is None:
+        init = (synth.gauss_population(pop, ga_seed) if prior == "gauss"
+                else synth.uniform_population(pop, ga_seed, lo=lo, hi=hi))
+    init = np.clip(np.asarray(init, np.float64), lo, hi)
+    genes = torch.tensor(init, dtype=torch.float64, device=dev)
+    nxt = torch.empty_like(genes)
+    tlo = torch.full((G,), float(lo), dtype=torch.float64, device=dev)
+    thi = torch.full((G,), float(hi), dtype=torch.float64, device=dev)
+    hist = History()
+    for g in range(generations):
+        f = evaluate(ctx, m, genes, ignition,
+                     sim_seeds(sim_seed, g, pop, reps), reps, kind, torch)
+        hist.params.append(genes.cpu().numpy())
+        hist.fitness.append(f.cpu().numpy())
+        if g + 1 < generations:
+            torch.cuda.synchronize(dev)
+            fire.ga_step(ctx, genes, f, g, generations, ga_seed, tlo, thi,
+                         device=True, out=nxt)
+            ctx.sync()
+            genes, nxt = nxt, genes
+    return hist
+
+
+def run_mc(ctx, m, ignition, n=4096, reps=1, lo=-30.0, hi=30.0, seed=1,
+           sim_seed=1, kind=fire.FITNESS_JACCARD):
+    """Appendix C brute-force Monte Carlo: parameters uniform in [lo, hi]^5,
+    each simulated `reps` times; returns (params, mean fitness)."""
+    import torch
+
+    dev = torch.device("cuda", ctx.device)
+    params = synth.uniform_population(n, seed, lo=lo, hi=hi)
+    f = evaluate(ctx, m, torch.tensor(params, dtype=torch.float64, device=dev),
+                 ignition, sim_seeds(sim_seed, 0, n, reps), reps, kind, torch)
+    return params, f.cpu().numpy()
+
+
+def ensemble(params, fitness, cutoff=None, keep=None):
+    """Ensemble estimate: the simulations with fitness <= cutoff (or the
+    `keep` best); returns dict(mean, sd, best, size)."""
+    params = np.asarray(params, np.float64)
+    fitness = np.asarray(fitness, np.float64)
+    order = np.argsort(fitness, kind="stable")
+    if cutoff is not None:
+        sel = order[fitness[order] <= cutoff]
+    else:
+        sel = order[: (keep or max(1, len(order) // 10))]
+    if sel.size == 0:
+        sel = order[:1]
+    ens = params[sel]
+    sd = ens.std(axis=0, ddof=1) if len(sel) > 1 else np.zeros(params.shape[1])
+    return {"mean": ens.mean(axis=0), "sd": sd, "best": params[order[0]],
+            "best_fitness": float(fitness[order[0]]), "size": int(sel.size)}

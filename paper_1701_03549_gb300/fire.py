@@ -59,6 +59,7 @@ EXPORTED = (
     "fire_thresholds", "fire_probabilities", "fire_map_features",
     "fire_screen_selftest", "fire_philox_blocks",
     "fire_simulate_batch_noalloc", "fire_simulate_multi", "fire_autotune",
+    "ga_step", "fire_group_mean",
 )
 
 
@@ -106,6 +107,9 @@ def load(path: str = LIB_PATH):
         "fire_simulate_multi": (i32, [vp, i32, vp, vp, i32, vp, vp, vp, u32,
                                       u32, vp]),
         "fire_autotune": (i32, [vp, i32, vp, vp, i32, vp, vp, vp, u32, vp]),
+        "ga_step": (i32, [vp, i32, i32, vp, vp, i32, i32, u64, vp, vp, u32,
+                          vp]),
+        "fire_group_mean": (i32, [vp, vp, i32, i32, u32, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -398,6 +402,46 @@ def fire_autotune(ctx: Context, maps, map_of_sim, params, ignitions, seeds,
             ctx.h, len(maps), handles, _ptr(mi), n, _ptr(p), _ptr(g), _ptr(s),
             0, C.byref(best)))
     return {f: getattr(best, f) for f, _ in FireLaunch._fields_}
+
+
+def ga_step(ctx: Context, genes, fitness, generation, total_gens, ga_seed,
+            lo, hi, device=False, out=None):
+    """One GA generation (Appendix B).  Host mode: numpy in/out.  Device mode:
+    torch CUDA float64 tensors (genes (P, G), fitness (P,), lo, hi (G,)) and a
+    preallocated `out` like genes."""
+    lib = ctx.lib
+    if device:
+        P, G = int(genes.shape[0]), int(genes.shape[1])
+        ctx.check(lib.ga_step(ctx.h, P, G, _ptr(genes), _ptr(fitness),
+                              int(generation), int(total_gens), int(ga_seed),
+                              _ptr(lo), _ptr(hi), FIRE_DEVICE_PTRS, _ptr(out)))
+        return out
+    g = _host(genes, np.float64)
+    P, G = g.shape
+    f = _host(fitness, np.float64).reshape(P)
+    l = _host(lo, np.float64).reshape(G)
+    h = _host(hi, np.float64).reshape(G)
+    o = np.zeros_like(g)
+    ctx.check(lib.ga_step(ctx.h, P, G, _ptr(g), _ptr(f), int(generation),
+                          int(total_gens), int(ga_seed), _ptr(l), _ptr(h), 0,
+                          _ptr(o)))
+    return o
+
+
+def fire_group_mean(ctx: Context, values, per_group, device=False, out=None):
+    lib = ctx.lib
+    if device:
+        groups = int(values.numel()) // int(per_group)
+        ctx.check(lib.fire_group_mean(ctx.h, _ptr(values), groups,
+                                      int(per_group), FIRE_DEVICE_PTRS,
+                                      _ptr(out)))
+        return out
+    v = _host(values, np.float64).ravel()
+    groups = v.size // int(per_group)
+    o = np.zeros(groups, np.float64)
+    ctx.check(lib.fire_group_mean(ctx.h, _ptr(v), groups, int(per_group), 0,
+                                  _ptr(o)))
+    return o
 
 
 def fire_fitness(ctx: Context, results, kind=FITNESS_PAPER_DELTA,

@@ -13,8 +13,9 @@ HEADER = os.path.join(ROOT, "include", "fire.h")
 
 def _declared():
     txt = open(HEADER).read()
-    return sorted(set(re.findall(r"^FIRE_API\s+[\w\s\*]*?\b(fire_\w+)\s*\(",
-                                 txt, flags=re.M)))
+    return sorted(set(re.findall(
+        r"^FIRE_API\s+(?:const\s+)?\w+\s*\**\s*(\w+)\s*\(", txt,
+        flags=re.M)))
 
 
 @pytest.fixture(scope="module")
@@ -27,7 +28,7 @@ def libpath():
 def test_header_declares_the_boundary():
     names = _declared()
     for required in ("fire_create", "fire_maps_upload", "fire_target_upload",
-                     "fire_simulate_batch", "fire_fitness"):
+                     "fire_simulate_batch", "fire_fitness", "ga_step"):
         assert required in names
 
 

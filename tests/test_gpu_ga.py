@@ -1,0 +1,103 @@
+"""GPU parity of the genetic-algorithm layer (Appendix B): ga_step and the
+replicate mean against the oracle, bit for bit, and a whole GA run driven by
+the library against the same run driven by the oracle."""
+import numpy as np
+import pytest
+
+from paper_1701_03549_gb300 import synth, workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    import oracle
+
+    __graft_entry__.build()
+    oracle.build()
+    from paper_1701_03549_gb300 import fire
+
+    ctx = fire.Context(0)
+    yield torch, fire, oracle, ctx
+    ctx.close()
+
+
+@pytest.mark.parametrize("P,G", [(256, 5), (257, 5), (2, 5), (3, 7), (1, 5),
+                                 (64, 1), (100, 2)])
+def test_ga_step_matches_oracle(env, P, G):
+    torch, fire, oracle, ctx = env
+    rng = np.random.default_rng(P * 31 + G)
+    genes = rng.normal(0, 8, (P, G))
+    f = rng.random(P)
+    f[rng.random(P) < 0.1] = np.nan
+    f[rng.random(P) < 0.2] = 0.5
+    lo, hi = np.full(G, -30.0), np.full(G, 30.0)
+    for g, NG, seed in ((0, 50, 1), (17, 50, 2 ** 40 + 3), (49, 50, 7)):
+        got = fire.ga_step(ctx, genes, f, g, NG, seed, lo, hi)
+        want = oracle.ga_step(genes, f, g, NG, seed, lo, hi)
+        assert np.array_equal(got.view(np.uint64), want.view(np.uint64))
+
+
+def test_group_mean_matches_oracle(env):
+    torch, fire, oracle, ctx = env
+    v = np.random.default_rng(1).normal(0, 10, 256 * 16)
+    assert np.array_equal(fire.fire_group_mean(ctx, v, 16),
+                          oracle.group_mean(v, 16))
+
+
+def test_ga_run_matches_oracle_driven_run(env):
+    """Four generations of population 8 x 2 replicates on a small map: every
+    generation's population and fitness must equal those of the same GA run
+    with the oracle's simulation, fitness, averaging and GA step."""
+    torch, fire, oracle, ctx = env
+    from paper_1701_03549_gb300 import calibrate
+
+    land = synth.landscape(48, 56, seed=31, wind_seed=31)
+    ign = synth.centre_ignition(land.veg)
+    F = oracle.Features(land)
+    _, target = workloads.pick_target(
+        lambda s: F.simulate(synth.TRUTH_BETA, ign, s)[1] >= 0,
+        int(F.burnable.sum()))
+    m = ctx.landscape_upload(land)
+    m.target_upload(target)
+    P, R, NG = 8, 2, 4
+    hist = calibrate.run_ga(ctx, m, ign, pop=P, reps=R, generations=NG,
+                            ga_seed=11, sim_seed=5)
+    genes = np.clip(synth.gauss_population(P, 11), -30, 30)
+    lo, hi = np.full(5, -30.0), np.full(5, 30.0)
+    for g in range(NG):
+        seeds = calibrate.sim_seeds(5, g, P, R)
+        fit = []
+        for i in range(P * R):
+            o, _ = F.simulate(genes[i // R], ign, int(seeds[i]), target=target,
+                              want_steps=False)
+            fit.append(oracle.fitness(o["burnt"], o["inter"], o["target"], 1))
+        f = oracle.group_mean(np.asarray(fit), R)
+        assert np.array_equal(hist.params[g], genes), g
+        assert np.array_equal(hist.fitness[g], f), g
+        genes = oracle.ga_step(genes, f, g, NG, 11, lo, hi)
+    m.free()
+
+
+def test_ga_improves_fitness_on_a_synthetic_scar(env):
+    torch, fire, oracle, ctx = env
+    from paper_1701_03549_gb300 import calibrate
+
+    land = synth.landscape(128, 128, seed=1)
+    ign = synth.centre_ignition(land.veg)
+    m = ctx.landscape_upload(land)
+    _, bs = m.simulate_batch([synth.TRUTH_BETA], [ign], [synth.TARGET_SEED + 1],
+                             want_steps=True)
+    m.target_upload(bs[0] >= 0)
+    hist = calibrate.run_ga(ctx, m, ign, pop=128, reps=4, generations=15,
+                            ga_seed=3, sim_seed=9)
+    first, last = hist.fitness[0], hist.fitness[-1]
+    assert np.nanmean(last) < np.nanmean(first)
+    assert np.nanmin(last) <= np.nanmin(first) + 0.05
+    est = calibrate.ensemble(*hist.all(), keep=64)
+    assert est["size"] == 64 and np.all(np.isfinite(est["mean"]))
+    m.free()
