@@ -281,6 +281,26 @@ FIRE_API int ga_step(fire_ctx *ctx, int pop, int genes, const double *genes_in,
                      uint64_t ga_seed, const double *lo, const double *hi,
                      uint32_t flags, double *genes_out);
 
+/* Ignition-point search: the ignition treated as unknown and sought inside
+ * the map's target scar (the paper's variable-ignition experiment).  A
+ * lat_h x lat_w lattice of equal strips spans the scar's bounding box;
+ * lattice point (a, b) sits at row r0 + floor((2a+1)(r1-r0+1) / (2 lat_h))
+ * and column c0 + floor((2b+1)(c1-c0+1) / (2 lat_w)) and is moved to the
+ * nearest burnable burnt cell (squared distance, ties to the lower row-major
+ * index).  Each candidate c = a lat_w + b is simulated reps times with
+ * `params` and seeds seed + c reps + r; fitness_map[c] is the replicate mean
+ * of fitness `kind`.  The ensemble is the candidates with fitness <= cutoff
+ * (or, if none, the best one); xy_mean_sd = {mean x, sd x, mean y, sd y} of
+ * its ignitions with x = column, y = row (sample standard deviation, 0 for
+ * a single candidate).  cells (nullable) receives the candidates as
+ * (row, col) pairs.  FIRE_EINVAL when the target is empty or has no
+ * burnable cell.  Synchronous. */
+FIRE_API int ignition_search(fire_ctx *ctx, const fire_map *map,
+                             const fire_params *params, int lat_h, int lat_w,
+                             int reps, uint64_t seed, int kind, double cutoff,
+                             uint32_t flags, double *fitness_map,
+                             int32_t *cells, double xy_mean_sd[4]);
+
 /* Mean of each of `groups` runs of per_group consecutive values (the fitness
  * of a GA individual over its replicate simulations), summed in index order
  * in double precision: out[groups]. */

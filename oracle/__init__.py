@@ -95,6 +95,12 @@ def lib():
                                   C.c_int, C.c_int, C.c_uint64, C.c_void_p,
                                   C.c_void_p, C.c_void_p]
         L.orc_group_mean.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_void_p]
+        L.orc_ignition_search.restype = C.c_int
+        L.orc_ignition_search.argtypes = [C.POINTER(_Map), C.c_void_p,
+                                          C.c_void_p, C.c_int, C.c_int,
+                                          C.c_int, C.c_uint64, C.c_int,
+                                          C.c_double, C.c_void_p, C.c_void_p,
+                                          C.c_void_p]
         _lib = L
     return _lib
 
@@ -239,6 +245,24 @@ class Features:
         out = dict(burnt=int(res[0]), inter=int(res[1]), target=int(res[2]),
                    steps=int(res[3]), status=int(res[4]), trials=int(res[5]))
         return out, bs
+
+    def ignition_search(self, target, beta, lat_h, lat_w, reps, seed,
+                        kind=KIND_PAPER_DELTA, cutoff=1.5):
+        """Lattice ignition search (see fire_oracle.c): returns
+        (fitness map (lat_h, lat_w), cells (lat_h, lat_w, 2) as (row, col),
+        [x mean, x sd, y mean, y sd])."""
+        b = np.ascontiguousarray(beta, np.float64)
+        tg = np.ascontiguousarray(target, np.uint8)
+        fm = np.zeros((lat_h, lat_w), np.float64)
+        cells = np.zeros((lat_h, lat_w, 2), np.int32)
+        xy = np.zeros(4, np.float64)
+        rc = lib().orc_ignition_search(C.byref(self._m), _p(tg), _p(b),
+                                       int(lat_h), int(lat_w), int(reps),
+                                       int(seed), int(kind), float(cutoff),
+                                       _p(fm), _p(cells), _p(xy))
+        if rc:
+            raise ValueError("target has no burnable burnt cell")
+        return fm, cells, xy
 
     def burn_frequency(self, beta, ignition, seed0: int, nseeds: int):
         b = np.ascontiguousarray(beta, np.float64)

@@ -576,3 +576,98 @@ void orc_group_mean(const double *v, int groups, int per_group, double *out)
         out[i] = s / (double)per_group;
     }
 }
+
+/* ------------------------------------------------------------------------ */
+/* Ignition-point search (Sec. 3: the ignition point treated as unknown and
+ * drawn from inside the reference fire's burnt area).  The reading used:
+ *   - the target's burnt cells span rows [r0, r1], columns [c0, c1];
+ *   - lattice point (a, b), a < LH, b < LW, sits at row
+ *     r0 + floor((2a + 1)(r1 - r0 + 1) / (2 LH)) and column
+ *     c0 + floor((2b + 1)(c1 - c0 + 1) / (2 LW)) (centres of equal strips);
+ *   - its candidate ignition is the burnable burnt cell nearest to it
+ *     (squared distance, ties to the lower row-major index);
+ *   - candidate c = a LW + b is simulated reps times with seeds
+ *     seed + c reps + r; its fitness is the mean over the replicates;
+ *   - the ensemble is the candidates with fitness <= cutoff (or, if none,
+ *     the best one, ties to the lower index); the estimate is the mean and
+ *     sample standard deviation of their x = column and y = row.
+ * Returns 0, or -1 when the target has no burnable burnt cell. */
+int orc_ignition_search(const orc_map *m, const uint8_t *target,
+                        const double beta[5], int LH, int LW, int reps,
+                        uint64_t seed, int kind, double cutoff,
+                        double *fitness_map, int32_t *cells, double xy[4])
+{
+    const int H = m->H, W = m->W;
+    int r0 = H, r1 = -1, c0 = W, c1 = -1;
+    for (int r = 0; r < H; ++r)
+        for (int c = 0; c < W; ++c)
+            if (target[(long)r * W + c]) {
+                if (r < r0) r0 = r;
+                if (r > r1) r1 = r;
+                if (c < c0) c0 = c;
+                if (c > c1) c1 = c;
+            }
+    if (r1 < 0) return -1;
+    const int L = LH * LW;
+    for (int a = 0; a < LH; ++a) {
+        for (int b = 0; b < LW; ++b) {
+            const long long R = r0 + ((2LL * a + 1) * (r1 - r0 + 1)) / (2LL * LH);
+            const long long C = c0 + ((2LL * b + 1) * (c1 - c0 + 1)) / (2LL * LW);
+            long long best = -1, bestd = 0;
+            for (long i = 0; i < (long)H * W; ++i) {
+                if (!target[i] || !m->burnable[i]) continue;
+                const long long dr = i / W - R, dc = i % W - C;
+                const long long d = dr * dr + dc * dc;
+                if (best < 0 || d < bestd) { best = i; bestd = d; }
+            }
+            if (best < 0) return -1;
+            const int cidx = a * LW + b;
+            cells[2 * cidx] = (int32_t)(best / W);
+            cells[2 * cidx + 1] = (int32_t)(best % W);
+        }
+    }
+    for (int cidx = 0; cidx < L; ++cidx) {
+        double s = 0.0;
+        for (int r = 0; r < reps; ++r) {
+            uint32_t res[6];
+            orc_simulate(m, target, beta, cells[2 * cidx], cells[2 * cidx + 1],
+                         seed + (uint64_t)cidx * (uint64_t)reps + (uint64_t)r, 0,
+                         NULL, res);
+            s = s + orc_fitness(res[0], res[1], res[2], kind);
+        }
+        fitness_map[cidx] = s / (double)reps;
+    }
+    /* ensemble */
+    int k = 0;
+    double sx = 0.0, sy = 0.0;
+    for (int cidx = 0; cidx < L; ++cidx)
+        if (fitness_map[cidx] <= cutoff) {
+            k++;
+            sx = sx + (double)cells[2 * cidx + 1];
+            sy = sy + (double)cells[2 * cidx];
+        }
+    int bestc = 0;
+    if (k == 0) {
+        for (int cidx = 1; cidx < L; ++cidx)
+            if (orc_better(fitness_map, cidx, bestc)) bestc = cidx;
+        xy[0] = (double)cells[2 * bestc + 1];
+        xy[1] = 0.0;
+        xy[2] = (double)cells[2 * bestc];
+        xy[3] = 0.0;
+        return 0;
+    }
+    const double mx = sx / (double)k, my = sy / (double)k;
+    double vx = 0.0, vy = 0.0;
+    for (int cidx = 0; cidx < L; ++cidx)
+        if (fitness_map[cidx] <= cutoff) {
+            const double dx = (double)cells[2 * cidx + 1] - mx;
+            const double dy = (double)cells[2 * cidx] - my;
+            vx = vx + dx * dx;
+            vy = vy + dy * dy;
+        }
+    xy[0] = mx;
+    xy[1] = k > 1 ? sqrt(vx / (double)(k - 1)) : 0.0;
+    xy[2] = my;
+    xy[3] = k > 1 ? sqrt(vy / (double)(k - 1)) : 0.0;
+    return 0;
+}

@@ -59,7 +59,7 @@ EXPORTED = (
     "fire_thresholds", "fire_probabilities", "fire_map_features",
     "fire_screen_selftest", "fire_philox_blocks",
     "fire_simulate_batch_noalloc", "fire_simulate_multi", "fire_autotune",
-    "ga_step", "fire_group_mean",
+    "ga_step", "fire_group_mean", "ignition_search",
 )
 
 
@@ -110,6 +110,8 @@ def load(path: str = LIB_PATH):
         "ga_step": (i32, [vp, i32, i32, vp, vp, i32, i32, u64, vp, vp, u32,
                           vp]),
         "fire_group_mean": (i32, [vp, vp, i32, i32, u32, vp]),
+        "ignition_search": (i32, [vp, vp, vp, i32, i32, i32, u64, i32,
+                                  C.c_double, u32, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -426,6 +428,22 @@ def ga_step(ctx: Context, genes, fitness, generation, total_gens, ga_seed,
                           int(total_gens), int(ga_seed), _ptr(l), _ptr(h), 0,
                           _ptr(o)))
     return o
+
+
+def ignition_search(ctx: Context, m: Map, beta, lat_h, lat_w, reps, seed,
+                    kind=FITNESS_PAPER_DELTA, cutoff=1.5):
+    """Lattice ignition search on the map's target (see fire.h); returns
+    (fitness map (lat_h, lat_w), cells (lat_h, lat_w, 2), [x mean, x sd,
+    y mean, y sd])."""
+    b = _host(beta, np.float64).reshape(5)
+    fm = np.zeros((lat_h, lat_w), np.float64)
+    cells = np.zeros((lat_h, lat_w, 2), np.int32)
+    xy = np.zeros(4, np.float64)
+    ctx.check(ctx.lib.ignition_search(ctx.h, m.h, _ptr(b), int(lat_h),
+                                      int(lat_w), int(reps), int(seed),
+                                      int(kind), float(cutoff), 0, _ptr(fm),
+                                      _ptr(cells), _ptr(xy)))
+    return fm, cells, xy
 
 
 def fire_group_mean(ctx: Context, values, per_group, device=False, out=None):
