@@ -107,6 +107,12 @@ enum {
 #define FIRE_SYNC 4u         /* block until the work has finished            */
 #define FIRE_GRAPH 8u        /* capture the call's device work as a CUDA graph
                                 once and replay it on later identical calls  */
+#define FIRE_CELL_UNIFORM 16u /* the paper's own CUDA update (Sec. 2.3): one
+                                uniform per target cell and step, word 0 of
+                                Philox block (cell, step, 2, 0), succeeding iff
+                                u < floor((1 - q) 2^32) with q the product of
+                                (1 - p_d) over the burning neighbours in
+                                increasing d, in double precision            */
 
 /* fire_result.status bits */
 #define FIRE_STATUS_BORDER 1u        /* a burnt cell lies on the grid edge   */

@@ -84,6 +84,15 @@ def lib():
         L.orc_simulate.argtypes = [C.POINTER(_Map), C.c_void_p, C.c_void_p,
                                    C.c_int, C.c_int, C.c_uint64, C.c_uint32,
                                    C.c_void_p, C.c_void_p]
+        L.orc_simulate_mode.restype = C.c_int
+        L.orc_simulate_mode.argtypes = [C.POINTER(_Map), C.c_void_p,
+                                        C.c_void_p, C.c_int, C.c_int,
+                                        C.c_uint64, C.c_uint32, C.c_int,
+                                        C.c_void_p, C.c_void_p]
+        L.orc_burn_frequency_mode.restype = C.c_int
+        L.orc_burn_frequency_mode.argtypes = [C.POINTER(_Map), C.c_void_p,
+                                              C.c_int, C.c_int, C.c_uint64,
+                                              C.c_long, C.c_int, C.c_void_p]
         L.orc_burn_frequency.restype = C.c_int
         L.orc_burn_frequency.argtypes = [C.POINTER(_Map), C.c_void_p, C.c_int,
                                          C.c_int, C.c_uint64, C.c_long,
@@ -226,18 +235,20 @@ class Features:
         return T
 
     def simulate(self, beta, ignition, seed: int, target=None,
-                 want_steps: bool = True, max_steps: int = 0):
-        """Run one fire; returns (result dict, burn-step map or None)."""
+                 want_steps: bool = True, max_steps: int = 0, mode: int = 0):
+        """Run one fire; returns (result dict, burn-step map or None).
+        mode 0: one trial per burning neighbour; mode 1: one uniform per
+        cell against 1 - prod(1 - p_i) (see fire_oracle.c)."""
         b = np.ascontiguousarray(beta, np.float64)
         res = np.zeros(6, np.uint32)
         bs = np.zeros((self.H, self.W), np.int32) if want_steps else None
         tg = None if target is None else np.ascontiguousarray(target,
                                                               np.uint8)
-        rc = lib().orc_simulate(C.byref(self._m),
-                                None if tg is None else _p(tg), _p(b),
-                                int(ignition[0]), int(ignition[1]),
-                                int(seed), int(max_steps),
-                                None if bs is None else _p(bs), _p(res))
+        rc = lib().orc_simulate_mode(C.byref(self._m),
+                                     None if tg is None else _p(tg), _p(b),
+                                     int(ignition[0]), int(ignition[1]),
+                                     int(seed), int(max_steps), int(mode),
+                                     None if bs is None else _p(bs), _p(res))
         if rc == -4:
             raise ValueError("ignition outside the grid or non-burnable")
         if rc:
@@ -264,12 +275,14 @@ class Features:
             raise ValueError("target has no burnable burnt cell")
         return fm, cells, xy
 
-    def burn_frequency(self, beta, ignition, seed0: int, nseeds: int):
+    def burn_frequency(self, beta, ignition, seed0: int, nseeds: int,
+                       mode: int = 0):
         b = np.ascontiguousarray(beta, np.float64)
         counts = np.zeros((self.H, self.W), np.uint32)
-        rc = lib().orc_burn_frequency(C.byref(self._m), _p(b),
-                                      int(ignition[0]), int(ignition[1]),
-                                      int(seed0), int(nseeds), _p(counts))
+        rc = lib().orc_burn_frequency_mode(C.byref(self._m), _p(b),
+                                           int(ignition[0]), int(ignition[1]),
+                                           int(seed0), int(nseeds), int(mode),
+                                           _p(counts))
         if rc:
             raise RuntimeError(f"oracle burn_frequency failed ({rc})")
         return counts

@@ -344,9 +344,56 @@ void orc_thresholds(const orc_map *m, const double beta[5], uint64_t *T)
  * Returns 0, or -4 when the ignition is outside the grid or non-burnable. */
 enum { ORC_UNBURNT = 0, ORC_BURNING = 1, ORC_BURNT = 2, ORC_BLOCKED = 3 };
 
+/* Update rules.  Mode 0: one Bernoulli trial per (target, burning
+ * neighbour), trial d succeeding iff u_d < T_d.  Mode 1, the paper's own
+ * CUDA rule (Sec. 2.3): one uniform per target cell and step, compared with
+ * the cell's ignition probability 1 - prod_d (1 - p_d) over its burning
+ * neighbours: success iff u < floor((1 - q) 2^32), q the product of (1 - p_d)
+ * in increasing d in double precision, u word 0 of the Philox block with
+ * counter (cell, step, 2, 0). */
+uint64_t orc_cell_threshold(const orc_map *m, const double beta[5], long i,
+                            unsigned dirmask)
+{
+    double q = 1.0;
+    for (int d = 0; d < 8; ++d) {
+        if (!((dirmask >> d) & 1u)) continue;
+        const double z = orc_z(m, beta, i, d);
+        double p;
+        if (!(z > -40.0)) p = 0.0;
+        else if (z >= 40.0) p = 1.0;
+        else p = orc_logistic(z);
+        q = q * (1.0 - p);
+    }
+    const double P = 1.0 - q;
+    return (uint64_t)floor(P * 4294967296.0);
+}
+
+static int orc_simulate_impl(const orc_map *m, const uint8_t *target,
+                             const double beta[5], int ign_r, int ign_c,
+                             uint64_t seed, uint32_t max_steps, int mode,
+                             int32_t *burn_step, uint32_t result[6]);
+
 int orc_simulate(const orc_map *m, const uint8_t *target, const double beta[5],
                  int ign_r, int ign_c, uint64_t seed, uint32_t max_steps,
                  int32_t *burn_step, uint32_t result[6])
+{
+    return orc_simulate_impl(m, target, beta, ign_r, ign_c, seed, max_steps, 0,
+                             burn_step, result);
+}
+
+int orc_simulate_mode(const orc_map *m, const uint8_t *target,
+                      const double beta[5], int ign_r, int ign_c,
+                      uint64_t seed, uint32_t max_steps, int mode,
+                      int32_t *burn_step, uint32_t result[6])
+{
+    return orc_simulate_impl(m, target, beta, ign_r, ign_c, seed, max_steps,
+                             mode, burn_step, result);
+}
+
+static int orc_simulate_impl(const orc_map *m, const uint8_t *target,
+                             const double beta[5], int ign_r, int ign_c,
+                             uint64_t seed, uint32_t max_steps, int mode,
+                             int32_t *burn_step, uint32_t result[6])
 {
     const int H = m->H, W = m->W;
     const long n = (long)H * W;
@@ -383,14 +430,25 @@ int orc_simulate(const orc_map *m, const uint8_t *target, const double beta[5],
                 long i = (long)r * W + c;
                 ignite[i] = 0;
                 if (state[i] != ORC_UNBURNT) continue;
+                unsigned dirmask = 0;
                 for (int d = 0; d < 8; ++d) {
                     int sr = r - ORC_DR[d], sc = c - ORC_DC[d];
                     if (sr < 0 || sr >= H || sc < 0 || sc >= W) continue;
                     if (state[(long)sr * W + sc] != ORC_BURNING) continue;
                     trials++;
+                    dirmask |= 1u << d;
+                    if (mode != 0) continue;
                     uint64_t T = orc_threshold_of_z(orc_z(m, beta, i, d));
                     uint32_t u = orc_draw(seed, (uint32_t)i, t, d);
                     if ((uint64_t)u < T) ignite[i] = 1;
+                }
+                if (mode != 0 && dirmask) {
+                    uint32_t ctr[4] = {(uint32_t)i, t, 2u, 0u};
+                    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+                    uint32_t w[4];
+                    orc_philox4x32_10(ctr, key, w);
+                    if ((uint64_t)w[0] < orc_cell_threshold(m, beta, i, dirmask))
+                        ignite[i] = 1;
                 }
             }
         }
@@ -426,8 +484,20 @@ int orc_simulate(const orc_map *m, const uint8_t *target, const double beta[5],
 
 /* Per-cell burn counts over many replicate seeds (seed0, seed0 + 1, ...),
  * for the Monte Carlo side of the exact-enumeration check.                */
+int orc_burn_frequency_mode(const orc_map *m, const double beta[5], int ign_r,
+                            int ign_c, uint64_t seed0, long nseeds, int mode,
+                            uint32_t *counts);
+
 int orc_burn_frequency(const orc_map *m, const double beta[5], int ign_r,
                        int ign_c, uint64_t seed0, long nseeds, uint32_t *counts)
+{
+    return orc_burn_frequency_mode(m, beta, ign_r, ign_c, seed0, nseeds, 0,
+                                   counts);
+}
+
+int orc_burn_frequency_mode(const orc_map *m, const double beta[5], int ign_r,
+                            int ign_c, uint64_t seed0, long nseeds, int mode,
+                            uint32_t *counts)
 {
     const long n = (long)m->H * m->W;
     int32_t *bs = (int32_t *)malloc((size_t)n * sizeof(int32_t));
@@ -435,8 +505,8 @@ int orc_burn_frequency(const orc_map *m, const double beta[5], int ign_r,
     memset(counts, 0, (size_t)n * sizeof(uint32_t));
     for (long s = 0; s < nseeds; ++s) {
         uint32_t res[6];
-        int rc = orc_simulate(m, NULL, beta, ign_r, ign_c, seed0 + (uint64_t)s,
-                              0, bs, res);
+        int rc = orc_simulate_impl(m, NULL, beta, ign_r, ign_c,
+                                   seed0 + (uint64_t)s, 0, mode, bs, res);
         if (rc) { free(bs); return rc; }
         for (long i = 0; i < n; ++i) counts[i] += bs[i] >= 0 ? 1u : 0u;
     }

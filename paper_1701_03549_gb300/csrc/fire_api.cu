@@ -497,6 +497,7 @@ int fire_simulate_batch(fire_ctx *ctx, const fire_map *m, int n,
     a.error_word = ctx->counter + 1;
     a.max_steps = max_steps;
     a.qcap = plan.qcap;
+    a.cell_uniform = (flags & FIRE_CELL_UNIFORM) ? 1 : 0;
     cudaError_t e = cudaMemsetAsync(ctx->counter, 0, 4, ctx->stream);
     if (e == cudaSuccess)
         e = launch_simulate(a, smem_state, plan.nwarps, (int)grid, plan.L.total,

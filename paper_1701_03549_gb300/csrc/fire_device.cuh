@@ -341,14 +341,20 @@ __device__ __forceinline__ float screen_p(float z)
     return r;
 }
 
+// Margin of the one-uniform-per-cell rule: 1 - prod(1 - p_d) over up to 8
+// directions accumulates at most 8 per-direction errors (each below 1e-6) and
+// 16 float roundings.
+constexpr float kCellScreenMargin = 2.5e-5f;
+
 // Decision of the trial with draw u.  Returns 1 success, 0 failure, -1 when
 // the screen cannot decide and the exact threshold is needed.
-__device__ __forceinline__ int screen_decide(float p32, uint32_t u)
+__device__ __forceinline__ int screen_decide(float p32, uint32_t u,
+                                             float margin = kScreenMargin)
 {
     const float v = __fmaf_rn(__uint2float_rn(u), 0x1p-32f, 0x1p-32f);
     const float d = __fsub_rn(p32, v);
-    if (d > kScreenMargin) return 1;
-    if (d < -kScreenMargin) return 0;
+    if (d > margin) return 1;
+    if (d < -margin) return 0;
     return -1;
 }
 

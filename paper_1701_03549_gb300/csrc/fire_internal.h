@@ -47,6 +47,7 @@ struct SimLaunch {
     uint32_t *error_word;      // set nonzero when a bounded wait runs out
     uint32_t max_steps;        // 0 = no cap
     int qcap;                  // candidate-queue capacity (entries)
+    int cell_uniform;          // 1: one uniform per target cell (Sec. 2.3)
 };
 
 // Cell-flag bits.

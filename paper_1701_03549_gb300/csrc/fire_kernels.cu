@@ -242,6 +242,25 @@ __device__ __forceinline__ bool test_dirs(uint32_t m4, int base, uint4 u4,
     return false;
 }
 
+// Exact decision of the one-uniform-per-cell rule: u < floor((1 - q) 2^32),
+// q = prod over the directions of dm (increasing d) of (1 - p_d).
+static __device__ __noinline__ int exact_cell_decide(const double *beta,
+                                                     bool forest, float4 f,
+                                                     uint32_t up, uint32_t dm,
+                                                     uint32_t u)
+{
+    double q = 1.0;
+    for (int d = 0; d < 8; ++d) {
+        if (!((dm >> d) & 1u)) continue;
+        const double z = spec::z_of(beta, forest, f.x, f.y, f.z, f.w,
+                                    (up >> d) & 1u, d);
+        const double p = !(z > -40.0) ? 0.0 : (z >= 40.0 ? 1.0 : spec::logistic(z));
+        q = __dmul_rn(q, __dsub_rn(1.0, p));
+    }
+    const double P = __dsub_rn(1.0, q);
+    return (uint64_t)u < (uint64_t)floor(__dmul_rn(P, 4294967296.0)) ? 1 : 0;
+}
+
 // All trials of one candidate cell (dm: directions with a burning source).
 __device__ __forceinline__ bool trial_cell(const SimCtx &s, uint32_t cell,
                                            uint32_t dm, uint32_t t)
@@ -256,6 +275,20 @@ __device__ __forceinline__ bool trial_cell(const SimCtx &s, uint32_t cell,
     const ScreenCell sc = screen_cell(sh.sp, forest, f.x, f.y, f.z, wd.x, f.w,
                                       wd.y);
     const ff b3 = sh.sp.b3;
+    if (s.a->cell_uniform) {
+        float q = 1.0f;
+        uint32_t mm = dm;
+        while (mm) {
+            const int d = __ffs(mm) - 1;
+            mm &= mm - 1;
+            const float p = screen_p(screen_z(sc, b3, (up >> d) & 1u, d));
+            q = __fmul_rn(q, __fsub_rn(1.0f, p));
+        }
+        const uint32_t u = philox4x32_10(cell, t, 2u, 0u, sh.key0, sh.key1).x;
+        int dec = screen_decide(__fsub_rn(1.0f, q), u, kCellScreenMargin);
+        if (dec < 0) dec = exact_cell_decide(sh.beta, forest, f, up, dm, u);
+        return dec != 0;
+    }
     bool ign = false;
     if (dm & 0x0fu) {
         const uint4 u = philox4x32_10(cell, t, 0u, 0u, sh.key0, sh.key1);

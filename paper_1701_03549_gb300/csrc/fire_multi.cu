@@ -191,6 +191,7 @@ int fire_simulate_multi(fire_ctx *ctx, int nmaps, const fire_map *const *maps,
     a.error_word = ctx->counter + 1;
     a.max_steps = max_steps;
     a.qcap = plan.qcap;
+    a.cell_uniform = (flags & FIRE_CELL_UNIFORM) ? 1 : 0;
 
     auto issue = [&]() -> int {
         CUDA_TRY(ctx, launch_order(n, dmap, nmaps, drank, dcounts, dorder, ctx->stream),

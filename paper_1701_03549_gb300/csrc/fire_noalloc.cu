@@ -146,6 +146,7 @@ extern "C" int fire_simulate_batch_noalloc(fire_ctx *ctx, const fire_map *m,
                                             kCounterBytes);
     a.max_steps = max_steps;
     a.qcap = plan.qcap;
+    a.cell_uniform = (flags & FIRE_CELL_UNIFORM) ? 1 : 0;
     e = cudaMemsetAsync(counters, 0, 2 * sizeof(uint32_t), ctx->stream);
     if (e == cudaSuccess)
         e = launch_simulate(a, smem_state, plan.nwarps, (int)grid, plan.L.total,

@@ -32,6 +32,7 @@ FIRE_DEVICE_PTRS = 1
 FIRE_WANT_STEPS = 2
 FIRE_SYNC = 4
 FIRE_GRAPH = 8
+FIRE_CELL_UNIFORM = 16
 
 STATUS_BORDER = 1
 STATUS_STEP_CAP = 2
@@ -247,7 +248,7 @@ class Map:
 
     def simulate_batch(self, params, ignitions, seeds, want_steps=False,
                        max_steps=0, device=False, out=None, burn_step=None,
-                       sync=False):
+                       sync=False, cell_uniform=False):
         """fire_simulate_batch.
 
         Host mode: params (n, 5) float64, ignitions (n, 2) int32 (row, col),
@@ -259,6 +260,7 @@ class Map:
         """
         lib = self.ctx.lib
         flags = FIRE_WANT_STEPS if want_steps else 0
+        flags |= FIRE_CELL_UNIFORM if cell_uniform else 0
         if device:
             n = int(params.shape[0])
             flags |= FIRE_DEVICE_PTRS | (FIRE_SYNC if sync else 0)
@@ -354,7 +356,7 @@ def _map_handles(maps):
 
 def fire_simulate_multi(ctx: Context, maps, map_of_sim, params, ignitions,
                         seeds, max_steps=0, device=False, out=None,
-                        graph=False, sync=False):
+                        graph=False, sync=False, cell_uniform=False):
     """Uneven batch over several maps (see fire_simulate_multi in fire.h).
 
     Host mode: numpy inputs, returns the structured results.  Device mode:
@@ -366,6 +368,7 @@ def fire_simulate_multi(ctx: Context, maps, map_of_sim, params, ignitions,
         n = int(params.shape[0])
         flags = FIRE_DEVICE_PTRS | (FIRE_GRAPH if graph else 0)
         flags |= FIRE_SYNC if sync else 0
+        flags |= FIRE_CELL_UNIFORM if cell_uniform else 0
         ctx.check(lib.fire_simulate_multi(
             ctx.h, len(maps), handles, _ptr(map_of_sim), n, _ptr(params),
             _ptr(ignitions), _ptr(seeds), int(max_steps), flags, _ptr(out)))
@@ -378,7 +381,7 @@ def fire_simulate_multi(ctx: Context, maps, map_of_sim, params, ignitions,
     res = np.zeros(n, RESULT_DTYPE)
     ctx.check(lib.fire_simulate_multi(
         ctx.h, len(maps), handles, _ptr(mi), n, _ptr(p), _ptr(g), _ptr(s),
-        int(max_steps), 0, _ptr(res)))
+        int(max_steps), FIRE_CELL_UNIFORM if cell_uniform else 0, _ptr(res)))
     return res
 
 

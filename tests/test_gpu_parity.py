@@ -302,3 +302,30 @@ def test_device_pointer_path_matches_host_path(ctx, orc):
     r = fire.results_view(out)
     assert r["status"][3] & fire.STATUS_BAD_IGNITION
     assert np.array_equal(np.delete(r, 3), np.delete(href, 3))
+
+
+@pytest.mark.parametrize("shape,seed", [((37, 61), 4), ((128, 128), 1),
+                                        ((3, 3), 3)])
+def test_cell_uniform_rule_matches_oracle(ctx, orc, shape, seed):
+    """The paper's one-uniform-per-cell update (FIRE_CELL_UNIFORM)."""
+    land = synth.landscape(*shape, seed=seed, wind_seed=seed)
+    rng = np.random.default_rng(seed + 50)
+    n = 24
+    params = np.concatenate([rng.normal(0, 3, (n - 3, 5)),
+                             [TRUTH, [1000.0, 0, 0, 0, 0],
+                              [-1000.0, 0, 0, 0, 0]]])
+    burnable = np.argwhere(land.veg != 0)
+    ign = burnable[rng.integers(0, len(burnable), n)].astype(np.int32)
+    seeds = rng.integers(1, 2 ** 63, n, dtype=np.uint64)
+    target = rng.random(shape) < 0.3
+    F = orc.Features(land)
+    m = ctx.landscape_upload(land)
+    m.target_upload(target)
+    res, bs = m.simulate_batch(params, ign, seeds, want_steps=True,
+                               cell_uniform=True)
+    for i in range(n):
+        o, obs = F.simulate(params[i], tuple(ign[i]), int(seeds[i]),
+                            target=target, mode=1)
+        assert np.array_equal(bs[i], obs), i
+        for k in ("burnt", "inter", "target", "steps", "status", "trials"):
+            assert int(res[k][i]) == o[k], (i, k)

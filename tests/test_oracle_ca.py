@@ -211,3 +211,39 @@ def test_target_map_counts(oracle_mod):
     res, bs = F.simulate([1.0, 0, 0, 0, 0], ign, seed=4, target=tgt)
     assert res["target"] == int(tgt.sum())
     assert res["inter"] == int(((bs >= 0) & tgt).sum())
+
+
+# --- the paper's one-uniform-per-cell update (Sec. 2.3), oracle mode 1 -----
+
+def test_cell_uniform_p_zero_and_p_one(oracle_mod):
+    L = synth.uniform_landscape(31, 29)
+    F = oracle_mod.Features(L)
+    res, bs = F.simulate([-1000.0, 0, 0, 0, 0], (10, 10), 3, mode=1)
+    assert res["burnt"] == 1 and res["steps"] == 1
+    res, bs = F.simulate([1000.0, 0, 0, 0, 0], (10, 10), 3, mode=1)
+    rr, cc = np.mgrid[0:31, 0:29]
+    assert np.array_equal(bs, np.maximum(abs(rr - 10), abs(cc - 10)))
+
+
+@pytest.mark.parametrize("shape,seed", [((2, 2), 7), ((3, 3), 8), ((2, 3), 9)])
+def test_cell_uniform_matches_the_per_neighbour_distribution(oracle_mod, shape,
+                                                             seed):
+    """One uniform against 1 - prod(1 - p_i) and one trial per neighbour give
+    the same ignition probability (up to threshold rounding, far below the
+    Monte Carlo error), so the per-neighbour exact enumeration pins the
+    cell-uniform rule too."""
+    H, W = shape
+    rng = np.random.default_rng(200 + seed)
+    L = synth.landscape(H, W, seed=seed, wind_deg=float(rng.uniform(0, 360)))
+    L.slope[:] = rng.uniform(0, 30, (H, W)).astype(np.float32)
+    L.elev[:] = rng.uniform(0, 100, (H, W)).astype(np.float32)
+    L.veg[:] = rng.integers(1, 3, (H, W)).astype(np.uint8)
+    F = oracle_mod.Features(L)
+    beta = rng.uniform(-2, 2, 5)
+    T = F.thresholds(beta)
+    ign = (0, 0)
+    p = exact_burn_probability(L.veg != 0, T, ign)
+    n = 60000
+    cnt = F.burn_frequency(beta, ign, 5000 + seed, n, mode=1)
+    ph = cnt / n
+    assert np.all(np.abs(ph - p) <= 5 * np.sqrt(p * (1 - p) / n) + 2.0 / n)
