@@ -113,6 +113,8 @@ enum {
                                 u < floor((1 - q) 2^32) with q the product of
                                 (1 - p_d) over the burning neighbours in
                                 increasing d, in double precision            */
+#define FIRE_TC_A_MN 32u      /* fire_tc_gemm: A stored MN-major (A[k][m])   */
+#define FIRE_TC_B_MN 64u      /* fire_tc_gemm: B stored MN-major (B[k][n])   */
 
 /* fire_result.status bits */
 #define FIRE_STATUS_BORDER 1u        /* a burnt cell lies on the grid edge   */
@@ -352,6 +354,24 @@ FIRE_API int fire_screen_selftest(fire_ctx *ctx, uint64_t n, uint64_t seed,
  * counter (c0 + i, c1, c2, c3) under key (k0, k1), for i < n. */
 FIRE_API int fire_philox_blocks(fire_ctx *ctx, uint64_t n, const uint32_t ctr[4],
                        const uint32_t key[2], uint32_t flags, uint32_t *out);
+
+/* Tensor-core GEMM (tcgen05, BF16 operands, FP32 accumulation in tensor
+ * memory): C[m][n] = sum_k A(m, k) B(n, k) for m < M, n < N, k < K.  The
+ * paper has no counterpart: this is the tile the surrogate network's
+ * convolutions run on, exported so that it can be checked on its own.
+ *   A, B   device BF16 (uint16 bit patterns), 16-byte aligned; A is A[m][k]
+ *          (K-major) or, with FIRE_TC_A_MN, A[k][m]; B is B[n][k] or, with
+ *          FIRE_TC_B_MN, B[k][n].
+ *   K      a multiple of 64; M a multiple of 8 with FIRE_TC_A_MN and N a
+ *          multiple of 8 with FIRE_TC_B_MN.
+ *   ksplit the K range is cut into ksplit parts run by separate CTAs and
+ *          summed with FP32 atomics (C is cleared first); 1 = plain store.
+ *   C      device FP32 [M][N], row-major, owned by the caller.
+ * FIRE_DEVICE_PTRS is required.  Returns FIRE_EINVAL on a shape, alignment
+ * or flag error; FIRE_ETIMEOUT (at the next fire_sync) if a bounded wait for
+ * the tensor core ran out. */
+FIRE_API int fire_tc_gemm(fire_ctx *ctx, int M, int N, int K, const uint16_t *A,
+                          const uint16_t *B, int ksplit, uint32_t flags, float *C);
 
 #ifdef __cplusplus
 }

@@ -33,6 +33,8 @@ FIRE_WANT_STEPS = 2
 FIRE_SYNC = 4
 FIRE_GRAPH = 8
 FIRE_CELL_UNIFORM = 16
+FIRE_TC_A_MN = 32
+FIRE_TC_B_MN = 64
 
 STATUS_BORDER = 1
 STATUS_STEP_CAP = 2
@@ -60,7 +62,7 @@ EXPORTED = (
     "fire_thresholds", "fire_probabilities", "fire_map_features",
     "fire_screen_selftest", "fire_philox_blocks",
     "fire_simulate_batch_noalloc", "fire_simulate_multi", "fire_autotune",
-    "ga_step", "fire_group_mean", "ignition_search",
+    "ga_step", "fire_group_mean", "ignition_search", "fire_tc_gemm",
 )
 
 
@@ -113,6 +115,7 @@ def load(path: str = LIB_PATH):
         "fire_group_mean": (i32, [vp, vp, i32, i32, u32, vp]),
         "ignition_search": (i32, [vp, vp, vp, i32, i32, i32, u64, i32,
                                   C.c_double, u32, vp, vp, vp]),
+        "fire_tc_gemm": (i32, [vp, i32, i32, i32, vp, vp, i32, u32, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -514,3 +517,15 @@ def results_view(out_tensor) -> np.ndarray:
     """Device results tensor (n, 6) int32 -> host structured array."""
     a = out_tensor.detach().cpu().numpy().astype(np.int32, copy=False)
     return a.view(np.uint32).reshape(-1, 6).copy().view(RESULT_DTYPE).reshape(-1)
+
+
+def fire_tc_gemm(ctx: Context, A, B, M: int, N: int, K: int, out,
+                 a_mn: bool = False, b_mn: bool = False, ksplit: int = 1,
+                 sync: bool = True):
+    """fire_tc_gemm on device tensors: A, B bfloat16 (A[M, K] or, a_mn,
+    A[K, M]; B[N, K] or, b_mn, B[K, N]); out float32 [M, N]."""
+    flags = FIRE_DEVICE_PTRS | (FIRE_SYNC if sync else 0)
+    flags |= (FIRE_TC_A_MN if a_mn else 0) | (FIRE_TC_B_MN if b_mn else 0)
+    ctx.check(ctx.lib.fire_tc_gemm(ctx.h, int(M), int(N), int(K), _ptr(A),
+                                   _ptr(B), int(ksplit), flags, _ptr(out)))
+    return out
