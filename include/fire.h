@@ -373,6 +373,123 @@ FIRE_API int fire_philox_blocks(fire_ctx *ctx, uint64_t n, const uint32_t ctr[4]
 FIRE_API int fire_tc_gemm(fire_ctx *ctx, int M, int N, int K, const uint16_t *A,
                           const uint16_t *B, int ksplit, uint32_t flags, float *C);
 
+/* ---------------------------------------------------------------------------
+ * Learned surrogate (no counterpart in the paper).  A BF16 convolutional
+ * network maps one parameter vector, the landscape and the ignition to a
+ * per-cell burn probability on an S x S coarse grid (each coarse cell the
+ * (H/S) x (W/S) block of fine cells); it is trained on burn fractions the
+ * automaton produces and ranks GA offspring before they are simulated.
+ *
+ * Input x[n][S][S][16] BF16 (NHWC): channels 0..4 the fraction of fine cells
+ * of vegetation class k (classes above 4 count as 4), 5 mean slope in
+ * degrees / 45, 6/7 mean sin/cos of the aspect, 8/9 mean sin/cos of the wind
+ * bearing, 10 one at the coarse cell of the ignition, 11..15 the parameters
+ * / 10.  Network: 3x3 conv 16 -> 128, seven 3x3 convs 128 -> 128 with
+ * dilations 1, 2, 4, ..., 64 (layer 1 has dilation 1), ReLU after each,
+ * zero padding, a 1x1 head 128 -> 1 and a sigmoid; loss = mean binary
+ * cross-entropy against the burn fraction.  Parameters are one FP32 vector
+ * (fire_net_param_count() = 1,051,777 floats): per layer W[o][t][i]
+ * (t = 3 t_y + t_x) then b[o], then the head's w[128] and b.  Convolutions
+ * run on tcgen05 tensor cores with BF16 operands and FP32 accumulation;
+ * activations and activation gradients are stored in BF16.
+ *
+ * Unless stated, array arguments are device pointers and FIRE_DEVICE_PTRS is
+ * required; calls are asynchronous on the context's stream (FIRE_SYNC
+ * blocks).  Errors: FIRE_EINVAL for shapes, NULLs, alignment or a missing
+ * flag; FIRE_ENOMEM; FIRE_ECUDA; FIRE_ETIMEOUT (at the next fire_sync) when
+ * a bounded tensor-core wait ran out.
+ * ------------------------------------------------------------------------- */
+#define FIRE_NET_CIN 16
+#define FIRE_NET_C 128
+#define FIRE_NET_LAYERS 8
+
+typedef struct fire_net fire_net;
+
+FIRE_API int64_t fire_net_param_count(void);
+
+/* A network for S x S inputs (S a power of two in [8, 1024]) and batches of
+ * up to max_batch samples (max_batch * S * S <= 2^24).  Allocates all
+ * parameter, optimiser and activation buffers up front (about
+ * 2 * 8 * max_batch * S * S * 256 bytes for activations and their
+ * gradients); parameters start at zero: call fire_net_set_params. */
+FIRE_API int fire_net_create(fire_ctx *ctx, int S, int max_batch, fire_net **out);
+FIRE_API void fire_net_free(fire_net *net);
+
+/* Load parameters (float[param_count], host, or device with
+ * FIRE_DEVICE_PTRS), reset Adam's moments and step count, refresh the BF16
+ * weight copies.  Blocks. */
+FIRE_API int fire_net_set_params(fire_ctx *ctx, fire_net *net, const float *params,
+                                 uint32_t flags);
+
+/* Copy out float[param_count]: which = 0 parameters, 1 the gradient of the
+ * last fire_net_backward, 2 / 3 Adam's first / second moments.  Host
+ * destination, or device with FIRE_DEVICE_PTRS.  Blocks. */
+FIRE_API int fire_net_get(fire_ctx *ctx, const fire_net *net, int which,
+                          uint32_t flags, float *out);
+
+/* Burn probabilities prob[n][S][S] (FP32) for inputs x[n][S][S][16] (BF16,
+ * 16-byte aligned); n may exceed max_batch (run in chunks). */
+FIRE_API int fire_net_forward(fire_ctx *ctx, fire_net *net, int n,
+                              const uint16_t *x, uint32_t flags, float *prob);
+
+/* Forward and backward over 1 <= n <= max_batch samples against labels
+ * target[n][S][S] (FP32 in [0, 1]); leaves the gradient of the mean BCE in
+ * the network (fire_net_get which = 1) and, when loss is not NULL, writes the
+ * loss to the device double *loss. */
+FIRE_API int fire_net_backward(fire_ctx *ctx, fire_net *net, int n,
+                               const uint16_t *x, const float *target,
+                               uint32_t flags, double *loss);
+
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected) with the
+ * gradient of the last fire_net_backward and learning rate lr. */
+FIRE_API int fire_net_adam(fire_ctx *ctx, fire_net *net, float lr, uint32_t flags);
+
+/* Debug copy of a buffer of the last call for its first n samples: which =
+ * 0 the BF16 activations of layer `layer` (0-based, [n][S][S][128]), 1 the
+ * BF16 gradient of that layer's pre-activation times its ReLU mask (same
+ * shape), 2 the FP32 probabilities [n][S][S] (layer ignored).  Blocks. */
+FIRE_API int fire_net_buffer(fire_ctx *ctx, const fire_net *net, int which,
+                             int layer, int n, uint32_t flags, void *out);
+
+/* Coarse map planes[S][S][10] (FP32, channels 0..9 of the input) from the
+ * fine rasters veg (uint8), slope, aspect, wind (FP32 degrees), each [H][W]
+ * row-major; H and W multiples of S. */
+FIRE_API int fire_net_planes(fire_ctx *ctx, int H, int W, int S, const uint8_t *veg,
+                             const float *slope, const float *aspect,
+                             const float *wind, uint32_t flags, float *planes);
+
+/* Network inputs x[n][S][S][16] (BF16) from planes, params[n] and fine-grid
+ * ignitions ign[n] of an H x W map. */
+FIRE_API int fire_net_inputs(fire_ctx *ctx, int S, int H, int W, int n,
+                             const float *planes, const fire_params *params,
+                             const fire_cell *ign, uint32_t flags, uint16_t *x);
+
+/* Training labels from the automaton: for each group g < groups, simulates
+ * reps fires with params[g] and ign[g] (simulation i = g reps + r draws with
+ * seed + i, exactly as fire_simulate_batch would), and writes
+ * labels[g][S][S] = the fraction of the coarse cell's fine cells burnt,
+ * averaged over the replicates.  results[groups * reps] (nullable) receives
+ * the fire_result of each simulation.  FIRE_CELL_UNIFORM is honoured. */
+FIRE_API int fire_net_labels(fire_ctx *ctx, const fire_map *map, int S, int groups,
+                             int reps, const fire_params *params,
+                             const fire_cell *ign, uint64_t seed,
+                             uint32_t max_steps, uint32_t flags, float *labels,
+                             fire_result *results);
+
+/* The target's burnt fraction per coarse cell, frac[S][S] (FP32). */
+FIRE_API int fire_net_target_frac(fire_ctx *ctx, const fire_map *map, int S,
+                                  uint32_t flags, float *frac);
+
+/* Screening: pred[s] = Eq. 2 (kind 0) or the Jaccard distance (kind 1)
+ * computed with expected set sizes from prob[s] (E|A*| = c sum q, |A| =
+ * c sum t, E|AnA*| = c sum q t, c = cells_per_coarse), and keep_idx[r] = the
+ * candidate of rank r < keep by increasing pred (NaN last, ties to the lower
+ * index). */
+FIRE_API int fire_net_screen(fire_ctx *ctx, int S, int n, const float *prob,
+                             const float *target_frac, double cells_per_coarse,
+                             int kind, int keep, uint32_t flags, double *pred,
+                             int32_t *keep_idx);
+
 #ifdef __cplusplus
 }
 #endif

@@ -391,6 +391,62 @@ int fire_target_upload(fire_ctx *ctx, fire_map *m, const uint8_t *burnt,
     return FIRE_OK;
 }
 
+}  // extern "C"
+
+namespace fire {
+
+// Launch the simulation kernel over n simulations of one map whose arguments
+// already sit on the device (the common tail of fire_simulate_batch, also
+// used by the surrogate's label builder for the burnt-word output).
+int launch_batch(fire_ctx *ctx, const fire_map *m, int n,
+                 const fire_params *dparams, const fire_cell *dign,
+                 const uint64_t *dseeds, uint32_t max_steps, uint32_t flags,
+                 fire_result *dout, int32_t *dsteps, uint32_t *dbits)
+{
+    const int ntiles = m->dev.ntiles;
+    LaunchPlan plan;
+    int rc = plan_launch(ctx, ntiles, n, &plan);
+    if (rc) return rc;
+    const bool smem_state = plan.smem_state;
+    const long long grid = plan.grid;
+    if (!smem_state) {
+        const size_t need = (size_t)grid * 2 * ntiles * 128;
+        rc = grow_device(ctx, (void **)&ctx->gstate, &ctx->gstate_bytes, need,
+                         "simulation state");
+        if (rc) return rc;
+    }
+    SimLaunch a;
+    a.map = m->dev;
+    a.maps = nullptr;
+    a.nmaps = 1;
+    a.map_of_sim = nullptr;
+    a.order = nullptr;
+    a.ntiles_max = ntiles;
+    a.n = n;
+    a.params = dparams;
+    a.ign = dign;
+    a.seeds = dseeds;
+    a.out = dout;
+    a.burn_step = dsteps;
+    a.burnt_bits = dbits;
+    a.work_counter = ctx->counter;
+    a.gstate = ctx->gstate;
+    a.error_word = ctx->counter + 1;
+    a.max_steps = max_steps;
+    a.qcap = plan.qcap;
+    a.cell_uniform = (flags & FIRE_CELL_UNIFORM) ? 1 : 0;
+    cudaError_t e = cudaMemsetAsync(ctx->counter, 0, 4, ctx->stream);
+    if (e == cudaSuccess)
+        e = launch_simulate(a, smem_state, plan.nwarps, (int)grid, plan.L.total,
+                            ctx->stream);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "simulate launch");
+    return FIRE_OK;
+}
+
+}  // namespace fire
+
+extern "C" {
+
 int fire_simulate_batch(fire_ctx *ctx, const fire_map *m, int n,
                         const fire_params *params, const fire_cell *ignitions,
                         const uint64_t *seeds, uint32_t max_steps,
@@ -423,13 +479,6 @@ int fire_simulate_batch(fire_ctx *ctx, const fire_map *m, int n,
                                "non-burnable", i, g.row, g.col);
         }
     }
-
-    const int ntiles = m->dev.ntiles;
-    LaunchPlan plan;
-    rc = plan_launch(ctx, ntiles, n, &plan);
-    if (rc) return rc;
-    const bool smem_state = plan.smem_state;
-    const long long grid = plan.grid;
 
     // staging of host arguments
     const fire_params *dparams = params;
@@ -472,43 +521,15 @@ int fire_simulate_batch(fire_ctx *ctx, const fire_map *m, int n,
             dsteps = (int32_t *)steps_tmp;
         }
     }
-    if (!smem_state) {
-        const size_t need = (size_t)grid * 2 * ntiles * 128;
-        rc = grow_device(ctx, (void **)&ctx->gstate, &ctx->gstate_bytes, need,
-                         "simulation state");
-        if (rc) { if (steps_tmp) cudaFree(steps_tmp); return rc; }
-    }
-
-    SimLaunch a;
-    a.map = m->dev;
-    a.maps = nullptr;
-    a.nmaps = 1;
-    a.map_of_sim = nullptr;
-    a.order = nullptr;
-    a.ntiles_max = ntiles;
-    a.n = n;
-    a.params = dparams;
-    a.ign = dign;
-    a.seeds = dseeds;
-    a.out = dout;
-    a.burn_step = dsteps;
-    a.work_counter = ctx->counter;
-    a.gstate = ctx->gstate;
-    a.error_word = ctx->counter + 1;
-    a.max_steps = max_steps;
-    a.qcap = plan.qcap;
-    a.cell_uniform = (flags & FIRE_CELL_UNIFORM) ? 1 : 0;
-    cudaError_t e = cudaMemsetAsync(ctx->counter, 0, 4, ctx->stream);
-    if (e == cudaSuccess)
-        e = launch_simulate(a, smem_state, plan.nwarps, (int)grid, plan.L.total,
-                            ctx->stream);
-    if (e != cudaSuccess) {
+    rc = launch_batch(ctx, m, n, dparams, dign, dseeds, max_steps, flags, dout,
+                      dsteps, nullptr);
+    if (rc) {
         if (steps_tmp) cudaFree(steps_tmp);
-        return cuda_err(ctx, e, "simulate launch");
+        return rc;
     }
     if (!dev) {
-        e = cudaMemcpyAsync(out, dout, (size_t)n * sizeof(fire_result),
-                            cudaMemcpyDeviceToHost, ctx->stream);
+        cudaError_t e = cudaMemcpyAsync(out, dout, (size_t)n * sizeof(fire_result),
+                                        cudaMemcpyDeviceToHost, ctx->stream);
         if (e == cudaSuccess && want_steps)
             e = cudaMemcpyAsync(burn_step, dsteps,
                                 (size_t)n * H * W * sizeof(int32_t),

@@ -1,0 +1,437 @@
+// TMA-fed implicit-GEMM convolution for the surrogate's 128 -> 128 layers
+// (forward and input gradient), on tcgen05 tensor cores.
+//
+// A CTA computes a 128-pixel x 128-channel tile.  The K loop runs over the
+// 9 taps x 2 halves of 64 input channels; for each 64-wide slab
+//   * one thread issues two TMA loads: the activation tile, shifted by the
+//     tap's offset, through a 4-D tensor map over the NHWC buffer (channels,
+//     x, y, sample) whose out-of-range elements read as zero (the zero
+//     padding of the convolution), and the 128 x 64 weight slab through a 2-D
+//     map; both land 128-byte swizzled, which is the canonical K-major
+//     SWIZZLE_128B operand layout of the tensor core;
+//   * another thread waits for the slab, issues four 128 x 128 x 16 MMAs into
+//     the tensor-memory accumulator and commits them to the slab's "empty"
+//     barrier, which hands the stage back to the loader.
+// Three stages (96 KB) let two CTAs share an SM, so one CTA's epilogue
+// (tensor memory -> registers -> bias/ReLU or ReLU mask -> BF16 stores)
+// overlaps the other's main loop.  Every wait is bounded; on a timeout the
+// CTA records an error, waits (bounded) for its own copies in flight, frees
+// its tensor memory and returns.
+#include "fire_internal.h"
+#include "fire_tc.cuh"
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+
+#include <mutex>
+
+namespace fire {
+namespace convtma {
+
+constexpr int kStages = 3;
+constexpr int kTileBytes = 128 * 128;           // 128 rows x 64 BF16
+constexpr int kStageBytes = 2 * kTileBytes;     // A + B
+constexpr int kSmem = kStages * kStageBytes + 1024;
+constexpr int kSlabs = 18;                      // 9 taps x 2 channel halves
+
+struct Epi {
+    int mode;                 // 0 forward (bias + ReLU), 1 input gradient (mask)
+    const float *bias;        // forward
+    const uint16_t *hprev;    // input gradient: activations of the layer below
+    uint16_t *out;            // [P][128] BF16
+};
+
+__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr)
+{
+    uint64_t d = (uint64_t)((saddr & 0x3ffffu) >> 4);
+    d |= (uint64_t)1 << 16;                 // LBO (unused for swizzled K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;       // SBO: 8 rows x 128 B
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;                 // SWIZZLE_128B
+    return d;
+}
+
+__device__ __forceinline__ void expect_tx(void *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(
+                     tc::smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tma_4d(uint32_t dst, const CUtensorMap *map, int c0,
+                                       int c1, int c2, int c3, void *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::"
+        "bytes [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3),
+        "r"(tc::smem_addr(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_2d(uint32_t dst, const CUtensorMap *map, int c0,
+                                       int c1, void *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::"
+        "bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1),
+        "r"(tc::smem_addr(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ uint32_t pack2(float a, float b)
+{
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<const uint32_t *>(&h);
+}
+
+__device__ __forceinline__ bool pos16(uint32_t u)
+{
+    return !(u & 0x8000u) && (u & 0x7fffu);
+}
+
+// sign = +1: forward (source pixel p + off(t)); -1: input gradient (p - off(t)).
+__global__ void __launch_bounds__(128, 2)
+    k_conv_tma(const __grid_constant__ CUtensorMap act,
+               const __grid_constant__ CUtensorMap wts, Epi epi, int S, int lgS,
+               int d, int sign, uint32_t *err)
+{
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    __shared__ __align__(8) unsigned long long full[kStages], empty[kStages], done;
+    __shared__ uint32_t tmem_slot;
+    __shared__ int s_fail, s_issued, s_consumed;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t base = (tc::smem_addr(smem_raw) + 1023u) & ~1023u;
+    const int m0 = blockIdx.x * 128;
+    const int b = m0 >> (2 * lgS);
+    const int y0 = (m0 >> lgS) & (S - 1), x0 = m0 & (S - 1);
+
+    if (warp == 0) {
+        tc::tmem_alloc(&tmem_slot, 128);
+        tc::tmem_relinquish();
+    }
+    if (tid == 0) {
+        for (int i = 0; i < kStages; ++i) {
+            tc::mbar_init(&full[i], 1);
+            tc::mbar_init(&empty[i], 1);
+        }
+        tc::mbar_init(&done, 1);
+        s_fail = 0;
+        s_issued = 0;
+        s_consumed = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = tmem_slot;
+
+    if (warp == 0 && lane == 0) {
+        // loader
+        int s = 0;
+        for (; s < kSlabs; ++s) {
+            const int st = s % kStages;
+            if (s >= kStages &&
+                !tc::mbar_wait_bounded(&empty[st], ((s / kStages) - 1) & 1)) {
+                atomicOr(&s_fail, 1);
+                break;
+            }
+            if (*(volatile int *)&s_fail) break;
+            const int tap = s >> 1, c0 = (s & 1) * 64;
+            const int dy = sign * (tap / 3 - 1) * d, dx = sign * (tap % 3 - 1) * d;
+            const uint32_t sa = base + st * kStageBytes;
+            expect_tx(&full[st], kStageBytes);
+            tma_4d(sa, &act, c0, x0 + dx, y0 + dy, b, &full[st]);
+            tma_2d(sa + kTileBytes, &wts, s * 64, 0, &full[st]);
+        }
+        s_issued = s;
+    } else if (warp == 1 && lane == 0) {
+        // MMA issuer
+        constexpr uint32_t idesc = tc::idesc_bf16(128, 128);
+        int s = 0;
+        for (; s < kSlabs; ++s) {
+            const int st = s % kStages;
+            if (!tc::mbar_wait_bounded(&full[st], (s / kStages) & 1)) {
+                atomicOr(&s_fail, 1);
+                break;
+            }
+            tc::fence_after_sync();
+            const uint32_t sa = base + st * kStageBytes, sb = sa + kTileBytes;
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk)
+                tc::mma_bf16(tmem, desc_sw128(sa + kk * 32), desc_sw128(sb + kk * 32),
+                             idesc, s > 0 || kk > 0);
+            tc::mma_commit(&empty[st]);
+        }
+        s_consumed = s;
+        if (s == kSlabs) tc::mma_commit(&done);
+    }
+    __syncwarp();
+    if (!tc::mbar_wait_bounded(&done, 0)) atomicOr(&s_fail, 1);
+    __syncthreads();
+    tc::fence_after_sync();
+
+    if (!s_fail) {
+        const int p = m0 + warp * 32 + lane;
+        uint16_t *orow = epi.out + (size_t)p * 128;
+#pragma unroll 1
+        for (int c0 = 0; c0 < 128; c0 += 16) {
+            float v[16];
+            tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+            uint32_t pk[8];
+            if (epi.mode == 0) {
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    pk[j] = pack2(fmaxf(v[2 * j] + epi.bias[c0 + 2 * j], 0.0f),
+                                  fmaxf(v[2 * j + 1] + epi.bias[c0 + 2 * j + 1], 0.0f));
+            } else {
+                const uint4 *hp =
+                    reinterpret_cast<const uint4 *>(epi.hprev + (size_t)p * 128 + c0);
+                const uint4 h0 = hp[0], h1 = hp[1];
+                const uint32_t hw[8] = {h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w};
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    pk[j] = pack2(pos16(hw[j] & 0xffffu) ? v[2 * j] : 0.0f,
+                                  pos16(hw[j] >> 16) ? v[2 * j + 1] : 0.0f);
+            }
+            uint4 *o = reinterpret_cast<uint4 *>(orow + c0);
+            o[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+            o[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+        }
+    } else if (tid == 0) {
+        atomicOr(err, 1u);
+        // copies issued but never consumed must land before the CTA leaves
+        for (int s = s_consumed; s < s_issued; ++s)
+            tc::mbar_wait_bounded(&full[s % kStages], (s / kStages) & 1);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, 128);
+}
+
+// Weight gradient of a 128 -> 128 layer: D[o][(t, i)] = sum_p dz[p, o]
+// in[p + off(t), i].  CTA (tap t = blockIdx.y, pixel range blockIdx.z) runs
+// 64-pixel slabs; both operands are MN-major (8 consecutive channels per 16
+// bytes, pixels along K).  Each slab is two 64-channel TMA boxes per operand,
+// which land as the MN-major SWIZZLE_128B layout: channel halves 8 KB apart
+// (LBO), 8-pixel groups 1 KB apart (SBO).  Partial sums are added to dW with
+// FP32 atomics.
+__device__ __forceinline__ uint64_t desc_sw128_mn(uint32_t saddr)
+{
+    uint64_t d = (uint64_t)((saddr & 0x3ffffu) >> 4);
+    d |= (uint64_t)(8192 >> 4) << 16;       // LBO: next 64 MN elements
+    d |= (uint64_t)(1024 >> 4) << 32;       // SBO: next 8 K rows
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;                 // SWIZZLE_128B
+    return d;
+}
+
+__global__ void __launch_bounds__(128, 2)
+    k_wgrad_tma(const __grid_constant__ CUtensorMap dzm,
+                const __grid_constant__ CUtensorMap inm, float *dw, int S, int lgS,
+                int d, int slabs_total, int slabs_per, uint32_t *err)
+{
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    __shared__ __align__(8) unsigned long long full[kStages], empty[kStages], done;
+    __shared__ uint32_t tmem_slot;
+    __shared__ int s_fail, s_issued, s_consumed;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t base = (tc::smem_addr(smem_raw) + 1023u) & ~1023u;
+    const int tap = blockIdx.y;
+    const int dy = (tap / 3 - 1) * d, dx = (tap % 3 - 1) * d;
+    const int s0 = blockIdx.z * slabs_per;
+    const int ns = min(slabs_total - s0, slabs_per);
+
+    if (warp == 0) {
+        tc::tmem_alloc(&tmem_slot, 128);
+        tc::tmem_relinquish();
+    }
+    if (tid == 0) {
+        for (int i = 0; i < kStages; ++i) {
+            tc::mbar_init(&full[i], 1);
+            tc::mbar_init(&empty[i], 1);
+        }
+        tc::mbar_init(&done, 1);
+        s_fail = 0;
+        s_issued = 0;
+        s_consumed = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = tmem_slot;
+
+    if (ns > 0 && warp == 0 && lane == 0) {
+        int s = 0;
+        for (; s < ns; ++s) {
+            const int st = s % kStages;
+            if (s >= kStages &&
+                !tc::mbar_wait_bounded(&empty[st], ((s / kStages) - 1) & 1)) {
+                atomicOr(&s_fail, 1);
+                break;
+            }
+            if (*(volatile int *)&s_fail) break;
+            const int p0 = (s0 + s) * 64;
+            const int b = p0 >> (2 * lgS);
+            const int y = (p0 >> lgS) & (S - 1), x = p0 & (S - 1);
+            const uint32_t sa = base + st * kStageBytes, sb = sa + kTileBytes;
+            expect_tx(&full[st], kStageBytes);
+            tma_4d(sa, &dzm, 0, x, y, b, &full[st]);
+            tma_4d(sa + 8192, &dzm, 64, x, y, b, &full[st]);
+            tma_4d(sb, &inm, 0, x + dx, y + dy, b, &full[st]);
+            tma_4d(sb + 8192, &inm, 64, x + dx, y + dy, b, &full[st]);
+        }
+        s_issued = s;
+    } else if (ns > 0 && warp == 1 && lane == 0) {
+        constexpr uint32_t idesc =
+            tc::idesc_bf16(128, 128) | (1u << 15) | (1u << 16);   // both MN-major
+        int s = 0;
+        for (; s < ns; ++s) {
+            const int st = s % kStages;
+            if (!tc::mbar_wait_bounded(&full[st], (s / kStages) & 1)) {
+                atomicOr(&s_fail, 1);
+                break;
+            }
+            tc::fence_after_sync();
+            const uint32_t sa = base + st * kStageBytes, sb = sa + kTileBytes;
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk)
+                tc::mma_bf16(tmem, desc_sw128_mn(sa + kk * 2048),
+                             desc_sw128_mn(sb + kk * 2048), idesc, s > 0 || kk > 0);
+            tc::mma_commit(&empty[st]);
+        }
+        s_consumed = s;
+        if (s == ns) tc::mma_commit(&done);
+    }
+    __syncwarp();
+    if (ns > 0 && !tc::mbar_wait_bounded(&done, 0)) atomicOr(&s_fail, 1);
+    __syncthreads();
+    tc::fence_after_sync();
+
+    if (ns > 0 && !s_fail) {
+        const int o = warp * 32 + lane;
+        float *row = dw + (size_t)o * 1152 + tap * 128;
+#pragma unroll 1
+        for (int c0 = 0; c0 < 128; c0 += 16) {
+            float v[16];
+            tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) atomicAdd(row + c0 + j, v[j]);
+        }
+    } else if (s_fail && tid == 0) {
+        atomicOr(err, 1u);
+        for (int s = s_consumed; s < s_issued; ++s)
+            tc::mbar_wait_bounded(&full[s % kStages], (s / kStages) & 1);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, 128);
+}
+
+// --- host: tensor maps ------------------------------------------------------
+
+PFN_cuTensorMapEncodeTiled_v12000 encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        cudaDriverEntryPointQueryResult q;
+        void *p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                             cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+// NHWC activations [n][S][S][128] BF16; box 64 channels x `pix` pixels
+// (a run of one row, or whole rows when S < pix).
+bool map_act(CUtensorMap *m, const uint16_t *ptr, int n, int S, int pix = 128)
+{
+    auto fn = encoder();
+    if (!fn) return false;
+    const cuuint64_t dims[4] = {128, (cuuint64_t)S, (cuuint64_t)S, (cuuint64_t)n};
+    const cuuint64_t strides[3] = {256, (cuuint64_t)S * 256, (cuuint64_t)S * S * 256};
+    const cuuint32_t bx = S >= pix ? pix : S, by = pix / bx;
+    const cuuint32_t box[4] = {64, bx, by, 1};
+    const cuuint32_t es[4] = {1, 1, 1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<uint16_t *>(ptr), dims,
+              strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Weights [128 rows][1152] BF16; box 64 x 128.
+bool map_wts(CUtensorMap *m, const uint16_t *ptr)
+{
+    auto fn = encoder();
+    if (!fn) return false;
+    const cuuint64_t dims[2] = {1152, 128};
+    const cuuint64_t strides[1] = {1152 * 2};
+    const cuuint32_t box[2] = {64, 128};
+    const cuuint32_t es[2] = {1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<uint16_t *>(ptr), dims,
+              strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace convtma
+
+// Forward (mode 0: out = ReLU(conv(in) + bias)) or input gradient (mode 1:
+// out = conv^T(in) masked by hprev > 0) of a 128 -> 128 layer over n samples
+// of S x S (S a power of two >= 16).  `w` is W[o][t][i] (forward) or
+// Wt[i][t][o] (input gradient), 16-byte aligned.
+cudaError_t launch_conv_tma(int mode, const uint16_t *in, const uint16_t *w,
+                            const float *bias, const uint16_t *hprev, uint16_t *out,
+                            int n, int S, int lgS, int d, uint32_t *err,
+                            cudaStream_t st)
+{
+    using namespace convtma;
+    if (S < 16 || (S & (S - 1)) || ((uintptr_t)in & 15) || ((uintptr_t)w & 15))
+        return cudaErrorInvalidValue;
+    CUtensorMap ma, mw;
+    if (!map_act(&ma, in, n, S) || !map_wts(&mw, w)) return cudaErrorInvalidValue;
+    cudaError_t attr = cudaFuncSetAttribute(
+        k_conv_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+    if (attr != cudaSuccess) return attr;
+    Epi e{mode, bias, hprev, out};
+    const long long P = (long long)n * S * S;
+    k_conv_tma<<<(unsigned)(P / 128), 128, kSmem, st>>>(ma, mw, e, S, lgS, d,
+                                                         mode == 0 ? 1 : -1, err);
+    return cudaGetLastError();
+}
+
+// Weight gradient of a 128 -> 128 layer, added into dw[128][1152] (FP32,
+// cleared by the caller): dz and in are [n][S][S][128] BF16, S a power of two
+// >= 16; the pixel range is split `split` ways.
+cudaError_t launch_wgrad_tma(const uint16_t *dz, const uint16_t *in, float *dw, int n,
+                             int S, int lgS, int d, int split, uint32_t *err,
+                             cudaStream_t st)
+{
+    using namespace convtma;
+    if (S < 16 || (S & (S - 1)) || ((uintptr_t)dz & 15) || ((uintptr_t)in & 15) ||
+        split < 1)
+        return cudaErrorInvalidValue;
+    CUtensorMap mz, mi;
+    if (!map_act(&mz, dz, n, S, 64) || !map_act(&mi, in, n, S, 64))
+        return cudaErrorInvalidValue;
+    cudaError_t attr = cudaFuncSetAttribute(
+        k_wgrad_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+    if (attr != cudaSuccess) return attr;
+    const int total = (int)((long long)n * S * S / 64);
+    if (split > total) split = total;
+    const int per = (total + split - 1) / split;
+    dim3 grid(1, 9, (total + per - 1) / per);
+    k_wgrad_tma<<<grid, 128, kSmem, st>>>(mz, mi, dw, S, lgS, d, total, per, err);
+    return cudaGetLastError();
+}
+
+}  // namespace fire

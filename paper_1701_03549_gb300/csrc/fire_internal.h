@@ -42,6 +42,9 @@ struct SimLaunch {
     const uint64_t *seeds;
     fire_result *out;
     int32_t *burn_step;        // nullable
+    uint32_t *burnt_bits;      // nullable; single-map launches only: the final
+                               // burnt words (tile-major, blocked cells
+                               // cleared), ntiles * 32 words per simulation
     uint32_t *work_counter;    // zeroed before launch
     uint32_t *gstate;          // global-state variant: 2 * ntiles * 32 words per block
     uint32_t *error_word;      // set nonzero when a bounded wait runs out
@@ -210,6 +213,17 @@ int grow_device(fire_ctx *ctx, void **buf, size_t *cap, size_t need,
 size_t round16(size_t x);
 bool valid_map(const fire_map *m);
 int plan_launch(fire_ctx *ctx, int ntiles, long long n, LaunchPlan *p);
+cudaError_t launch_conv_tma(int mode, const uint16_t *in, const uint16_t *w,
+                            const float *bias, const uint16_t *hprev, uint16_t *out,
+                            int n, int S, int lgS, int d, uint32_t *err,
+                            cudaStream_t st);
+cudaError_t launch_wgrad_tma(const uint16_t *dz, const uint16_t *in, float *dw, int n,
+                             int S, int lgS, int d, int split, uint32_t *err,
+                             cudaStream_t st);
+int launch_batch(fire_ctx *ctx, const fire_map *m, int n,
+                 const fire_params *dparams, const fire_cell *dign,
+                 const uint64_t *dseeds, uint32_t max_steps, uint32_t flags,
+                 fire_result *dout, int32_t *dsteps, uint32_t *dbits);
 }  // namespace fire
 
 #define CUDA_TRY(ctx, expr, what)                                   \

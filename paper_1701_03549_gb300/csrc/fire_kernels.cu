@@ -699,6 +699,8 @@ __global__ void __launch_bounds__(kSimMaxThreads, 2) k_simulate(SimLaunch a)
         bool border = false;
         for (int w = threadIdx.x; w < m.ntiles * 32; w += blockDim.x) {
             const uint32_t bw = (s.X[w] | s.Y[w]) & ~__ldg(&m.blk[w]);
+            if (a.burnt_bits)
+                a.burnt_bits[(long long)sim * m.ntiles * 32 + w] = bw;
             if (!bw) continue;
             nb += __popc(bw);
             ni += __popc(bw & __ldg(&m.tgt[w]));

@@ -186,6 +186,7 @@ int fire_simulate_multi(fire_ctx *ctx, int nmaps, const fire_map *const *maps,
     a.seeds = dseeds;
     a.out = dout;
     a.burn_step = nullptr;
+    a.burnt_bits = nullptr;
     a.work_counter = ctx->counter;
     a.gstate = ctx->gstate;
     a.error_word = ctx->counter + 1;

@@ -140,6 +140,7 @@ extern "C" int fire_simulate_batch_noalloc(fire_ctx *ctx, const fire_map *m,
     a.seeds = seeds;
     a.out = out;
     a.burn_step = want_steps ? burn_step : nullptr;
+    a.burnt_bits = nullptr;
     a.work_counter = counters;
     a.error_word = counters + 1;
     a.gstate = reinterpret_cast<uint32_t *>(static_cast<char *>(scratch) +

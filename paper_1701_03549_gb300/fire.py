@@ -63,6 +63,11 @@ EXPORTED = (
     "fire_screen_selftest", "fire_philox_blocks",
     "fire_simulate_batch_noalloc", "fire_simulate_multi", "fire_autotune",
     "ga_step", "fire_group_mean", "ignition_search", "fire_tc_gemm",
+    "fire_net_param_count", "fire_net_create", "fire_net_free",
+    "fire_net_set_params", "fire_net_get", "fire_net_forward",
+    "fire_net_backward", "fire_net_adam", "fire_net_buffer",
+    "fire_net_planes", "fire_net_inputs", "fire_net_labels",
+    "fire_net_target_frac", "fire_net_screen",
 )
 
 
@@ -116,6 +121,24 @@ def load(path: str = LIB_PATH):
         "ignition_search": (i32, [vp, vp, vp, i32, i32, i32, u64, i32,
                                   C.c_double, u32, vp, vp, vp]),
         "fire_tc_gemm": (i32, [vp, i32, i32, i32, vp, vp, i32, u32, vp]),
+        "fire_net_param_count": (C.c_int64, []),
+        "fire_net_create": (i32, [vp, i32, i32, C.POINTER(vp)]),
+        "fire_net_free": (None, [vp]),
+        "fire_net_set_params": (i32, [vp, vp, vp, u32]),
+        "fire_net_get": (i32, [vp, vp, i32, u32, vp]),
+        "fire_net_forward": (i32, [vp, vp, i32, vp, u32, vp]),
+        "fire_net_backward": (i32, [vp, vp, i32, vp, vp, u32, vp]),
+        "fire_net_adam": (i32, [vp, vp, C.c_float, u32]),
+        "fire_net_buffer": (i32, [vp, vp, i32, i32, i32, u32, vp]),
+        "fire_net_planes": (i32, [vp, i32, i32, i32, vp, vp, vp, vp, u32,
+                                  vp]),
+        "fire_net_inputs": (i32, [vp, i32, i32, i32, i32, vp, vp, vp, u32,
+                                  vp]),
+        "fire_net_labels": (i32, [vp, vp, i32, i32, i32, vp, vp, u64, u32,
+                                  u32, vp, vp]),
+        "fire_net_target_frac": (i32, [vp, vp, i32, u32, vp]),
+        "fire_net_screen": (i32, [vp, i32, i32, vp, vp, C.c_double, i32,
+                                  i32, u32, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -529,3 +552,129 @@ def fire_tc_gemm(ctx: Context, A, B, M: int, N: int, K: int, out,
     ctx.check(ctx.lib.fire_tc_gemm(ctx.h, int(M), int(N), int(K), _ptr(A),
                                    _ptr(B), int(ksplit), flags, _ptr(out)))
     return out
+
+
+# ---------------------------------------------------------------------------
+# learned surrogate (fire_net_*); device tensors throughout
+
+NET_CIN = 16
+NET_C = 128
+NET_LAYERS = 8
+NET_PARAMS, NET_GRAD, NET_ADAM_M, NET_ADAM_V = 0, 1, 2, 3
+BUF_ACT, BUF_DZ, BUF_PROB = 0, 1, 2
+
+
+def fire_net_param_count() -> int:
+    return int(load().fire_net_param_count())
+
+
+class Net:
+    """fire_net: the surrogate network of one context (S x S inputs,
+    batches of up to max_batch samples)."""
+
+    def __init__(self, ctx: Context, S: int, max_batch: int):
+        self.ctx, self.S, self.max_batch = ctx, int(S), int(max_batch)
+        h = C.c_void_p()
+        ctx.check(ctx.lib.fire_net_create(ctx.h, self.S, self.max_batch,
+                                          C.byref(h)))
+        self.h = h
+        self.P = fire_net_param_count()
+
+    def free(self):
+        if self.h:
+            self.ctx.lib.fire_net_free(self.h)
+            self.h = None
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def set_params(self, theta):
+        """theta: float32 numpy array or CUDA tensor of param_count."""
+        if _is_tensor(theta):
+            self.ctx.check(self.ctx.lib.fire_net_set_params(
+                self.ctx.h, self.h, _ptr(theta), FIRE_DEVICE_PTRS))
+        else:
+            t = _host(theta, np.float32).ravel()
+            assert t.size == self.P
+            self.ctx.check(self.ctx.lib.fire_net_set_params(
+                self.ctx.h, self.h, _ptr(t), 0))
+
+    def get(self, which=NET_PARAMS) -> np.ndarray:
+        out = np.zeros(self.P, np.float32)
+        self.ctx.check(self.ctx.lib.fire_net_get(self.ctx.h, self.h,
+                                                 int(which), 0, _ptr(out)))
+        return out
+
+    def forward(self, x, prob, sync=False):
+        n = int(x.shape[0])
+        self.ctx.check(self.ctx.lib.fire_net_forward(
+            self.ctx.h, self.h, n, _ptr(x),
+            FIRE_DEVICE_PTRS | (FIRE_SYNC if sync else 0), _ptr(prob)))
+        return prob
+
+    def backward(self, x, target, loss=None, sync=False):
+        n = int(x.shape[0])
+        self.ctx.check(self.ctx.lib.fire_net_backward(
+            self.ctx.h, self.h, n, _ptr(x), _ptr(target),
+            FIRE_DEVICE_PTRS | (FIRE_SYNC if sync else 0), _ptr(loss)))
+        return loss
+
+    def adam(self, lr: float, sync=False):
+        self.ctx.check(self.ctx.lib.fire_net_adam(
+            self.ctx.h, self.h, float(lr), FIRE_SYNC if sync else 0))
+
+    def buffer(self, which, layer, n, out):
+        self.ctx.check(self.ctx.lib.fire_net_buffer(
+            self.ctx.h, self.h, int(which), int(layer), int(n),
+            FIRE_DEVICE_PTRS, _ptr(out)))
+        return out
+
+
+def fire_net_planes(ctx: Context, S: int, veg, slope, aspect, wind, out,
+                    sync=False):
+    H, W = veg.shape
+    ctx.check(ctx.lib.fire_net_planes(
+        ctx.h, int(H), int(W), int(S), _ptr(veg), _ptr(slope), _ptr(aspect),
+        _ptr(wind), FIRE_DEVICE_PTRS | (FIRE_SYNC if sync else 0), _ptr(out)))
+    return out
+
+
+def fire_net_inputs(ctx: Context, S: int, H: int, W: int, planes, params,
+                    ign, out, sync=False):
+    n = int(params.shape[0])
+    ctx.check(ctx.lib.fire_net_inputs(
+        ctx.h, int(S), int(H), int(W), n, _ptr(planes), _ptr(params),
+        _ptr(ign), FIRE_DEVICE_PTRS | (FIRE_SYNC if sync else 0), _ptr(out)))
+    return out
+
+
+def fire_net_labels(ctx: Context, m: Map, S: int, params, ign, reps: int,
+                    seed: int, labels, results=None, max_steps=0,
+                    cell_uniform=False, sync=False):
+    groups = int(params.shape[0])
+    flags = FIRE_DEVICE_PTRS | (FIRE_SYNC if sync else 0)
+    flags |= FIRE_CELL_UNIFORM if cell_uniform else 0
+    ctx.check(ctx.lib.fire_net_labels(
+        ctx.h, m.h, int(S), groups, int(reps), _ptr(params), _ptr(ign),
+        int(seed), int(max_steps), flags, _ptr(labels), _ptr(results)))
+    return labels
+
+
+def fire_net_target_frac(ctx: Context, m: Map, S: int, out, sync=False):
+    ctx.check(ctx.lib.fire_net_target_frac(
+        ctx.h, m.h, int(S), FIRE_DEVICE_PTRS | (FIRE_SYNC if sync else 0),
+        _ptr(out)))
+    return out
+
+
+def fire_net_screen(ctx: Context, S: int, prob, target_frac, cells: float,
+                    kind: int, keep: int, pred, keep_idx=None, sync=False):
+    n = int(prob.shape[0])
+    ctx.check(ctx.lib.fire_net_screen(
+        ctx.h, int(S), n, _ptr(prob), _ptr(target_frac), float(cells),
+        int(kind), int(keep), FIRE_DEVICE_PTRS | (FIRE_SYNC if sync else 0),
+        _ptr(pred), _ptr(keep_idx)))
+    return pred, keep_idx
