@@ -89,6 +89,16 @@ def lib():
                                         C.c_void_p, C.c_int, C.c_int,
                                         C.c_uint64, C.c_uint32, C.c_int,
                                         C.c_void_p, C.c_void_p]
+        L.orc_simulate_burnout.restype = C.c_int
+        L.orc_simulate_burnout.argtypes = [C.POINTER(_Map), C.c_void_p,
+                                           C.c_void_p, C.c_int, C.c_int,
+                                           C.c_uint64, C.c_uint32, C.c_void_p,
+                                           C.c_void_p, C.c_void_p]
+        L.orc_burn_frequency_burnout.restype = C.c_int
+        L.orc_burn_frequency_burnout.argtypes = [C.POINTER(_Map), C.c_void_p,
+                                                 C.c_int, C.c_int, C.c_uint64,
+                                                 C.c_long, C.c_void_p,
+                                                 C.c_void_p]
         L.orc_burn_frequency_mode.restype = C.c_int
         L.orc_burn_frequency_mode.argtypes = [C.POINTER(_Map), C.c_void_p,
                                               C.c_int, C.c_int, C.c_uint64,
@@ -235,20 +245,35 @@ class Features:
         return T
 
     def simulate(self, beta, ignition, seed: int, target=None,
-                 want_steps: bool = True, max_steps: int = 0, mode: int = 0):
+                 want_steps: bool = True, max_steps: int = 0, mode: int = 0,
+                 burn_time=None):
         """Run one fire; returns (result dict, burn-step map or None).
         mode 0: one trial per burning neighbour; mode 1: one uniform per
-        cell against 1 - prod(1 - p_i) (see fire_oracle.c)."""
+        cell against 1 - prod(1 - p_i) (see fire_oracle.c).  burn_time
+        (uint8 (H, W), mode 0 only): steps each cell burns once ignited."""
         b = np.ascontiguousarray(beta, np.float64)
         res = np.zeros(6, np.uint32)
         bs = np.zeros((self.H, self.W), np.int32) if want_steps else None
         tg = None if target is None else np.ascontiguousarray(target,
                                                               np.uint8)
-        rc = lib().orc_simulate_mode(C.byref(self._m),
-                                     None if tg is None else _p(tg), _p(b),
-                                     int(ignition[0]), int(ignition[1]),
-                                     int(seed), int(max_steps), int(mode),
-                                     None if bs is None else _p(bs), _p(res))
+        if burn_time is not None:
+            if mode != 0:
+                raise ValueError("burn times apply to the per-neighbour rule")
+            bt = np.ascontiguousarray(burn_time, np.uint8).reshape(self.H,
+                                                                   self.W)
+            rc = lib().orc_simulate_burnout(
+                C.byref(self._m), None if tg is None else _p(tg), _p(b),
+                int(ignition[0]), int(ignition[1]), int(seed), int(max_steps),
+                _p(bt), None if bs is None else _p(bs), _p(res))
+            if rc == -1:
+                raise ValueError("burn time 0 on a burnable cell")
+        else:
+            rc = lib().orc_simulate_mode(C.byref(self._m),
+                                         None if tg is None else _p(tg), _p(b),
+                                         int(ignition[0]), int(ignition[1]),
+                                         int(seed), int(max_steps), int(mode),
+                                         None if bs is None else _p(bs),
+                                         _p(res))
         if rc == -4:
             raise ValueError("ignition outside the grid or non-burnable")
         if rc:
@@ -276,13 +301,21 @@ class Features:
         return fm, cells, xy
 
     def burn_frequency(self, beta, ignition, seed0: int, nseeds: int,
-                       mode: int = 0):
+                       mode: int = 0, burn_time=None):
         b = np.ascontiguousarray(beta, np.float64)
         counts = np.zeros((self.H, self.W), np.uint32)
-        rc = lib().orc_burn_frequency_mode(C.byref(self._m), _p(b),
-                                           int(ignition[0]), int(ignition[1]),
-                                           int(seed0), int(nseeds), int(mode),
-                                           _p(counts))
+        if burn_time is not None:
+            bt = np.ascontiguousarray(burn_time, np.uint8).reshape(self.H,
+                                                                   self.W)
+            rc = lib().orc_burn_frequency_burnout(
+                C.byref(self._m), _p(b), int(ignition[0]), int(ignition[1]),
+                int(seed0), int(nseeds), _p(bt), _p(counts))
+        else:
+            rc = lib().orc_burn_frequency_mode(C.byref(self._m), _p(b),
+                                               int(ignition[0]),
+                                               int(ignition[1]), int(seed0),
+                                               int(nseeds), int(mode),
+                                               _p(counts))
         if rc:
             raise RuntimeError(f"oracle burn_frequency failed ({rc})")
         return counts

@@ -368,17 +368,26 @@ uint64_t orc_cell_threshold(const orc_map *m, const double beta[5], long i,
     return (uint64_t)floor(P * 4294967296.0);
 }
 
+/* Burn-out times.  The paper burns every fuel out one step after it
+ * ignites (Sec. 2.1) and names fitting fuel-consumption times as future
+ * work.  With burn_time (uint8 per cell, >= 1 on burnable cells) a cell
+ * ignited at step t stays burning during steps t+1 .. t+burn_time, trying
+ * its unburnt neighbours at each of them with the same per-trial draws
+ * (counter (cell, step, d/4, 0)); NULL means one step everywhere, the
+ * paper's rule.  steps = the number of update steps run while some cell
+ * was burning. */
 static int orc_simulate_impl(const orc_map *m, const uint8_t *target,
                              const double beta[5], int ign_r, int ign_c,
                              uint64_t seed, uint32_t max_steps, int mode,
-                             int32_t *burn_step, uint32_t result[6]);
+                             const uint8_t *burn_time, int32_t *burn_step,
+                             uint32_t result[6]);
 
 int orc_simulate(const orc_map *m, const uint8_t *target, const double beta[5],
                  int ign_r, int ign_c, uint64_t seed, uint32_t max_steps,
                  int32_t *burn_step, uint32_t result[6])
 {
     return orc_simulate_impl(m, target, beta, ign_r, ign_c, seed, max_steps, 0,
-                             burn_step, result);
+                             NULL, burn_step, result);
 }
 
 int orc_simulate_mode(const orc_map *m, const uint8_t *target,
@@ -387,13 +396,24 @@ int orc_simulate_mode(const orc_map *m, const uint8_t *target,
                       int32_t *burn_step, uint32_t result[6])
 {
     return orc_simulate_impl(m, target, beta, ign_r, ign_c, seed, max_steps,
-                             mode, burn_step, result);
+                             mode, NULL, burn_step, result);
+}
+
+int orc_simulate_burnout(const orc_map *m, const uint8_t *target,
+                         const double beta[5], int ign_r, int ign_c,
+                         uint64_t seed, uint32_t max_steps,
+                         const uint8_t *burn_time, int32_t *burn_step,
+                         uint32_t result[6])
+{
+    return orc_simulate_impl(m, target, beta, ign_r, ign_c, seed, max_steps, 0,
+                             burn_time, burn_step, result);
 }
 
 static int orc_simulate_impl(const orc_map *m, const uint8_t *target,
                              const double beta[5], int ign_r, int ign_c,
                              uint64_t seed, uint32_t max_steps, int mode,
-                             int32_t *burn_step, uint32_t result[6])
+                             const uint8_t *burn_time, int32_t *burn_step,
+                             uint32_t result[6])
 {
     const int H = m->H, W = m->W;
     const long n = (long)H * W;
@@ -404,15 +424,26 @@ static int orc_simulate_impl(const orc_map *m, const uint8_t *target,
     if (ign_r < 0 || ign_r >= H || ign_c < 0 || ign_c >= W) return -4;
     if (!m->burnable[(long)ign_r * W + ign_c]) return -4;
 
+    if (n <= 0) return -1;
+    if (burn_time) {
+        for (long i = 0; i < n; ++i)
+            if (m->burnable[i] && burn_time[i] == 0) return -1;
+    }
     uint8_t *state = (uint8_t *)malloc((size_t)n);
     uint8_t *ignite = (uint8_t *)malloc((size_t)n);
-    if (!state || !ignite) { free(state); free(ignite); return -2; }
+    uint8_t *left = (uint8_t *)malloc((size_t)n);   /* burning steps left */
+    if (!state || !ignite || !left) {
+        free(state); free(ignite); free(left);
+        return -2;
+    }
     for (long i = 0; i < n; ++i) {
         state[i] = m->burnable[i] ? ORC_UNBURNT : ORC_BLOCKED;
+        left[i] = 0;
         if (burn_step) burn_step[i] = m->burnable[i] ? -1 : -2;
     }
     long ign = (long)ign_r * W + ign_c;
     state[ign] = ORC_BURNING;
+    left[ign] = burn_time ? burn_time[ign] : 1;
     if (burn_step) burn_step[ign] = 0;
 
     uint32_t burnt = 1, inter = (target && target[ign]) ? 1u : 0u;
@@ -452,16 +483,21 @@ static int orc_simulate_impl(const orc_map *m, const uint8_t *target,
                 }
             }
         }
-        /* burning cells burn out; newly ignited cells start burning */
+        /* burning cells spend one step of fuel and burn out when none is
+           left; newly ignited cells start burning */
         any_burning = 0;
         for (long i = 0; i < n; ++i) {
-            if (state[i] == ORC_BURNING) state[i] = ORC_BURNT;
+            if (state[i] != ORC_BURNING) continue;
+            left[i]--;
+            if (left[i] == 0) state[i] = ORC_BURNT;
+            else any_burning = 1;
         }
         for (int r = 0; r < H; ++r) {
             for (int c = 0; c < W; ++c) {
                 long i = (long)r * W + c;
                 if (!ignite[i]) continue;
                 state[i] = ORC_BURNING;
+                left[i] = burn_time ? burn_time[i] : 1;
                 any_burning = 1;
                 burnt++;
                 if (target && target[i]) inter++;
@@ -479,6 +515,7 @@ static int orc_simulate_impl(const orc_map *m, const uint8_t *target,
     result[5] = trials;
     free(state);
     free(ignite);
+    free(left);
     return 0;
 }
 
@@ -495,9 +532,32 @@ int orc_burn_frequency(const orc_map *m, const double beta[5], int ign_r,
                                    counts);
 }
 
+static int orc_burn_frequency_impl(const orc_map *m, const double beta[5],
+                                   int ign_r, int ign_c, uint64_t seed0,
+                                   long nseeds, int mode,
+                                   const uint8_t *burn_time, uint32_t *counts);
+
 int orc_burn_frequency_mode(const orc_map *m, const double beta[5], int ign_r,
                             int ign_c, uint64_t seed0, long nseeds, int mode,
                             uint32_t *counts)
+{
+    return orc_burn_frequency_impl(m, beta, ign_r, ign_c, seed0, nseeds, mode,
+                                   NULL, counts);
+}
+
+int orc_burn_frequency_burnout(const orc_map *m, const double beta[5],
+                               int ign_r, int ign_c, uint64_t seed0,
+                               long nseeds, const uint8_t *burn_time,
+                               uint32_t *counts)
+{
+    return orc_burn_frequency_impl(m, beta, ign_r, ign_c, seed0, nseeds, 0,
+                                   burn_time, counts);
+}
+
+static int orc_burn_frequency_impl(const orc_map *m, const double beta[5],
+                                   int ign_r, int ign_c, uint64_t seed0,
+                                   long nseeds, int mode,
+                                   const uint8_t *burn_time, uint32_t *counts)
 {
     const long n = (long)m->H * m->W;
     int32_t *bs = (int32_t *)malloc((size_t)n * sizeof(int32_t));
@@ -506,7 +566,8 @@ int orc_burn_frequency_mode(const orc_map *m, const double beta[5], int ign_r,
     for (long s = 0; s < nseeds; ++s) {
         uint32_t res[6];
         int rc = orc_simulate_impl(m, NULL, beta, ign_r, ign_c,
-                                   seed0 + (uint64_t)s, 0, mode, bs, res);
+                                   seed0 + (uint64_t)s, 0, mode, burn_time, bs,
+                                   res);
         if (rc) { free(bs); return rc; }
         for (long i = 0; i < n; ++i) counts[i] += bs[i] >= 0 ? 1u : 0u;
     }
