@@ -355,6 +355,29 @@ FIRE_API int fire_screen_selftest(fire_ctx *ctx, uint64_t n, uint64_t seed,
 FIRE_API int fire_philox_blocks(fire_ctx *ctx, uint64_t n, const uint32_t ctr[4],
                        const uint32_t key[2], uint32_t flags, uint32_t *out);
 
+/* Burn-out times (the paper burns every fuel out one step after ignition,
+ * Sec. 2.1, and leaves fuel-consumption times to future work): as
+ * fire_simulate_batch with the per-neighbour rule, except that a cell ignited
+ * at step t stays burning for burn_time[cell] steps (t+1 .. t+burn_time) and
+ * tries its unburnt neighbours at each of them with the same keyed draws
+ * (counter (cell, step, d/4, 0)); burn_time = 1 everywhere gives exactly the
+ * fires of fire_simulate_batch.  steps = the number of update steps run
+ * while some cell was burning.
+ *   burn_time  uint8[H*W] row-major, 1..250 on burnable cells (host values
+ *              are checked; device values outside are clamped); per-fuel
+ *              times are a table lookup by vegetation class on the caller's
+ *              side.
+ * Other arguments, layouts and errors as fire_simulate_batch;
+ * FIRE_CELL_UNIFORM and FIRE_GRAPH are rejected (FIRE_EINVAL).  Runs a
+ * simpler kernel than fire_simulate_batch (a byte of state per cell, dense
+ * sweeps of the burning box). */
+FIRE_API int fire_simulate_burnout(fire_ctx *ctx, const fire_map *map, int n,
+                                   const fire_params *params,
+                                   const fire_cell *ignitions,
+                                   const uint64_t *seeds, const uint8_t *burn_time,
+                                   uint32_t max_steps, uint32_t flags,
+                                   fire_result *out, int32_t *burn_step);
+
 /* Tensor-core GEMM (tcgen05, BF16 operands, FP32 accumulation in tensor
  * memory): C[m][n] = sum_k A(m, k) B(n, k) for m < M, n < N, k < K.  The
  * paper has no counterpart: this is the tile the surrogate network's

@@ -1,0 +1,128 @@
+// C ABI of the burn-out-time variant (fire_simulate_burnout, include/fire.h):
+// argument checks, staging of host arguments and the launch of k_burnout.
+#include <cmath>
+
+#include "fire_internal.h"
+
+using namespace fire;
+
+extern "C" int fire_simulate_burnout(fire_ctx *ctx, const fire_map *m, int n,
+                                     const fire_params *params,
+                                     const fire_cell *ignitions,
+                                     const uint64_t *seeds,
+                                     const uint8_t *burn_time, uint32_t max_steps,
+                                     uint32_t flags, fire_result *out,
+                                     int32_t *burn_step)
+{
+    if (!ctx) return FIRE_EINVAL;
+    if (!valid_map(m)) return set_err(ctx, FIRE_EINVAL, "invalid map");
+    if (n < 0) return set_err(ctx, FIRE_EINVAL, "n = %d", n);
+    if (n == 0) return FIRE_OK;
+    if (!params || !ignitions || !seeds || !out || !burn_time)
+        return set_err(ctx, FIRE_EINVAL, "NULL argument");
+    const bool want_steps = (flags & FIRE_WANT_STEPS) != 0;
+    if (want_steps && !burn_step)
+        return set_err(ctx, FIRE_EINVAL, "FIRE_WANT_STEPS without burn_step");
+    if (flags & (FIRE_CELL_UNIFORM | FIRE_GRAPH))
+        return set_err(ctx, FIRE_EINVAL,
+                       "burn times take the per-neighbour rule, without graphs");
+    int rc = ensure_device(ctx);
+    if (rc) return rc;
+    const bool dev = flags & FIRE_DEVICE_PTRS;
+    const int H = m->dev.H, W = m->dev.W;
+    const size_t HW = (size_t)H * W;
+    if (!dev) {
+        for (int i = 0; i < n; ++i) {
+            for (int j = 0; j < 5; ++j)
+                if (!std::isfinite(params[i].b[j]))
+                    return set_err(ctx, FIRE_EINVAL,
+                                   "params[%d].b[%d] is not finite", i, j);
+            const fire_cell g = ignitions[i];
+            if (g.row < 0 || g.row >= H || g.col < 0 || g.col >= W ||
+                !m->burnable_host[(size_t)g.row * W + g.col])
+                return set_err(ctx, FIRE_EIGNITION,
+                               "ignition %d (%d, %d) is outside the grid or "
+                               "non-burnable", i, g.row, g.col);
+        }
+        for (size_t i = 0; i < HW; ++i)
+            if (m->burnable_host[i] && (burn_time[i] < 1 || burn_time[i] > 250))
+                return set_err(ctx, FIRE_EINVAL,
+                               "burn_time[%zu] = %d outside 1..250", i,
+                               (int)burn_time[i]);
+    }
+    // host arguments go through one temporary device buffer
+    void *tmp = nullptr;
+    const fire_params *dp = params;
+    const fire_cell *di = ignitions;
+    const uint64_t *ds = seeds;
+    const uint8_t *db = burn_time;
+    fire_result *dout = out;
+    int32_t *dsteps = want_steps ? burn_step : nullptr;
+    if (!dev) {
+        const size_t bp = round16((size_t)n * sizeof(fire_params));
+        const size_t bi = round16((size_t)n * sizeof(fire_cell));
+        const size_t bs = round16((size_t)n * 8);
+        const size_t bb = round16(HW);
+        const size_t bo = round16((size_t)n * sizeof(fire_result));
+        const size_t bst = want_steps ? (size_t)n * HW * 4 : 0;
+        cudaError_t e = cudaMalloc(&tmp, bp + bi + bs + bb + bo + bst);
+        if (e != cudaSuccess)
+            return set_err(ctx, FIRE_ENOMEM, "burn-out staging");
+        char *p = (char *)tmp;
+        cudaStream_t st = ctx->stream;
+        e = cudaMemcpyAsync(p, params, (size_t)n * sizeof(fire_params),
+                            cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(p + bp, ignitions, (size_t)n * sizeof(fire_cell),
+                                cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(p + bp + bi, seeds, (size_t)n * 8,
+                                cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(p + bp + bi + bs, burn_time, HW,
+                                cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) {
+            cudaFree(tmp);
+            return cuda_err(ctx, e, "burn-out staging copy");
+        }
+        dp = (const fire_params *)p;
+        di = (const fire_cell *)(p + bp);
+        ds = (const uint64_t *)(p + bp + bi);
+        db = (const uint8_t *)(p + bp + bi + bs);
+        dout = (fire_result *)(p + bp + bi + bs + bb);
+        if (want_steps) dsteps = (int32_t *)(p + bp + bi + bs + bb + bo);
+    }
+    const int grid = (int)std::min<long long>((long long)n, (long long)ctx->num_sms * 4);
+    rc = grow_device(ctx, (void **)&ctx->gstate, &ctx->gstate_bytes,
+                     (size_t)grid * HW, "burn-out state");
+    if (rc) {
+        if (tmp) cudaFree(tmp);
+        return rc;
+    }
+    BurnLaunch a;
+    a.map = m->dev;
+    a.n = n;
+    a.params = dp;
+    a.ign = di;
+    a.seeds = ds;
+    a.burn_time = db;
+    a.out = dout;
+    a.burn_step = dsteps;
+    a.state = (uint8_t *)ctx->gstate;
+    a.work_counter = ctx->counter;
+    a.max_steps = max_steps;
+    cudaError_t e = cudaMemsetAsync(ctx->counter, 0, 4, ctx->stream);
+    if (e == cudaSuccess) e = launch_burnout(a, grid, ctx->stream);
+    if (e == cudaSuccess && !dev) {
+        e = cudaMemcpyAsync(out, dout, (size_t)n * sizeof(fire_result),
+                            cudaMemcpyDeviceToHost, ctx->stream);
+        if (e == cudaSuccess && want_steps)
+            e = cudaMemcpyAsync(burn_step, dsteps, (size_t)n * HW * 4,
+                                cudaMemcpyDeviceToHost, ctx->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    }
+    if (tmp) cudaFree(tmp);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "burn-out launch");
+    if (!dev || (flags & FIRE_SYNC)) return fire_sync(ctx);
+    return FIRE_OK;
+}

@@ -53,6 +53,21 @@ struct SimLaunch {
     int cell_uniform;          // 1: one uniform per target cell (Sec. 2.3)
 };
 
+// Launch of the burn-out-time variant (per-cell burn times, byte state).
+struct BurnLaunch {
+    MapDev map;
+    int n;
+    const fire_params *params;
+    const fire_cell *ign;
+    const uint64_t *seeds;
+    const uint8_t *burn_time;  // per cell; >= 1 on burnable cells
+    fire_result *out;
+    int32_t *burn_step;        // nullable
+    uint8_t *state;            // H * W bytes per block
+    uint32_t *work_counter;    // zeroed before launch
+    uint32_t max_steps;        // 0 = no cap
+};
+
 // Cell-flag bits.
 constexpr uint16_t kFlagForest = 1u << 8;
 constexpr uint16_t kFlagBurnable = 1u << 9;
@@ -118,6 +133,7 @@ cudaError_t launch_simulate(const SimLaunch &a, bool smem_state, int nwarps,
 // Threads per block the simulation kernel is compiled for (upper bound).
 constexpr int kSimMaxThreads = 512;
 const void *simulate_kernel_ptr(bool smem_state);
+cudaError_t launch_burnout(const BurnLaunch &a, int grid, cudaStream_t st);
 cudaError_t launch_fitness(const fire_result *r, int n, int kind, double *out,
                            cudaStream_t st);
 // Counting sort of simulations by rank[map_of_sim[i]] (counts: nmaps + 1).

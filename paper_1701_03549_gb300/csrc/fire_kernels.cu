@@ -734,6 +734,224 @@ __global__ void __launch_bounds__(kSimMaxThreads, 2) k_simulate(SimLaunch a)
 }
 
 // ---------------------------------------------------------------------------
+// Burn-out times (the paper burns every fuel out one step after it ignites,
+// Sec. 2.1, and names fuel-consumption times as future work).  A cell ignited
+// at step t stays burning for burn_time[cell] steps and tries its unburnt
+// neighbours at each of them, with the trial draws and decisions of
+// k_simulate (counter (cell, step, d/4, 0), screened FP32 with the exact FP64
+// fallback), so burn_time = 1 everywhere reproduces k_simulate's fires.
+//
+// A plainer design than k_simulate: one block per simulation at a time, one
+// byte of state per cell in a per-block global buffer (0 unburnt, 1..250
+// steps of fuel left, 253 igniting in this step, 254 burnt, 255
+// non-burnable), and per step two sweeps over the box of burning cells grown
+// by one cell: (1) trials for every unburnt cell with a burning neighbour,
+// (2) burning cells spend a step of fuel and the step's new cells start
+// burning.
+__device__ __forceinline__ bool burnout_decide(const MapDev &m,
+                                               const ScreenParams &sp,
+                                               const double *beta, uint32_t key0,
+                                               uint32_t key1, uint32_t cell,
+                                               uint32_t dm, uint32_t t)
+{
+    const float4 f = __ldg(&m.feat[cell]);
+    const float2 wd = __ldg(&m.wdiag[cell]);
+    const uint32_t fl = __ldg(&m.cfl[cell]);
+    const bool forest = (fl & kFlagForest) != 0;
+    const uint32_t up = fl & 0xffu;
+    const ScreenCell sc = screen_cell(sp, forest, f.x, f.y, f.z, wd.x, f.w, wd.y);
+    bool ign = false;
+    if (dm & 0x0fu) {
+        const uint4 u = philox4x32_10(cell, t, 0u, 0u, key0, key1);
+        ign = test_dirs(dm & 0x0fu, 0, u, sc, sp.b3, up, beta, forest, f);
+    }
+    if (!ign && (dm & 0xf0u)) {
+        const uint4 u = philox4x32_10(cell, t, 1u, 0u, key0, key1);
+        ign = test_dirs(dm >> 4, 4, u, sc, sp.b3, up, beta, forest, f);
+    }
+    return ign;
+}
+
+__device__ __forceinline__ uint32_t target_bit(const MapDev &m, int r, int c)
+{
+    const uint32_t w = __ldg(&m.tgt[((r >> 5) * m.TW + (c >> 5)) * 32 + (r & 31)]);
+    return (w >> (c & 31)) & 1u;
+}
+
+constexpr uint8_t kBoUnburnt = 0, kBoMaxFuel = 250, kBoIgnite = 253,
+                  kBoBurnt = 254, kBoBlocked = 255;
+
+__global__ void __launch_bounds__(256) k_burnout(BurnLaunch a)
+{
+    __shared__ double beta[5];
+    __shared__ ScreenParams sp;
+    __shared__ uint32_t key0, key1;
+    __shared__ int sim, skip, r0, r1, c0, c1, nr0, nr1, nc0, nc1;
+    __shared__ unsigned nburn, burnt, inter, trials, status;
+    const MapDev &m = a.map;
+    const int H = m.H, W = m.W;
+    const long long HW = (long long)H * W;
+    uint8_t *st = a.state + (size_t)blockIdx.x * HW;
+    const unsigned long long hard_cap = (unsigned long long)(HW + 2) * 256ull;
+
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const uint32_t w = atomicAdd(a.work_counter, 1u);
+            sim = w < (uint32_t)a.n ? (int)w : a.n;
+        }
+        __syncthreads();
+        const int s = sim;
+        if (s >= a.n) break;
+        if (threadIdx.x == 0) {
+            const fire_params P = a.params[s];
+            for (int j = 0; j < 5; ++j) beta[j] = P.b[j];
+            sp = screen_params(P.b);
+            const uint64_t seed = a.seeds[s];
+            key0 = (uint32_t)seed;
+            key1 = (uint32_t)(seed >> 32);
+            const fire_cell g = a.ign[s];
+            const bool ok = g.row >= 0 && g.row < H && g.col >= 0 && g.col < W &&
+                            (m.cfl[(long long)g.row * W + g.col] & kFlagBurnable);
+            skip = ok ? 0 : 1;
+            status = ok ? 0u : FIRE_STATUS_BAD_IGNITION;
+            burnt = inter = trials = 0;
+            r0 = r1 = g.row;
+            c0 = c1 = g.col;
+        }
+        for (long long i = threadIdx.x; i < HW; i += blockDim.x) {
+            const bool b = (__ldg(&m.cfl[i]) & kFlagBurnable) != 0;
+            st[i] = b ? kBoUnburnt : kBoBlocked;
+            if (a.burn_step) a.burn_step[(long long)s * HW + i] = b ? -1 : -2;
+        }
+        __syncthreads();
+        uint32_t t = 0;
+        bool capped = false;
+        if (!skip) {
+            if (threadIdx.x == 0) {
+                const long long gi = (long long)r0 * W + c0;
+                const uint8_t b = __ldg(&a.burn_time[gi]);
+                st[gi] = b < 1 ? 1 : (b > kBoMaxFuel ? kBoMaxFuel : b);
+                burnt = 1;
+                inter = target_bit(m, r0, c0);
+                if (r0 == 0 || r0 == H - 1 || c0 == 0 || c0 == W - 1)
+                    status |= FIRE_STATUS_BORDER;
+                if (a.burn_step) a.burn_step[(long long)s * HW + gi] = 0;
+            }
+            __syncthreads();
+            for (;;) {
+                if (a.max_steps && t >= a.max_steps) {
+                    capped = true;
+                    break;
+                }
+                if (t > hard_cap) {
+                    if (threadIdx.x == 0) status |= FIRE_STATUS_TIMEOUT;
+                    break;
+                }
+                const int R0 = max(r0 - 1, 0), R1 = min(r1 + 1, H - 1);
+                const int C0 = max(c0 - 1, 0), C1 = min(c1 + 1, W - 1);
+                const int rw = C1 - C0 + 1;
+                const long long cnt = (long long)(R1 - R0 + 1) * rw;
+                // (1) trials
+                unsigned my_trials = 0;
+                for (long long q = threadIdx.x; q < cnt; q += blockDim.x) {
+                    const int r = R0 + (int)(q / rw), c = C0 + (int)(q % rw);
+                    const long long i = (long long)r * W + c;
+                    if (st[i] != kBoUnburnt) continue;
+                    uint32_t dm = 0;
+                    for (int d = 0; d < 8; ++d) {
+                        const int sr = r - kDR[d], sc = c - kDC[d];
+                        if (sr < 0 || sr >= H || sc < 0 || sc >= W) continue;
+                        const uint8_t v = st[(long long)sr * W + sc];
+                        if (v >= 1 && v <= kBoMaxFuel) dm |= 1u << d;
+                    }
+                    if (!dm) continue;
+                    my_trials += __popc(dm);
+                    if (burnout_decide(m, sp, beta, key0, key1, (uint32_t)i, dm, t))
+                        st[i] = kBoIgnite;
+                }
+                my_trials = __reduce_add_sync(kFull, my_trials);
+                if ((threadIdx.x & 31) == 0 && my_trials) atomicAdd(&trials, my_trials);
+                if (threadIdx.x == 0) {
+                    nr0 = nc0 = 0x7fffffff;
+                    nr1 = nc1 = -1;
+                    nburn = 0;
+                }
+                __syncthreads();
+                // (2) fuel and new cells
+                int lr0 = 0x7fffffff, lr1 = -1, lc0 = 0x7fffffff, lc1 = -1;
+                unsigned lb = 0, lnew = 0, lint = 0, lst = 0;
+                for (long long q = threadIdx.x; q < cnt; q += blockDim.x) {
+                    const int r = R0 + (int)(q / rw), c = C0 + (int)(q % rw);
+                    const long long i = (long long)r * W + c;
+                    uint8_t v = st[i];
+                    if (v >= 1 && v <= kBoMaxFuel) {
+                        v = v - 1;
+                        st[i] = v == 0 ? kBoBurnt : v;
+                        if (v == 0) continue;
+                    } else if (v == kBoIgnite) {
+                        const uint8_t b = __ldg(&a.burn_time[i]);
+                        st[i] = b < 1 ? 1 : (b > kBoMaxFuel ? kBoMaxFuel : b);
+                        lnew++;
+                        lint += target_bit(m, r, c);
+                        if (r == 0 || r == H - 1 || c == 0 || c == W - 1)
+                            lst |= FIRE_STATUS_BORDER;
+                        if (a.burn_step)
+                            a.burn_step[(long long)s * HW + i] = (int32_t)(t + 1);
+                    } else {
+                        continue;
+                    }
+                    lb++;
+                    lr0 = min(lr0, r);
+                    lr1 = max(lr1, r);
+                    lc0 = min(lc0, c);
+                    lc1 = max(lc1, c);
+                }
+                lb = __reduce_add_sync(kFull, lb);
+                lnew = __reduce_add_sync(kFull, lnew);
+                lint = __reduce_add_sync(kFull, lint);
+                lst = __reduce_or_sync(kFull, lst);
+                lr0 = __reduce_min_sync(kFull, lr0);
+                lc0 = __reduce_min_sync(kFull, lc0);
+                lr1 = __reduce_max_sync(kFull, lr1);
+                lc1 = __reduce_max_sync(kFull, lc1);
+                if ((threadIdx.x & 31) == 0 && lb) {
+                    atomicAdd(&nburn, lb);
+                    atomicAdd(&burnt, lnew);
+                    atomicAdd(&inter, lint);
+                    atomicOr(&status, lst);
+                    atomicMin(&nr0, lr0);
+                    atomicMax(&nr1, lr1);
+                    atomicMin(&nc0, lc0);
+                    atomicMax(&nc1, lc1);
+                }
+                __syncthreads();
+                ++t;
+                if (nburn == 0) break;
+                if (threadIdx.x == 0) {
+                    r0 = nr0;
+                    r1 = nr1;
+                    c0 = nc0;
+                    c1 = nc1;
+                }
+                __syncthreads();
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            fire_result r;
+            r.burnt = burnt;
+            r.inter = inter;
+            r.target = *m.tgt_count;
+            r.steps = t;
+            r.status = status | (capped ? FIRE_STATUS_STEP_CAP : 0u);
+            r.trials = trials;
+            a.out[s] = r;
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Fitness of Eq. 2 (kind 0) or Jaccard distance (kind 1).
 __global__ void k_fitness(const fire_result *__restrict__ r, int n, int kind,
                           double *__restrict__ out)
@@ -988,6 +1206,12 @@ cudaError_t launch_simulate(const SimLaunch &a, bool smem_state, int nwarps,
         k_simulate<true><<<grid, nwarps * 32, smem_bytes, st>>>(a);
     else
         k_simulate<false><<<grid, nwarps * 32, smem_bytes, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_burnout(const BurnLaunch &a, int grid, cudaStream_t st)
+{
+    k_burnout<<<grid, 256, 0, st>>>(a);
     return cudaGetLastError();
 }
 

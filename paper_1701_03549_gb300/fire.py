@@ -67,7 +67,7 @@ EXPORTED = (
     "fire_net_set_params", "fire_net_get", "fire_net_forward",
     "fire_net_backward", "fire_net_adam", "fire_net_buffer",
     "fire_net_planes", "fire_net_inputs", "fire_net_labels",
-    "fire_net_target_frac", "fire_net_screen",
+    "fire_net_target_frac", "fire_net_screen", "fire_simulate_burnout",
 )
 
 
@@ -121,6 +121,8 @@ def load(path: str = LIB_PATH):
         "ignition_search": (i32, [vp, vp, vp, i32, i32, i32, u64, i32,
                                   C.c_double, u32, vp, vp, vp]),
         "fire_tc_gemm": (i32, [vp, i32, i32, i32, vp, vp, i32, u32, vp]),
+        "fire_simulate_burnout": (i32, [vp, vp, i32, vp, vp, vp, vp, u32,
+                                        u32, vp, vp]),
         "fire_net_param_count": (C.c_int64, []),
         "fire_net_create": (i32, [vp, i32, i32, C.POINTER(vp)]),
         "fire_net_free": (None, [vp]),
@@ -304,6 +306,33 @@ class Map:
         self.ctx.check(lib.fire_simulate_batch(
             self.ctx.h, self.h, n, _ptr(p), _ptr(g), _ptr(s), int(max_steps),
             flags, _ptr(res), _ptr(bs)))
+        return res, bs
+
+    def simulate_burnout(self, params, ignitions, seeds, burn_time,
+                         want_steps=False, max_steps=0, device=False, out=None,
+                         burn_step=None, sync=False):
+        """fire_simulate_burnout: as simulate_batch with per-cell burn times
+        burn_time (uint8 (H, W); a torch CUDA uint8 tensor in device mode)."""
+        lib = self.ctx.lib
+        flags = FIRE_WANT_STEPS if want_steps else 0
+        if device:
+            n = int(params.shape[0])
+            flags |= FIRE_DEVICE_PTRS | (FIRE_SYNC if sync else 0)
+            self.ctx.check(lib.fire_simulate_burnout(
+                self.ctx.h, self.h, n, _ptr(params), _ptr(ignitions),
+                _ptr(seeds), _ptr(burn_time), int(max_steps), flags, _ptr(out),
+                _ptr(burn_step)))
+            return out, burn_step
+        p = _host(params, np.float64).reshape(-1, 5)
+        n = p.shape[0]
+        g = _host(ignitions, np.int32).reshape(n, 2)
+        s = _host(seeds, np.uint64).reshape(n)
+        bt = _host(burn_time, np.uint8).reshape(self.H, self.W)
+        res = np.zeros(n, RESULT_DTYPE)
+        bs = np.zeros((n, self.H, self.W), np.int32) if want_steps else None
+        self.ctx.check(lib.fire_simulate_burnout(
+            self.ctx.h, self.h, n, _ptr(p), _ptr(g), _ptr(s), _ptr(bt),
+            int(max_steps), flags, _ptr(res), _ptr(bs)))
         return res, bs
 
     def simulate_batch_noalloc(self, params, ignitions, seeds, out,
