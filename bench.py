@@ -534,6 +534,184 @@ def run_uneven(args):
     return 0
 
 
+SURROGATE = ("surrogate_screened_ga_1024: 1024x1024 map (spatially varying "
+             "wind), target from the reference parameters at the centre "
+             "ignition; BF16 surrogate (S=256, ~1.05M params) trained on "
+             "200k automaton runs (6250 Gauss(0,5) draws x 16 replicates on "
+             "each of the 512x512 and 1024x1024 maps); plain GA population "
+             "1024 x 16 replicates against the screened GA (1024 candidates "
+             "per generation, 256 simulated x 16 replicates: the 192 best "
+             "predicted and 64 drawn from the rest)")
+TRAIN_FLOP_PER_PIXEL = 2.0 * 128 * ((144 + 7 * 1152) * 2 + 7 * 1152)
+FWD_FLOP_PER_PIXEL = 2.0 * 128 * (144 + 7 * 1152)
+
+
+def _recovery(ctx, m, ign, hist, truth, f_star, torch, reps=64, frac=0.1,
+              tol=0.05, seed=1 << 33):
+    """Per generation: the ensemble (best `frac` of the evaluated population)
+    mean, its fitness re-scored with `reps` fresh replicates, and the
+    relative error of each parameter.  Recovered = the first generation whose
+    ensemble fits the target within `tol` of the reference parameters' own
+    fitness f_star; returns (fits, errors, generation, seconds) with the
+    seconds of the GA up to and including that generation."""
+    from paper_1701_03549_gb300 import calibrate, fire
+
+    ens = []
+    for P, F in zip(hist.params, hist.fitness):
+        order = np.argsort(F, kind="stable")
+        ens.append(P[order[:max(1, int(len(F) * frac))]].mean(axis=0))
+    ens = np.asarray(ens)
+    G = len(ens)
+    fits = calibrate.evaluate(
+        ctx, m, torch.tensor(ens, device="cuda"), ign,
+        np.arange(seed, seed + G * reps, dtype=np.uint64), reps,
+        fire.FITNESS_JACCARD, torch).cpu().numpy()
+    errs = np.abs(ens - truth) / np.abs(truth)
+    t = np.cumsum(hist.seconds)
+    hit = np.nonzero(fits <= (1.0 + tol) * f_star)[0]
+    g = int(hit[0]) if hit.size else None
+    return fits, errs, g, (float(t[g]) if g is not None else None)
+
+
+def run_surrogate(args):
+    """Config 4: surrogate-screened GA against the plain GA (one GPU)."""
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_1701_03549_gb300 import calibrate, fire, surrogate
+
+    rank, world, local = parallel.env_rank()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    ctx = fire.Context(local, stream)
+    truth = np.asarray(synth.TRUTH_BETA, np.float64)
+    land = synth.preset_landscape("ignition_search_1024")
+    land2 = synth.preset_landscape("ga_generation_512")
+    m = ctx.landscape_upload(land)
+    m2 = ctx.landscape_upload(land2)
+    ign = synth.centre_ignition(land.veg)
+
+    def sim_target(seed):
+        _, bs = m.simulate_batch(truth[None], np.asarray([ign], np.int32),
+                                 np.asarray([seed], np.uint64), want_steps=True)
+        return bs[0] >= 0
+
+    _, tgt = workloads.pick_target(sim_target, int((land.veg != 0).sum()))
+    m.target_upload(tgt)
+    sur = surrogate.Surrogate(ctx, S=256, max_batch=8, seed=1)
+
+    # training data from the automaton
+    t0 = time.perf_counter()
+    groups = args.train_groups
+    data = [surrogate.make_dataset(ctx, m2, land2, sur, groups, 16, 21),
+            surrogate.make_dataset(ctx, m, land, sur, groups, 16, 22)]
+    torch.cuda.synchronize()
+    t_data = time.perf_counter() - t0
+    # training
+    t0 = time.perf_counter()
+    losses = sur.train(data, steps=args.train_steps, lr=2e-3, lr_final=1e-4,
+                       seed=3)
+    t_train = time.perf_counter() - t0
+    pix_per_step = 8 * 256 * 256
+    train_tflops = (args.train_steps * pix_per_step * TRAIN_FLOP_PER_PIXEL /
+                    t_train / 1e12)
+    # forward pass alone (roofline of the convolution path)
+    x = torch.empty((8, 256, 256, 16), dtype=torch.bfloat16, device=dev)
+    sur.inputs(data[1].planes, 1024, 1024, data[1].params[:8].contiguous(),
+               data[1].ign[:8].contiguous(), out=x)
+    prob = torch.empty((8, 256, 256), dtype=torch.float32, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    for _ in range(3):
+        sur.net.forward(x, prob)
+    ms = []
+    for _ in range(10):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sur.net.forward(x, prob)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    fwd_ms = statistics.median(ms)
+    fwd_tflops = pix_per_step * FWD_FLOP_PER_PIXEL / (fwd_ms / 1e3) / 1e12
+
+    # the two GAs
+    gens = args.generations
+    clocks = Clocks(local)
+    t0 = time.perf_counter()
+    plain = calibrate.run_ga(ctx, m, ign, pop=1024, reps=16, generations=gens,
+                             ga_seed=5, sim_seed=1 << 30)
+    t_plain = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    scr = surrogate.run_screened_ga(ctx, m, land, sur, ign, pop=256, pool=1024,
+                                    reps=16, generations=gens, ga_seed=5,
+                                    sim_seed=1 << 31)
+    t_scr = time.perf_counter() - t0
+    ck = clocks.stop()
+    f_star = float(calibrate.evaluate(
+        ctx, m, torch.tensor(truth[None], device=dev), ign,
+        np.arange(1 << 34, (1 << 34) + 64, dtype=np.uint64), 64,
+        fire.FITNESS_JACCARD, torch).cpu().numpy()[0])
+    f_plain, e_plain, g_plain, s_plain = _recovery(ctx, m, ign, plain, truth,
+                                                   f_star, torch)
+    f_scr, e_scr, g_scr, s_scr = _recovery(ctx, m, ign, scr, truth, f_star,
+                                           torch)
+    peaks, kind = _peaks()
+    peak = float(peaks.get("bf16_tflops", 1900.0))
+    line = {
+        "metric": "time-to-recover 5 params, surrogate-GA vs plain GA",
+        "value": s_scr, "unit": "s", "n_gpus": world, "steps": gens,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t_scr / gens,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16 (surrogate) / u32 (automaton)", "data": "synthetic",
+        "config": {"workload": SURROGATE, "S": 256, "train_groups": 2 * groups,
+                   "train_runs": 2 * groups * 16,
+                   "train_steps": args.train_steps, "batch": 8,
+                   "recovered_when": "the mean of the best 10% of a generation, "
+                                     "re-scored with 64 fresh replicates, fits "
+                                     "the target within 5% of the reference "
+                                     "parameters' own fitness (64 replicates)"},
+        "reference_fitness": f_star,
+        "plain_ga": {"generations": gens, "seconds": t_plain,
+                     "recovered_generation": g_plain, "recovered_s": s_plain,
+                     "sims_per_generation": 1024 * 16,
+                     "ensemble_fitness_by_gen": [round(float(x), 4)
+                                                 for x in f_plain],
+                     "final_rel_error": [round(float(x), 3)
+                                         for x in e_plain[-1]]},
+        "screened_ga": {"generations": gens, "seconds": t_scr,
+                        "recovered_generation": g_scr, "recovered_s": s_scr,
+                        "sims_per_generation": 256 * 16,
+                        "ensemble_fitness_by_gen": [round(float(x), 4)
+                                                    for x in f_scr],
+                        "final_rel_error": [round(float(x), 3)
+                                            for x in e_scr[-1]]},
+        "training": {"data_s": t_data, "train_s": t_train,
+                     "tflops": train_tflops,
+                     "loss_first": float(np.mean(losses[:10])),
+                     "loss_last": float(np.mean(losses[-50:]))},
+        "roofline": {"bound": "tensor", "achieved": fwd_tflops, "peak": peak,
+                     "unit": "TFLOP/s", "frac": fwd_tflops / peak,
+                     "traffic": None, "kernel": "surrogate forward "
+                     "(k_conv_tma x7 + layer-1 tile + head), batch 8 x 256^2",
+                     "peak_source": f"bf16_tflops ({kind})"},
+        "cpu_baseline": None, "e2e": None, "gpu_launches": None,
+        "clocks": ck,
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    sur.net.free()
+    m.free()
+    m2.free()
+    ctx.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -542,10 +720,15 @@ def main():
     ap.add_argument("--impl", choices=("native", "reference"),
                     default="native")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=("ga512", "uneven"), default="ga512",
+    ap.add_argument("--workload", choices=("ga512", "uneven", "surrogate"),
+                    default="ga512",
                     help="ga512: 512x512 GA generation (default line); "
                          "uneven: nine fires 200x300..2000x1500, 100k "
-                         "simulations in one launch")
+                         "simulations in one launch; surrogate: the "
+                         "surrogate-screened GA against the plain GA")
+    ap.add_argument("--generations", type=int, default=50)
+    ap.add_argument("--train-steps", type=int, default=1500)
+    ap.add_argument("--train-groups", type=int, default=6250)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -553,6 +736,8 @@ def main():
         return run_reference(args)
     if args.workload == "uneven":
         return run_uneven(args)
+    if args.workload == "surrogate":
+        return run_surrogate(args)
     return run_native(args)
 
 

@@ -12,6 +12,7 @@ between torch and the library.
 """
 from __future__ import annotations
 
+import time
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -23,6 +24,7 @@ from . import fire, synth
 class History:
     params: list = field(default_factory=list)     # per generation (P, 5)
     fitness: list = field(default_factory=list)    # per generation (P,)
+    seconds: list = field(default_factory=list)    # wall time per generation
 
     def all(self):
         return np.concatenate(self.params), np.concatenate(self.fitness)
@@ -75,6 +77,7 @@ def run_ga(ctx, m, ignition, pop=256, reps=16, generations=50,
     thi = torch.full((G,), float(hi), dtype=torch.float64, device=dev)
     hist = History()
     for g in range(generations):
+        t0 = time.perf_counter()
         f = evaluate(ctx, m, genes, ignition,
                      sim_seeds(sim_seed, g, pop, reps), reps, kind, torch)
         hist.params.append(genes.cpu().numpy())
@@ -85,6 +88,7 @@ def run_ga(ctx, m, ignition, pop=256, reps=16, generations=50,
                          device=True, out=nxt)
             ctx.sync()
             genes, nxt = nxt, genes
+        hist.seconds.append(time.perf_counter() - t0)
     return hist
 
 

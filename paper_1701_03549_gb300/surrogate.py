@@ -220,17 +220,45 @@ def make_dataset(ctx, m, land, sur: Surrogate, groups: int, reps: int,
 @dataclass
 class ScreenedHistory(calibrate.History):
     predicted: list = field(default_factory=list)  # per generation (pool,)
-    seconds: list = field(default_factory=list)    # wall time per generation
+
+
+def _evaluate_with_labels(ctx, m, sur, genes, ign_dev, seed0, reps, kind):
+    """Mean fitness over `reps` replicates of each row of `genes` (as
+    calibrate.evaluate, seeds seed0 + i R + r) and the burn fractions of the
+    same runs (the surrogate's labels), from one fire_net_labels call."""
+    torch = _torch()
+    dev = genes.device
+    P = int(genes.shape[0])
+    res = torch.zeros((P * reps, 6), dtype=torch.int32, device=dev)
+    lab = torch.empty((P, sur.S, sur.S), dtype=torch.float32, device=dev)
+    fit = torch.empty(P * reps, dtype=torch.float64, device=dev)
+    mean = torch.empty(P, dtype=torch.float64, device=dev)
+    torch.cuda.synchronize(dev)
+    fire.fire_net_labels(ctx, m, sur.S, genes, ign_dev[:P].contiguous(), reps,
+                         seed0, lab, results=res)
+    fire.fire_fitness(ctx, res, kind, device=True, out=fit)
+    fire.fire_group_mean(ctx, fit, reps, device=True, out=mean)
+    ctx.sync()
+    return mean, lab
 
 
 def run_screened_ga(ctx, m, land, sur: Surrogate, ignition, pop=256, pool=1024,
                     reps=16, generations=50, ga_seed=1, sim_seed=1,
-                    kind=fire.FITNESS_JACCARD, lo=-30.0, hi=30.0, init=None):
+                    kind=fire.FITNESS_JACCARD, lo=-30.0, hi=30.0, init=None,
+                    finetune_steps=32, finetune_lr=3e-4, replay_cap=8192,
+                    explore=0.25):
     """The GA with surrogate screening: each generation breeds `pool`
     candidates from the `pop` evaluated parents (ga_step over the parents
     tiled pool / pop times), ranks them by predicted fitness, and simulates
-    only the best `pop` (pool = 4 pop keeps the top 25%).  Generation 0
-    screens `pool` draws of the initial prior the same way."""
+    only `pop` of them (pool = 4 pop simulates a quarter): the best
+    (1 - explore) pop by predicted fitness and explore pop drawn uniformly
+    from the rest (seeded), so that candidates the surrogate wrongly rejects
+    still reach the automaton; generation 0 screens `pool` draws of the
+    initial prior the same way.  The automaton runs of the simulated
+    candidates also yield their burn fractions, which join a replay buffer
+    the surrogate is fine-tuned on for `finetune_steps` Adam steps per
+    generation (0: no fine-tuning), so that it stays accurate where the GA
+    is searching."""
     torch = _torch()
     dev = torch.device("cuda", ctx.device)
     H, W = land.veg.shape
@@ -250,21 +278,42 @@ def run_screened_ga(ctx, m, land, sur: Surrogate, ignition, pop=256, pool=1024,
     tlo = torch.full((5,), float(lo), dtype=torch.float64, device=dev)
     thi = torch.full((5,), float(hi), dtype=torch.float64, device=dev)
     pred = torch.empty(pool, dtype=torch.float64, device=dev)
-    keep = torch.empty(pop, dtype=torch.int32, device=dev)
+    rank = torch.empty(pool, dtype=torch.int32, device=dev)
+    n_top = pop - int(round(explore * pop))
+    rng = np.random.default_rng(ga_seed + 7919)
     nxt = torch.empty_like(cand)
+    replay = None
     hist = ScreenedHistory()
     for g in range(generations):
         t0 = time.perf_counter()
         prob = sur.predict(planes, H, W, cand, ign)
-        fire.fire_net_screen(ctx, S, prob, tfrac, cells, kind, pop, pred, keep)
+        fire.fire_net_screen(ctx, S, prob, tfrac, cells, kind, pool, pred,
+                             rank)
         ctx.sync()
-        genes = cand[keep.long()].contiguous()
-        f = calibrate.evaluate(ctx, m, genes, ignition,
-                               calibrate.sim_seeds(sim_seed, g, pop, reps),
-                               reps, kind, torch)
+        order = rank.cpu().numpy()
+        rest = order[n_top:]
+        pick = np.concatenate([order[:n_top],
+                               rng.choice(rest, pop - n_top, replace=False)])
+        genes = cand[torch.as_tensor(pick, device=dev).long()].contiguous()
+        seed0 = sim_seed + g * pop * reps
+        f, lab = _evaluate_with_labels(ctx, m, sur, genes, ign, seed0, reps,
+                                       kind)
         hist.params.append(genes.cpu().numpy())
         hist.fitness.append(f.cpu().numpy())
         hist.predicted.append(pred.cpu().numpy())
+        if finetune_steps:
+            chunk = Dataset(H, W, planes, genes, ign[:pop].contiguous(), lab)
+            if replay is None:
+                replay = chunk
+            else:
+                start = max(0, len(replay) + pop - replay_cap)
+                replay = Dataset(
+                    H, W, planes,
+                    torch.cat([replay.params[start:], genes]),
+                    torch.cat([replay.ign[start:], chunk.ign]),
+                    torch.cat([replay.labels[start:], lab]))
+            sur.train([replay], steps=finetune_steps, lr=finetune_lr,
+                      seed=g + 1)
         if g + 1 < generations:
             torch.cuda.synchronize(dev)
             fire.ga_step(ctx, genes.repeat(rep, 1).contiguous(),
