@@ -647,6 +647,9 @@ def run_surrogate(args):
     plain = calibrate.run_ga(ctx, m, ign, pop=1024, reps=16, generations=gens,
                              ga_seed=5, sim_seed=1 << 30)
     t_plain = time.perf_counter() - t0
+    plain256 = calibrate.run_ga(ctx, m, ign, pop=256, reps=16,
+                                generations=gens, ga_seed=5,
+                                sim_seed=1 << 32)
     t0 = time.perf_counter()
     scr = surrogate.run_screened_ga(ctx, m, land, sur, ign, pop=256, pool=1024,
                                     reps=16, generations=gens, ga_seed=5,
@@ -661,6 +664,8 @@ def run_surrogate(args):
                                                    f_star, torch)
     f_scr, e_scr, g_scr, s_scr = _recovery(ctx, m, ign, scr, truth, f_star,
                                            torch)
+    f_p256, e_p256, g_p256, s_p256 = _recovery(ctx, m, ign, plain256, truth,
+                                               f_star, torch)
     peaks, kind = _peaks()
     peak = float(peaks.get("bf16_tflops", 1900.0))
     line = {
@@ -684,6 +689,15 @@ def run_surrogate(args):
                                                  for x in f_plain],
                      "final_rel_error": [round(float(x), 3)
                                          for x in e_plain[-1]]},
+        "plain_ga_256": {"generations": gens,
+                         "seconds": float(sum(plain256.seconds)),
+                         "recovered_generation": g_p256,
+                         "recovered_s": s_p256,
+                         "sims_per_generation": 256 * 16,
+                         "ensemble_fitness_by_gen": [round(float(x), 4)
+                                                     for x in f_p256],
+                         "final_rel_error": [round(float(x), 3)
+                                             for x in e_p256[-1]]},
         "screened_ga": {"generations": gens, "seconds": t_scr,
                         "recovered_generation": g_scr, "recovered_s": s_scr,
                         "sims_per_generation": 256 * 16,
@@ -712,6 +726,82 @@ def run_surrogate(args):
     return 0
 
 
+def run_surrogate_step(args):
+    """Surrogate network alone: forward passes and training steps (forward,
+    backward, Adam) on a batch of 8 inputs of 256 x 256 (random weights and
+    inputs; no automaton), with the tensor-core roofline."""
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_1701_03549_gb300 import fire, surrogate
+
+    rank, world, local = parallel.env_rank()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    ctx = fire.Context(local, stream)
+    B, S = 8, 256
+    net = fire.Net(ctx, S, B)
+    net.set_params(surrogate.init_params(1))
+    g = torch.Generator(device=dev).manual_seed(0)
+    x = torch.rand((B, S, S, 16), device=dev, generator=g).to(torch.bfloat16)
+    t = torch.rand((B, S, S), device=dev, generator=g)
+    prob = torch.empty((B, S, S), device=dev)
+    loss = torch.zeros(1, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    pix = B * S * S
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        ms = []
+        for _ in range(args.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return statistics.median(ms)
+
+    clocks = Clocks(local)
+    fwd_ms = timed(lambda: net.forward(x, prob))
+    train_ms = timed(lambda: (net.backward(x, t, loss), net.adam(1e-4)))
+    ck = clocks.stop()
+    fwd = pix * FWD_FLOP_PER_PIXEL / (fwd_ms / 1e3) / 1e12
+    trn = pix * TRAIN_FLOP_PER_PIXEL / (train_ms / 1e3) / 1e12
+    peaks, kind = _peaks()
+    peak = float(peaks.get("bf16_tflops", 1900.0))
+    if rank == 0:
+        print(json.dumps({
+            "metric": "surrogate training throughput", "value": trn,
+            "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": train_ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": "surrogate_step: 1.05M-parameter dilated "
+                       "conv net, batch 8 x 256 x 256 x 16, random weights "
+                       "and inputs", "l2": "flushed between timed steps "
+                       "(256 MB write)"},
+            "forward_ms": fwd_ms, "forward_tflops": fwd,
+            "roofline": {"bound": "tensor", "achieved": trn, "peak": peak,
+                         "unit": "TFLOP/s", "frac": trn / peak,
+                         "traffic": None, "kernel": "training step (k_conv_tma "
+                         "forward and input gradient, k_wgrad_tma, layer-1 "
+                         "tile, head, Adam)",
+                         "peak_source": f"bf16_tflops ({kind})"},
+            "cpu_baseline": None, "e2e": None, "gpu_launches": None,
+            "clocks": ck}))
+    net.free()
+    ctx.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -720,7 +810,8 @@ def main():
     ap.add_argument("--impl", choices=("native", "reference"),
                     default="native")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=("ga512", "uneven", "surrogate"),
+    ap.add_argument("--workload",
+                    choices=("ga512", "uneven", "surrogate", "surrogate_step"),
                     default="ga512",
                     help="ga512: 512x512 GA generation (default line); "
                          "uneven: nine fires 200x300..2000x1500, 100k "
@@ -738,6 +829,8 @@ def main():
         return run_uneven(args)
     if args.workload == "surrogate":
         return run_surrogate(args)
+    if args.workload == "surrogate_step":
+        return run_surrogate_step(args)
     return run_native(args)
 
 
