@@ -64,9 +64,9 @@ def _kernel_hash():
     return h.hexdigest()
 
 
-def _committed_traffic():
-    """DRAM bytes per launch of the simulation kernel from the committed ncu
-    summary, or None when the kernel changed since it was captured."""
+def _committed_profile():
+    """The committed ncu record of the simulation kernel (DRAM and L2 bytes
+    per launch), or None when the kernel changed since it was captured."""
     p = os.path.join(ROOT, "profiles", "k_simulate_traffic.json")
     try:
         with open(p) as f:
@@ -75,7 +75,30 @@ def _committed_traffic():
         return None
     if d.get("source_sha256") != _kernel_hash():
         return None
-    return d.get("dram_bytes_per_launch")
+    return d
+
+
+def _committed_traffic():
+    d = _committed_profile()
+    return None if d is None else d.get("dram_bytes_per_launch")
+
+
+def _memory_roofs(kernel_s, peaks, peaks_kind):
+    """DRAM and L2 bandwidth of the simulation kernel: bytes per launch from
+    the committed ncu capture over the event-timed launch duration, against
+    the measured HBM copy bandwidth and ncu's L2 sector peak."""
+    d = _committed_profile()
+    if d is None:
+        return None
+    dram = d["dram_bytes_per_launch"] / kernel_s / 1e9
+    l2 = d["l2_bytes_per_launch"] / kernel_s / 1e9
+    l2_peak = (d["l2_bytes_per_launch"] / (d["ncu_duration_ms"] / 1e3) / 1e9 /
+               (d["l2_pct_of_peak_sectors"] / 100.0))
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    return {"dram_gbs": dram, "dram_frac": dram / hbm,
+            "dram_peak_gbs": hbm, "dram_peak_source": f"hbm_gbs ({peaks_kind})",
+            "l2_gbs": l2, "l2_frac": l2 / l2_peak, "l2_peak_gbs": l2_peak,
+            "l2_peak_source": "ncu lts__t_sectors peak"}
 
 
 class Clocks:
@@ -382,7 +405,8 @@ def run_native(args):
                                         f"{sm_max:.0f} MHz ({peaks_kind} max "
                                         "SM clock)",
                          "ops_per_trial": OPS_PER_TRIAL,
-                         "kernel_ms": 1e3 * mean_sim_s},
+                         "kernel_ms": 1e3 * mean_sim_s,
+                         "memory": _memory_roofs(mean_sim_s, peaks, peaks_kind)},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
