@@ -12,9 +12,11 @@
 //   * another thread waits for the slab, issues four 128 x 128 x 16 MMAs into
 //     the tensor-memory accumulator and commits them to the slab's "empty"
 //     barrier, which hands the stage back to the loader.
-// Three stages (96 KB) let two CTAs share an SM, so one CTA's epilogue
+// Two stages (64 KB) let three CTAs share an SM, so the epilogues of some
 // (tensor memory -> registers -> bias/ReLU or ReLU mask -> BF16 stores)
-// overlaps the other's main loop.  Every wait is bounded; on a timeout the
+// overlap the main loops of the others; on a GB300 this beat three stages
+// with two CTAs per SM by 5-10 % and four or more stages with one CTA per SM
+// by about 50 %.  Every wait is bounded; on a timeout the
 // CTA records an error, waits (bounded) for its own copies in flight, frees
 // its tensor memory and returns.
 #include "fire_internal.h"
@@ -29,11 +31,18 @@
 namespace fire {
 namespace convtma {
 
-constexpr int kStages = 3;
+#ifndef FIRE_CONV_STAGES
+#define FIRE_CONV_STAGES 2
+#endif
+constexpr int kStages = FIRE_CONV_STAGES;       // shared-memory stages per CTA
 constexpr int kTileBytes = 128 * 128;           // 128 rows x 64 BF16
 constexpr int kStageBytes = 2 * kTileBytes;     // A + B
 constexpr int kSmem = kStages * kStageBytes + 1024;
 constexpr int kSlabs = 18;                      // 9 taps x 2 channel halves
+// CTAs that fit on one SM (227 KB of shared memory; 128 tensor-memory
+// columns each, so at most four).
+constexpr int kCtasPerSm =
+    (227 * 1024) / (kSmem + 2048) > 4 ? 4 : (227 * 1024) / (kSmem + 2048);
 
 struct Epi {
     int mode;                 // 0 forward (bias + ReLU), 1 input gradient (mask)
@@ -94,7 +103,7 @@ __device__ __forceinline__ bool pos16(uint32_t u)
 }
 
 // sign = +1: forward (source pixel p + off(t)); -1: input gradient (p - off(t)).
-__global__ void __launch_bounds__(128, 2)
+__global__ void __launch_bounds__(128, kCtasPerSm)
     k_conv_tma(const __grid_constant__ CUtensorMap act,
                const __grid_constant__ CUtensorMap wts, Epi epi, int S, int lgS,
                int d, int sign, uint32_t *err)
@@ -103,10 +112,12 @@ __global__ void __launch_bounds__(128, 2)
     __shared__ __align__(8) unsigned long long full[kStages], empty[kStages], done;
     __shared__ uint32_t tmem_slot;
     __shared__ int s_fail, s_issued, s_consumed;
+    __shared__ float s_bias[128];
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t base = (tc::smem_addr(smem_raw) + 1023u) & ~1023u;
     const int m0 = blockIdx.x * 128;
+    if (epi.mode == 0) s_bias[tid] = epi.bias[tid];
     const int b = m0 >> (2 * lgS);
     const int y0 = (m0 >> lgS) & (S - 1), x0 = m0 & (S - 1);
 
@@ -179,28 +190,34 @@ __global__ void __launch_bounds__(128, 2)
         const int p = m0 + warp * 32 + lane;
         uint16_t *orow = epi.out + (size_t)p * 128;
 #pragma unroll 1
-        for (int c0 = 0; c0 < 128; c0 += 16) {
-            float v[16];
-            tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-            uint32_t pk[8];
+        for (int c0 = 0; c0 < 128; c0 += 32) {
+            float v[32];
+            tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+            uint32_t pk[16];
             if (epi.mode == 0) {
 #pragma unroll
-                for (int j = 0; j < 8; ++j)
-                    pk[j] = pack2(fmaxf(v[2 * j] + epi.bias[c0 + 2 * j], 0.0f),
-                                  fmaxf(v[2 * j + 1] + epi.bias[c0 + 2 * j + 1], 0.0f));
+                for (int j = 0; j < 16; ++j)
+                    pk[j] = pack2(fmaxf(v[2 * j] + s_bias[c0 + 2 * j], 0.0f),
+                                  fmaxf(v[2 * j + 1] + s_bias[c0 + 2 * j + 1], 0.0f));
             } else {
                 const uint4 *hp =
                     reinterpret_cast<const uint4 *>(epi.hprev + (size_t)p * 128 + c0);
-                const uint4 h0 = hp[0], h1 = hp[1];
-                const uint32_t hw[8] = {h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w};
 #pragma unroll
-                for (int j = 0; j < 8; ++j)
-                    pk[j] = pack2(pos16(hw[j] & 0xffffu) ? v[2 * j] : 0.0f,
-                                  pos16(hw[j] >> 16) ? v[2 * j + 1] : 0.0f);
+                for (int q = 0; q < 4; ++q) {
+                    const uint4 h = hp[q];
+                    const uint32_t hw[4] = {h.x, h.y, h.z, h.w};
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const int e = 2 * (4 * q + j);
+                        pk[4 * q + j] = pack2(pos16(hw[j] & 0xffffu) ? v[e] : 0.0f,
+                                              pos16(hw[j] >> 16) ? v[e + 1] : 0.0f);
+                    }
+                }
             }
             uint4 *o = reinterpret_cast<uint4 *>(orow + c0);
-            o[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-            o[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                o[q] = make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
         }
     } else if (tid == 0) {
         atomicOr(err, 1u);
@@ -230,7 +247,7 @@ __device__ __forceinline__ uint64_t desc_sw128_mn(uint32_t saddr)
     return d;
 }
 
-__global__ void __launch_bounds__(128, 2)
+__global__ void __launch_bounds__(128, kCtasPerSm)
     k_wgrad_tma(const __grid_constant__ CUtensorMap dzm,
                 const __grid_constant__ CUtensorMap inm, float *dw, int S, int lgS,
                 int d, int slabs_total, int slabs_per, uint32_t *err)
@@ -316,13 +333,17 @@ __global__ void __launch_bounds__(128, 2)
 
     if (ns > 0 && !s_fail) {
         const int o = warp * 32 + lane;
-        float *row = dw + (size_t)o * 1152 + tap * 128;
+        // 16-byte aligned: dw, the row stride (1152 floats) and tap * 128 are
+        // multiples of four floats
+        float4 *row = reinterpret_cast<float4 *>(dw + (size_t)o * 1152 + tap * 128);
 #pragma unroll 1
-        for (int c0 = 0; c0 < 128; c0 += 16) {
-            float v[16];
-            tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+        for (int c0 = 0; c0 < 128; c0 += 32) {
+            float v[32];
+            tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
 #pragma unroll
-            for (int j = 0; j < 16; ++j) atomicAdd(row + c0 + j, v[j]);
+            for (int j = 0; j < 8; ++j)
+                atomicAdd(row + c0 / 4 + j,
+                          make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]));
         }
     } else if (s_fail && tid == 0) {
         atomicOr(err, 1u);
@@ -418,7 +439,7 @@ cudaError_t launch_wgrad_tma(const uint16_t *dz, const uint16_t *in, float *dw, 
 {
     using namespace convtma;
     if (S < 16 || (S & (S - 1)) || ((uintptr_t)dz & 15) || ((uintptr_t)in & 15) ||
-        split < 1)
+        ((uintptr_t)dw & 15) || split < 1)
         return cudaErrorInvalidValue;
     CUtensorMap mz, mi;
     if (!map_act(&mz, dz, n, S, 64) || !map_act(&mi, in, n, S, 64))
