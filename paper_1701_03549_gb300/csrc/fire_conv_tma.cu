@@ -355,6 +355,131 @@ __global__ void __launch_bounds__(128, kCtasPerSm)
     if (warp == 0) tc::tmem_dealloc(tmem, 128);
 }
 
+// First layer (16 -> 128 channels): one tap per 16-wide K slab.  The
+// activation box is 16 channels (32 bytes) x 128 pixels and the weight box
+// 16 x 128 rows of W1[o][t][i]; both land 32-byte swizzled, the canonical
+// K-major SWIZZLE_32B layout (8-row groups 256 bytes apart), and one
+// 128 x 128 x 16 MMA consumes a slab.  Nine slabs, no padding of K.
+constexpr int kC1Stages = 6;                     // 49 KB: four CTAs per SM, as
+                                                  // many as tensor memory holds
+constexpr int kC1Tile = 128 * 32;                 // 128 rows x 16 BF16
+constexpr int kC1Stage = 2 * kC1Tile;
+constexpr int kC1Smem = kC1Stages * kC1Stage + 1024;
+
+__device__ __forceinline__ uint64_t desc_sw32(uint32_t saddr)
+{
+    uint64_t d = (uint64_t)((saddr & 0x3ffffu) >> 4);
+    d |= (uint64_t)1 << 16;                 // LBO (unused for swizzled K-major)
+    d |= (uint64_t)(256 >> 4) << 32;        // SBO: 8 rows x 32 B
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)6 << 61;                 // SWIZZLE_32B
+    return d;
+}
+
+__global__ void __launch_bounds__(128, 4)
+    k_conv1_tma(const __grid_constant__ CUtensorMap act,
+                const __grid_constant__ CUtensorMap wts, const float *bias,
+                uint16_t *out, int S, int lgS, uint32_t *err)
+{
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    __shared__ __align__(8) unsigned long long full[kC1Stages], empty[kC1Stages], done;
+    __shared__ uint32_t tmem_slot;
+    __shared__ int s_fail, s_issued, s_consumed;
+    __shared__ float s_bias[128];
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t base = (tc::smem_addr(smem_raw) + 1023u) & ~1023u;
+    const int m0 = blockIdx.x * 128;
+    const int b = m0 >> (2 * lgS);
+    const int y0 = (m0 >> lgS) & (S - 1), x0 = m0 & (S - 1);
+    s_bias[tid] = bias[tid];
+
+    if (warp == 0) {
+        tc::tmem_alloc(&tmem_slot, 128);
+        tc::tmem_relinquish();
+    }
+    if (tid == 0) {
+        for (int i = 0; i < kC1Stages; ++i) {
+            tc::mbar_init(&full[i], 1);
+            tc::mbar_init(&empty[i], 1);
+        }
+        tc::mbar_init(&done, 1);
+        s_fail = 0;
+        s_issued = 0;
+        s_consumed = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = tmem_slot;
+
+    if (warp == 0 && lane == 0) {
+        int s = 0;
+        for (; s < 9; ++s) {
+            const int st = s % kC1Stages;
+            if (s >= kC1Stages &&
+                !tc::mbar_wait_bounded(&empty[st], ((s / kC1Stages) - 1) & 1)) {
+                atomicOr(&s_fail, 1);
+                break;
+            }
+            if (*(volatile int *)&s_fail) break;
+            const int dy = s / 3 - 1, dx = s % 3 - 1;   // dilation 1
+            const uint32_t sa = base + st * kC1Stage;
+            expect_tx(&full[st], kC1Stage);
+            tma_4d(sa, &act, 0, x0 + dx, y0 + dy, b, &full[st]);
+            tma_2d(sa + kC1Tile, &wts, s * 16, 0, &full[st]);
+        }
+        s_issued = s;
+    } else if (warp == 1 && lane == 0) {
+        constexpr uint32_t idesc = tc::idesc_bf16(128, 128);
+        int s = 0;
+        for (; s < 9; ++s) {
+            const int st = s % kC1Stages;
+            if (!tc::mbar_wait_bounded(&full[st], (s / kC1Stages) & 1)) {
+                atomicOr(&s_fail, 1);
+                break;
+            }
+            tc::fence_after_sync();
+            const uint32_t sa = base + st * kC1Stage;
+            tc::mma_bf16(tmem, desc_sw32(sa), desc_sw32(sa + kC1Tile), idesc, s > 0);
+            tc::mma_commit(&empty[st]);
+        }
+        s_consumed = s;
+        if (s == 9) tc::mma_commit(&done);
+    }
+    __syncwarp();
+    if (!tc::mbar_wait_bounded(&done, 0)) atomicOr(&s_fail, 1);
+    __syncthreads();
+    tc::fence_after_sync();
+
+    if (!s_fail) {
+        const int p = m0 + warp * 32 + lane;
+        uint16_t *orow = out + (size_t)p * 128;
+#pragma unroll 1
+        for (int c0 = 0; c0 < 128; c0 += 32) {
+            float v[32];
+            tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+            uint32_t pk[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+                pk[j] = pack2(fmaxf(v[2 * j] + s_bias[c0 + 2 * j], 0.0f),
+                              fmaxf(v[2 * j + 1] + s_bias[c0 + 2 * j + 1], 0.0f));
+            uint4 *o = reinterpret_cast<uint4 *>(orow + c0);
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                o[q] = make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
+        }
+    } else if (tid == 0) {
+        atomicOr(err, 1u);
+        for (int s = s_consumed; s < s_issued; ++s)
+            tc::mbar_wait_bounded(&full[s % kC1Stages], (s / kC1Stages) & 1);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, 128);
+}
+
 // --- host: tensor maps ------------------------------------------------------
 
 PFN_cuTensorMapEncodeTiled_v12000 encoder()
@@ -385,6 +510,37 @@ bool map_act(CUtensorMap *m, const uint16_t *ptr, int n, int S, int pix = 128)
     const cuuint32_t es[4] = {1, 1, 1, 1};
     return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<uint16_t *>(ptr), dims,
               strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// First-layer input [n][S][S][16] BF16; box 16 channels x 128 pixels.
+bool map_in16(CUtensorMap *m, const uint16_t *ptr, int n, int S)
+{
+    auto fn = encoder();
+    if (!fn) return false;
+    const cuuint64_t dims[4] = {16, (cuuint64_t)S, (cuuint64_t)S, (cuuint64_t)n};
+    const cuuint64_t strides[3] = {32, (cuuint64_t)S * 32, (cuuint64_t)S * S * 32};
+    const cuuint32_t bx = S >= 128 ? 128 : S, by = 128 / bx;
+    const cuuint32_t box[4] = {16, bx, by, 1};
+    const cuuint32_t es[4] = {1, 1, 1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<uint16_t *>(ptr), dims,
+              strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// First-layer weights [128 rows][144] BF16; box 16 x 128.
+bool map_w144(CUtensorMap *m, const uint16_t *ptr)
+{
+    auto fn = encoder();
+    if (!fn) return false;
+    const cuuint64_t dims[2] = {144, 128};
+    const cuuint64_t strides[1] = {144 * 2};
+    const cuuint32_t box[2] = {16, 128};
+    const cuuint32_t es[2] = {1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<uint16_t *>(ptr), dims,
+              strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B,
               CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
@@ -452,6 +608,26 @@ cudaError_t launch_wgrad_tma(const uint16_t *dz, const uint16_t *in, float *dw, 
     const int per = (total + split - 1) / split;
     dim3 grid(1, 9, (total + per - 1) / per);
     k_wgrad_tma<<<grid, 128, kSmem, st>>>(mz, mi, dw, S, lgS, d, total, per, err);
+    return cudaGetLastError();
+}
+
+// First layer forward: out = ReLU(conv3x3(x, W1) + b1) for x [n][S][S][16]
+// and W1 [128][9][16] (BF16, 16-byte aligned), S a power of two >= 16.
+cudaError_t launch_conv1_tma(const uint16_t *x, const uint16_t *w, const float *bias,
+                             uint16_t *out, int n, int S, int lgS, uint32_t *err,
+                             cudaStream_t st)
+{
+    using namespace convtma;
+    if (S < 16 || (S & (S - 1)) || ((uintptr_t)x & 15) || ((uintptr_t)w & 15))
+        return cudaErrorInvalidValue;
+    CUtensorMap ma, mw;
+    if (!map_in16(&ma, x, n, S) || !map_w144(&mw, w)) return cudaErrorInvalidValue;
+    cudaError_t attr = cudaFuncSetAttribute(
+        k_conv1_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, kC1Smem);
+    if (attr != cudaSuccess) return attr;
+    const long long P = (long long)n * S * S;
+    k_conv1_tma<<<(unsigned)(P / 128), 128, kC1Smem, st>>>(ma, mw, bias, out, S, lgS,
+                                                           err);
     return cudaGetLastError();
 }
 

@@ -484,7 +484,11 @@ cudaError_t net_forward(fire_net *net, int n, const uint16_t *x, uint32_t *err,
     const int S = net->S, lgS = net->lgS;
     const int M = n * S * S;
     cudaError_t e;
-    {
+    if (S >= 16) {
+        e = launch_conv1_tma(x, net->wb + w_off(0), net->theta + b_off(0), net->h[0],
+                             n, S, lgS, err, st);
+        if (e != cudaSuccess) return e;
+    } else {
         ConvFwd<kCin> p{x, net->wb + w_off(0), net->theta + b_off(0), net->h[0],
                         M, kC, 192, S, lgS, kDil[0]};
         e = tc::launch_tc_tile<128>(p, 1, err, st);
