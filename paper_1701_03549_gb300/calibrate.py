@@ -58,11 +58,55 @@ def evaluate(ctx, m, params_dev, ignition, seeds, reps, kind, torch):
     return mean
 
 
+def evaluate_sharded(ctx, m, params_dev, ignition, seeds, reps, kind, torch,
+                     rank: int, world: int):
+    """evaluate() with the generation's P x reps simulations split over
+    `world` ranks (one GPU each): each rank simulates its contiguous block,
+    the fire_result records are all-gathered (24 bytes per simulation, the
+    only collective), and every rank computes the same fitness and replicate
+    means on its device."""
+    from . import parallel
+
+    dev = params_dev.device
+    P = params_dev.shape[0]
+    n = P * reps
+    p_all = params_dev.repeat_interleave(reps, dim=0).contiguous()
+    s_all = np.asarray(seeds, np.uint64)
+
+    def shard(lo, hi):
+        k = hi - lo
+        if k == 0:
+            return np.zeros(0, fire.RESULT_DTYPE)
+        ign = torch.tensor(np.tile(np.asarray(ignition, np.int32), (k, 1)),
+                           device=dev)
+        s = torch.tensor(s_all[lo:hi].view(np.int64), device=dev)
+        out = torch.zeros((k, 6), dtype=torch.int32, device=dev)
+        torch.cuda.synchronize(dev)
+        m.simulate_batch(p_all[lo:hi].contiguous(), ign, s, device=True,
+                         out=out)
+        ctx.sync()
+        return fire.results_view(out)
+
+    res = parallel.sharded_results(n, shard, rank, world)
+    raw = np.ascontiguousarray(res).view(np.int32).reshape(n, 6)
+    out = torch.tensor(raw, device=dev)
+    fit = torch.zeros(n, dtype=torch.float64, device=dev)
+    mean = torch.zeros(P, dtype=torch.float64, device=dev)
+    torch.cuda.synchronize(dev)
+    fire.fire_fitness(ctx, out, kind, device=True, out=fit)
+    fire.fire_group_mean(ctx, fit, reps, device=True, out=mean)
+    ctx.sync()
+    return mean
+
+
 def run_ga(ctx, m, ignition, pop=256, reps=16, generations=50,
            prior="gauss", lo=-30.0, hi=30.0, ga_seed=1, sim_seed=1,
-           kind=fire.FITNESS_JACCARD, init=None):
+           kind=fire.FITNESS_JACCARD, init=None, rank=0, world=1):
     """The Appendix B genetic algorithm on map `m` (which holds the target).
-    Returns the History of every generation's population and fitness."""
+    Returns the History of every generation's population and fitness.  With
+    world > 1 (one process per GPU, default process group initialised) each
+    generation's simulations are split over the ranks (evaluate_sharded);
+    the GA step is replicated, so every rank holds the same population."""
     import torch
 
     dev = torch.device("cuda", ctx.device)
@@ -78,8 +122,12 @@ def run_ga(ctx, m, ignition, pop=256, reps=16, generations=50,
     hist = History()
     for g in range(generations):
         t0 = time.perf_counter()
-        f = evaluate(ctx, m, genes, ignition,
-                     sim_seeds(sim_seed, g, pop, reps), reps, kind, torch)
+        seeds = sim_seeds(sim_seed, g, pop, reps)
+        if world > 1:
+            f = evaluate_sharded(ctx, m, genes, ignition, seeds, reps, kind,
+                                 torch, rank, world)
+        else:
+            f = evaluate(ctx, m, genes, ignition, seeds, reps, kind, torch)
         hist.params.append(genes.cpu().numpy())
         hist.fitness.append(f.cpu().numpy())
         if g + 1 < generations:

@@ -71,3 +71,16 @@ def max_over_ranks(x: float, world: int, device=None) -> float:
                      device=device if device is not None else "cpu")
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def sharded_results(n: int, simulate_shard, rank: int, world: int):
+    """Results of n independent simulations computed by `world` ranks: rank r
+    runs simulate_shard(lo, hi) on its contiguous block [lo, hi) and one
+    all-gather (the only collective) returns the whole batch, in index
+    order, on every rank."""
+    lo, hi = shard_range(n, rank, world)
+    mine = simulate_shard(lo, hi)
+    if len(mine) != hi - lo:
+        raise ValueError(f"rank {rank}: shard [{lo}, {hi}) returned "
+                         f"{len(mine)} results")
+    return gather_results(mine, world)

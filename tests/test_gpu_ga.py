@@ -101,3 +101,26 @@ def test_ga_improves_fitness_on_a_synthetic_scar(env):
     est = calibrate.ensemble(*hist.all(), keep=64)
     assert est["size"] == 64 and np.all(np.isfinite(est["mean"]))
     m.free()
+
+
+def test_sharded_evaluation_on_one_rank_equals_evaluate(env):
+    """The sharded path (split simulations, gathered results, fitness on the
+    device) gives the same replicate means as the single-call path."""
+    torch, fire, oracle, ctx = env
+    from paper_1701_03549_gb300 import calibrate
+
+    land = synth.landscape(96, 96, seed=6)
+    m = ctx.landscape_upload(land)
+    ign = synth.centre_ignition(land.veg)
+    _, bs = m.simulate_batch(np.asarray([synth.TRUTH_BETA]),
+                             np.asarray([ign], np.int32),
+                             np.asarray([9], np.uint64), want_steps=True)
+    m.target_upload(bs[0] >= 0)
+    genes = torch.tensor(synth.gauss_population(12, 3), device="cuda")
+    seeds = calibrate.sim_seeds(5, 0, 12, 4)
+    a = calibrate.evaluate(ctx, m, genes, ign, seeds, 4,
+                           fire.FITNESS_JACCARD, torch)
+    b = calibrate.evaluate_sharded(ctx, m, genes, ign, seeds, 4,
+                                   fire.FITNESS_JACCARD, torch, 0, 1)
+    assert torch.equal(a, b)
+    m.free()

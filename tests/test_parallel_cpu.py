@@ -78,3 +78,81 @@ def test_gather_and_max_over_two_gloo_ranks():
         assert burnt == [3 * i for i in range(11)]
         assert steps == [1] * 6 + [2] * 5
         assert t == 1.5
+
+
+def _shard_worker(rank, world, port, q):
+    import torch.distributed as dist
+
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        def fake(lo, hi):        # a deterministic stand-in for one GPU's shard
+            r = np.zeros(hi - lo, RESULT_DTYPE)
+            r["burnt"] = (np.arange(lo, hi) * 7919) % 1000
+            r["trials"] = np.arange(lo, hi)
+            return r
+        got = parallel.sharded_results(23, fake, rank, world)
+        q.put((rank, got["burnt"].tolist(), got["trials"].tolist()))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_sharded_results_equal_the_unsharded_batch():
+    import torch.multiprocessing as mp
+
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_shard_worker, args=(r, 3, port, q))
+             for r in range(3)]
+    for p in procs:
+        p.start()
+    out = [q.get(timeout=120) for _ in procs]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank, burnt, trials in out:
+        assert burnt == [(i * 7919) % 1000 for i in range(23)]
+        assert trials == list(range(23))
+
+
+def _dying_worker(rank, world, port, q):
+    import datetime
+
+    import torch.distributed as dist
+
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world,
+                            timeout=datetime.timedelta(seconds=10))
+    if rank == 1:
+        os._exit(3)              # dies between generations, before the gather
+    import time
+    t0 = time.time()
+    try:
+        parallel.sharded_results(8, lambda lo, hi: np.zeros(hi - lo,
+                                                             RESULT_DTYPE),
+                                 rank, world)
+        q.put((rank, "no error", time.time() - t0))
+    except Exception as e:   # the collective fails instead of hanging
+        q.put((rank, type(e).__name__, time.time() - t0))
+    os._exit(0)
+
+
+def test_a_dead_rank_is_an_error_not_a_hang():
+    import torch.multiprocessing as mp
+
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_dying_worker, args=(r, 2, port, q))
+             for r in range(2)]
+    for p in procs:
+        p.start()
+    rank, what, dt = q.get(timeout=120)
+    for p in procs:
+        p.join(timeout=60)
+    assert rank == 0 and what != "no error", (what, dt)
+    assert dt < 60
+    assert procs[1].exitcode == 3
