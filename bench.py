@@ -64,10 +64,10 @@ def _kernel_hash():
     return h.hexdigest()
 
 
-def _committed_profile():
+def _committed_profile(name="k_simulate_traffic.json"):
     """The committed ncu record of the simulation kernel (DRAM and L2 bytes
     per launch), or None when the kernel changed since it was captured."""
-    p = os.path.join(ROOT, "profiles", "k_simulate_traffic.json")
+    p = os.path.join(ROOT, "profiles", name)
     try:
         with open(p) as f:
             d = json.load(f)
@@ -83,11 +83,11 @@ def _committed_traffic():
     return None if d is None else d.get("dram_bytes_per_launch")
 
 
-def _memory_roofs(kernel_s, peaks, peaks_kind):
+def _memory_roofs(kernel_s, peaks, peaks_kind, name="k_simulate_traffic.json"):
     """DRAM and L2 bandwidth of the simulation kernel: bytes per launch from
     the committed ncu capture over the event-timed launch duration, against
     the measured HBM copy bandwidth and ncu's L2 sector peak."""
-    d = _committed_profile()
+    d = _committed_profile(name)
     if d is None:
         return None
     dram = d["dram_bytes_per_launch"] / kernel_s / 1e9
@@ -521,6 +521,7 @@ def run_uneven(args):
         props = torch.cuda.get_device_properties(dev)
         peak_ops = props.multi_processor_count * ALU_LANES_PER_SM * sm_max * 1e6
         achieved = trials_sum * OPS_PER_TRIAL / (total_ms / 1e3)
+        uprof = _committed_profile("k_simulate_uneven_traffic.json")
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
@@ -539,12 +540,18 @@ def run_uneven(args):
             "mean_steps_per_sim": steps_sum / (n * args.steps),
             "roofline": {"bound": "alu", "achieved": achieved / 1e12,
                          "peak": peak_ops / 1e12, "unit": "Tops/s",
-                         "frac": achieved / peak_ops, "traffic": None,
+                         "frac": achieved / peak_ops,
+                         "traffic": (None if uprof is None
+                                     else uprof["dram_bytes_per_launch"]),
                          "kernel": "k_simulate",
                          "peak_source": f"{props.multi_processor_count} SMs x "
                                         f"{ALU_LANES_PER_SM} lanes x "
                                         f"{sm_max:.0f} MHz ({peaks_kind})",
-                         "ops_per_trial": OPS_PER_TRIAL},
+                         "ops_per_trial": OPS_PER_TRIAL,
+                         "kernel_ms": total_ms / args.steps,
+                         "memory": _memory_roofs(
+                             total_ms / args.steps / 1e3, peaks, peaks_kind,
+                             "k_simulate_uneven_traffic.json")},
             "cpu_baseline": None, "e2e": None,
             "gpu_launches": 5 * args.steps,
             "clocks": ck,
