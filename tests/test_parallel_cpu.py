@@ -137,6 +137,8 @@ def _dying_worker(rank, world, port, q):
         q.put((rank, "no error", time.time() - t0))
     except Exception as e:   # the collective fails instead of hanging
         q.put((rank, type(e).__name__, time.time() - t0))
+    q.close()
+    q.join_thread()          # flush the message before the hard exit
     os._exit(0)
 
 
