@@ -294,7 +294,8 @@ def run_native(args):
     torch.cuda.synchronize()
 
     def step(k):
-        m.simulate_batch(p_dev, g_dev, s_dev[k], device=True, out=outs[k])
+        m.simulate_batch(p_dev, g_dev, s_dev[k], device=True, out=outs[k],
+                         longest_first=True)
         fire.fire_fitness(ctx, outs[k], fire.FITNESS_JACCARD, device=True,
                           out=fit[k])
 
@@ -315,7 +316,8 @@ def run_native(args):
         flush.zero_()
         e0, e1, e2 = ev[j]
         e0.record(stream)
-        m.simulate_batch(p_dev, g_dev, s_dev[k], device=True, out=outs[k])
+        m.simulate_batch(p_dev, g_dev, s_dev[k], device=True, out=outs[k],
+                         longest_first=True)
         e1.record(stream)
         fire.fire_fitness(ctx, outs[k], fire.FITNESS_JACCARD, device=True,
                           out=fit[k])
@@ -357,10 +359,11 @@ def run_native(args):
     e2e_seeds = [torch.from_numpy((wl.seeds + np.uint64((nsteps + j) * SIMS))
                                   .view(np.int64)).pin_memory().numpy()
                  .view(np.uint64) for j in range(e2e_steps)]
-    m.simulate_batch(pin_p, pin_g, e2e_seeds[0])   # warm the staging buffers
+    m.simulate_batch(pin_p, pin_g, e2e_seeds[0],    # warm the staging buffers
+                     longest_first=True)
     t0 = time.perf_counter()
     for j in range(e2e_steps):
-        r, _ = m.simulate_batch(pin_p, pin_g, e2e_seeds[j])
+        r, _ = m.simulate_batch(pin_p, pin_g, e2e_seeds[j], longest_first=True)
         f = fire.fire_fitness(ctx, r, fire.FITNESS_JACCARD)
     e2e_s = time.perf_counter() - t0
     e2e_s = parallel.max_over_ranks(e2e_s, world, dev)
@@ -390,6 +393,8 @@ def run_native(args):
                        "target_cells": int(target.sum()),
                        "l2": "flushed between timed steps (256 MB write)",
                        "parallelism": f"replicas x{world}",
+                       "order": "longest-first by predicted spread "
+                                "(FIRE_LONGEST_FIRST)",
                        "launch": {k: tuned[k] for k in (
                            "warps_per_block", "blocks_per_sm",
                            "queue_entries", "state_mode")}},

@@ -113,6 +113,11 @@ enum {
                                 u < floor((1 - q) 2^32) with q the product of
                                 (1 - p_d) over the burning neighbours in
                                 increasing d, in double precision            */
+#define FIRE_LONGEST_FIRST 128u /* fire_simulate_batch: hand the fires to the
+                                GPU's blocks longest-first, by a key predicted
+                                from each fire's parameters on the map (for
+                                batches larger than the grid, up to 8192
+                                fires); scheduling only, results unchanged   */
 #define FIRE_TC_A_MN 32u      /* fire_tc_gemm: A stored MN-major (A[k][m])   */
 #define FIRE_TC_B_MN 64u      /* fire_tc_gemm: B stored MN-major (B[k][n])   */
 

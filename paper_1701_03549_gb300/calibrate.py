@@ -51,7 +51,7 @@ def evaluate(ctx, m, params_dev, ignition, seeds, reps, kind, torch):
     fit = torch.zeros(n, dtype=torch.float64, device=dev)
     mean = torch.zeros(P, dtype=torch.float64, device=dev)
     torch.cuda.synchronize(dev)
-    m.simulate_batch(p_sims, ign, s, device=True, out=out)
+    m.simulate_batch(p_sims, ign, s, device=True, out=out, longest_first=True)
     fire.fire_fitness(ctx, out, kind, device=True, out=fit)
     fire.fire_group_mean(ctx, fit, reps, device=True, out=mean)
     ctx.sync()
@@ -83,7 +83,7 @@ def evaluate_sharded(ctx, m, params_dev, ignition, seeds, reps, kind, torch,
         out = torch.zeros((k, 6), dtype=torch.int32, device=dev)
         torch.cuda.synchronize(dev)
         m.simulate_batch(p_all[lo:hi].contiguous(), ign, s, device=True,
-                         out=out)
+                         out=out, longest_first=True)
         ctx.sync()
         return fire.results_view(out)
 

@@ -193,6 +193,7 @@ void fire_destroy(fire_ctx *ctx)
     for (GraphEntry &g : ctx->graphs) cudaGraphExecDestroy(g.exec);
     if (ctx->table) cudaFree(ctx->table);
     if (ctx->order) cudaFree(ctx->order);
+    if (ctx->lpt) cudaFree(ctx->lpt);
     if (ctx->counter) cudaFree(ctx->counter);
     if (ctx->staging) cudaFree(ctx->staging);
     if (ctx->gstate) cudaFree(ctx->gstate);
@@ -415,12 +416,25 @@ int launch_batch(fire_ctx *ctx, const fire_map *m, int n,
                          "simulation state");
         if (rc) return rc;
     }
+    // longest-first processing order (scheduling only: every fire's result
+    // depends on its own parameters, ignition and seed alone)
+    const uint32_t *dorder = nullptr;
+    if ((flags & FIRE_LONGEST_FIRST) && n > grid && n <= kLongestFirstMax) {
+        rc = grow_device(ctx, &ctx->lpt, &ctx->lpt_bytes, (size_t)n * 8,
+                         "longest-first order");
+        if (rc) return rc;
+        float *key = (float *)ctx->lpt;
+        uint32_t *ord = (uint32_t *)((char *)ctx->lpt + (size_t)n * 4);
+        cudaError_t e = launch_longest_first(m->dev, n, dparams, key, ord, ctx->stream);
+        if (e != cudaSuccess) return cuda_err(ctx, e, "longest-first order");
+        dorder = ord;
+    }
     SimLaunch a;
     a.map = m->dev;
     a.maps = nullptr;
     a.nmaps = 1;
     a.map_of_sim = nullptr;
-    a.order = nullptr;
+    a.order = dorder;
     a.ntiles_max = ntiles;
     a.n = n;
     a.params = dparams;

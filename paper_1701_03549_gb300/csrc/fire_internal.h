@@ -68,6 +68,9 @@ struct BurnLaunch {
     uint32_t max_steps;        // 0 = no cap
 };
 
+// Largest batch ordered longest-first (the ranking is quadratic in n).
+constexpr int kLongestFirstMax = 8192;
+
 // Cell-flag bits.
 constexpr uint16_t kFlagForest = 1u << 8;
 constexpr uint16_t kFlagBurnable = 1u << 9;
@@ -134,6 +137,8 @@ cudaError_t launch_simulate(const SimLaunch &a, bool smem_state, int nwarps,
 constexpr int kSimMaxThreads = 512;
 const void *simulate_kernel_ptr(bool smem_state);
 cudaError_t launch_burnout(const BurnLaunch &a, int grid, cudaStream_t st);
+cudaError_t launch_longest_first(const MapDev &m, int n, const fire_params *params,
+                                 float *key, uint32_t *order, cudaStream_t st);
 cudaError_t launch_fitness(const fire_result *r, int n, int kind, double *out,
                            cudaStream_t st);
 // Counting sort of simulations by rank[map_of_sim[i]] (counts: nmaps + 1).
@@ -200,6 +205,8 @@ struct fire_ctx {
     size_t table_bytes = 0;
     void *order = nullptr;           // bucket counts + processing order
     size_t order_bytes = 0;
+    void *lpt = nullptr;             // longest-first keys + order (single map)
+    size_t lpt_bytes = 0;
     std::vector<TuneEntry> tuned;    // autotuned launch shapes
     std::vector<GraphEntry> graphs;  // captured calls
     unsigned epoch = 0;              // bumped when a device buffer moves

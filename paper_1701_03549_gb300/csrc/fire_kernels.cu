@@ -952,6 +952,71 @@ __global__ void __launch_bounds__(256) k_burnout(BurnLaunch a)
 }
 
 // ---------------------------------------------------------------------------
+// Longest-first order of a batch (scheduling only).  A fire's work grows with
+// how readily its parameters spread fire on this map, so each fire gets the
+// key: mean over a fixed sample of burnable cells (about 2048, every stride-th
+// cell) of the single-precision probability 1 - prod_d (1 - p_d) that a cell
+// with all eight neighbours burning ignites; fires are then handed to the
+// persistent blocks by decreasing key (ties to the lower index), so the
+// longest fires start first and the launch's tail shrinks.
+__global__ void k_spread_key(MapDev m, int n, const fire_params *__restrict__ params,
+                             long long stride, float *__restrict__ key)
+{
+    const int i = blockIdx.x;
+    if (i >= n) return;
+    const ScreenParams sp = screen_params(params[i].b);
+    const long long HW = (long long)m.H * m.W;
+    float acc = 0.0f;
+    unsigned cnt = 0;
+    for (long long c = (long long)threadIdx.x * stride; c < HW;
+         c += (long long)blockDim.x * stride) {
+        const uint32_t fl = __ldg(&m.cfl[c]);
+        if (!(fl & kFlagBurnable)) continue;
+        const float4 f = __ldg(&m.feat[c]);
+        const float2 wd = __ldg(&m.wdiag[c]);
+        const ScreenCell sc = screen_cell(sp, (fl & kFlagForest) != 0, f.x, f.y, f.z,
+                                          wd.x, f.w, wd.y);
+        float q = 1.0f;
+#pragma unroll
+        for (int d = 0; d < 8; ++d)
+            q *= 1.0f - screen_p(screen_z(sc, sp.b3, (fl >> d) & 1u, d));
+        acc += 1.0f - q;
+        cnt++;
+    }
+    __shared__ float sa[256];
+    __shared__ unsigned sc_[256];
+    sa[threadIdx.x] = acc;
+    sc_[threadIdx.x] = cnt;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+            sa[threadIdx.x] += sa[threadIdx.x + s];
+            sc_[threadIdx.x] += sc_[threadIdx.x + s];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const float k = sc_[0] ? sa[0] / (float)sc_[0] : 0.0f;
+        key[i] = k == k ? k : -1.0f;   // NaN parameters go last
+    }
+}
+
+// order[r] = the fire of rank r by decreasing key (ties: lower index first).
+__global__ void k_rank_desc(int n, const float *__restrict__ key,
+                            uint32_t *__restrict__ order)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float ki = key[i];
+    int r = 0;
+    for (int j = 0; j < n; ++j) {
+        const float kj = key[j];
+        r += (kj > ki) || (kj == ki && j < i);
+    }
+    order[r] = (uint32_t)i;
+}
+
+// ---------------------------------------------------------------------------
 // Fitness of Eq. 2 (kind 0) or Jaccard distance (kind 1).
 __global__ void k_fitness(const fire_result *__restrict__ r, int n, int kind,
                           double *__restrict__ out)
@@ -1212,6 +1277,16 @@ cudaError_t launch_simulate(const SimLaunch &a, bool smem_state, int nwarps,
 cudaError_t launch_burnout(const BurnLaunch &a, int grid, cudaStream_t st)
 {
     k_burnout<<<grid, 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_longest_first(const MapDev &m, int n, const fire_params *params,
+                                 float *key, uint32_t *order, cudaStream_t st)
+{
+    const long long HW = (long long)m.H * m.W;
+    const long long stride = HW > 2048 ? HW / 2048 : 1;
+    k_spread_key<<<n, 256, 0, st>>>(m, n, params, stride, key);
+    k_rank_desc<<<grid_for(n, 256), 256, 0, st>>>(n, key, order);
     return cudaGetLastError();
 }
 

@@ -34,6 +34,7 @@ FIRE_SYNC = 4
 FIRE_GRAPH = 8
 FIRE_CELL_UNIFORM = 16
 FIRE_TC_A_MN = 32
+FIRE_LONGEST_FIRST = 128
 FIRE_TC_B_MN = 64
 
 STATUS_BORDER = 1
@@ -276,7 +277,7 @@ class Map:
 
     def simulate_batch(self, params, ignitions, seeds, want_steps=False,
                        max_steps=0, device=False, out=None, burn_step=None,
-                       sync=False, cell_uniform=False):
+                       sync=False, cell_uniform=False, longest_first=False):
         """fire_simulate_batch.
 
         Host mode: params (n, 5) float64, ignitions (n, 2) int32 (row, col),
@@ -289,6 +290,7 @@ class Map:
         lib = self.ctx.lib
         flags = FIRE_WANT_STEPS if want_steps else 0
         flags |= FIRE_CELL_UNIFORM if cell_uniform else 0
+        flags |= FIRE_LONGEST_FIRST if longest_first else 0
         if device:
             n = int(params.shape[0])
             flags |= FIRE_DEVICE_PTRS | (FIRE_SYNC if sync else 0)

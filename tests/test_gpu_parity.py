@@ -329,3 +329,28 @@ def test_cell_uniform_rule_matches_oracle(ctx, orc, shape, seed):
         assert np.array_equal(bs[i], obs), i
         for k in ("burnt", "inter", "target", "steps", "status", "trials"):
             assert int(res[k][i]) == o[k], (i, k)
+
+
+def test_longest_first_order_changes_no_result():
+    """FIRE_LONGEST_FIRST only reorders how fires are handed to the blocks:
+    every result is the same as in batch order."""
+    import torch
+
+    from paper_1701_03549_gb300 import fire, synth, workloads
+
+    ctx = fire.Context(0)
+    wl = workloads.ga_generation_512(256, 16)
+    m = ctx.landscape_upload(wl.land)
+    m.target_upload(np.zeros(wl.land.veg.shape, bool))
+    dev = torch.device("cuda")
+    p = torch.tensor(wl.params, device=dev)
+    g = torch.tensor(wl.ignitions, device=dev)
+    s = torch.tensor(wl.seeds.view(np.int64), device=dev)
+    a = torch.zeros((4096, 6), dtype=torch.int32, device=dev)
+    b = torch.zeros((4096, 6), dtype=torch.int32, device=dev)
+    torch.cuda.synchronize()
+    m.simulate_batch(p, g, s, device=True, out=a, sync=True)
+    m.simulate_batch(p, g, s, device=True, out=b, sync=True, longest_first=True)
+    assert torch.equal(a, b)
+    m.free()
+    ctx.close()
