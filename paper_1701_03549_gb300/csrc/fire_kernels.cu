@@ -289,14 +289,18 @@ __device__ __forceinline__ bool trial_cell(const SimCtx &s, uint32_t cell,
         if (dec < 0) dec = exact_cell_decide(sh.beta, forest, f, up, dm, u);
         return dec != 0;
     }
+    // The cell ignites iff any trial succeeds, whatever the order they are
+    // tested in; the half with more burning sources goes first, so that the
+    // second Philox block is needed less often.
+    const uint32_t lo = dm & 0x0fu, hi = dm >> 4;
+    const uint32_t first = __popc(hi) > __popc(lo) ? 1u : 0u;
     bool ign = false;
-    if (dm & 0x0fu) {
-        const uint4 u = philox4x32_10(cell, t, 0u, 0u, sh.key0, sh.key1);
-        ign = test_dirs(dm & 0x0fu, 0, u, sc, b3, up, sh.beta, forest, f);
-    }
-    if (!ign && (dm & 0xf0u)) {
-        const uint4 u = philox4x32_10(cell, t, 1u, 0u, sh.key0, sh.key1);
-        ign = test_dirs(dm >> 4, 4, u, sc, b3, up, sh.beta, forest, f);
+    for (uint32_t k = 0; k < 2 && !ign; ++k) {
+        const uint32_t half = first ^ k;
+        const uint32_t m4 = half ? hi : lo;
+        if (!m4) continue;
+        const uint4 u = philox4x32_10(cell, t, half, 0u, sh.key0, sh.key1);
+        ign = test_dirs(m4, (int)(half * 4), u, sc, b3, up, sh.beta, forest, f);
     }
     return ign;
 }
