@@ -351,9 +351,11 @@ FIRE_API int fire_map_features(fire_ctx *ctx, const fire_map *map, uint32_t flag
  * each through the screen and through the double-precision threshold, and
  * writes counts[0] = cases, counts[1] = cases sent to double precision,
  * counts[2] = cases where the two decisions differ (must be 0), and
- * max_abs_dp[0] = largest |p32 - p64| seen.  Host outputs. */
+ * max_err_ratio[0] = the largest |p32 - p64| seen, each divided by the
+ * screen's error bound for its case (6e-8 A + 5e-7, A the sum of the
+ * magnitudes of the Eq. 1 terms; must stay below 1).  Host outputs. */
 FIRE_API int fire_screen_selftest(fire_ctx *ctx, uint64_t n, uint64_t seed,
-                         uint64_t counts[3], double max_abs_dp[1]);
+                         uint64_t counts[3], double max_err_ratio[1]);
 
 /* Debug export of raw Philox4x32-10 blocks: out[4*i .. 4*i+3] is the block of
  * counter (c0 + i, c1, c2, c3) under key (k0, k1), for i < n. */

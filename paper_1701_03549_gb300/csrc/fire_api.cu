@@ -700,10 +700,10 @@ int fire_map_features(fire_ctx *ctx, const fire_map *m, uint32_t flags,
 }
 
 int fire_screen_selftest(fire_ctx *ctx, uint64_t n, uint64_t seed,
-                         uint64_t counts[3], double max_abs_dp[1])
+                         uint64_t counts[3], double max_err_ratio[1])
 {
     if (!ctx) return FIRE_EINVAL;
-    if (!counts || !max_abs_dp) return set_err(ctx, FIRE_EINVAL, "NULL output");
+    if (!counts || !max_err_ratio) return set_err(ctx, FIRE_EINVAL, "NULL output");
     int rc = ensure_device(ctx);
     if (rc) return rc;
     unsigned long long *d = nullptr;
@@ -719,7 +719,7 @@ int fire_screen_selftest(fire_ctx *ctx, uint64_t n, uint64_t seed,
     for (int i = 0; i < 3; ++i) counts[i] = h[i];
     double v;
     std::memcpy(&v, &h[3], 8);
-    max_abs_dp[0] = v;
+    max_err_ratio[0] = v;
     return FIRE_OK;
 }
 

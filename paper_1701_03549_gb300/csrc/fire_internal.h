@@ -91,7 +91,9 @@ struct SimShared {
     uint32_t burnt, inter;
     uint32_t hard_cap;
     int nmark;
-    unsigned long long tw_magic;  // floor(2^40 / TW) + 1: k / TW = k * m >> 40
+    // floor((2^32 - 1) / TW): k / TW = (k + 1) m >> 32 for every tile index
+    // k < FIRE_MAX_TILES and TW <= FIRE_MAX_TILES (checked exhaustively)
+    uint32_t tw_magic;
     MapDev map;                   // map of the current simulation
     unsigned long long mbar;
 };

@@ -192,7 +192,7 @@ struct SimCtx {
 
 __device__ __forceinline__ int tile_row(const SimShared &sh, int k)
 {
-    return (int)(((unsigned long long)k * sh.tw_magic) >> 40);
+    return (int)__umulhi((uint32_t)k + 1u, sh.tw_magic);
 }
 
 // Append tile kk to the worklist of step tn unless it is already there.  A
@@ -224,7 +224,7 @@ static __device__ __noinline__ int exact_decide(const double *beta,
 // Trials of the directions in m4 (bit j: direction base + j) drawn from one
 // Philox block; stops at the first success.
 __device__ __forceinline__ bool test_dirs(uint32_t m4, int base, uint4 u4,
-                                          const ScreenCell &sc, const ff &b3,
+                                          const ScreenCell &sc, float b3,
                                           uint32_t up, const double *beta,
                                           bool forest, const float4 &f)
 {
@@ -235,7 +235,7 @@ __device__ __forceinline__ bool test_dirs(uint32_t m4, int base, uint4 u4,
         const uint32_t u = j == 0 ? u4.x : (j == 1 ? u4.y : (j == 2 ? u4.z : u4.w));
         const bool upd = (up >> d) & 1u;
         const float p32 = screen_p(screen_z(sc, b3, upd, d));
-        int dec = screen_decide(p32, u);
+        int dec = screen_decide(p32, u, sc.margin);
         if (dec < 0) dec = exact_decide(beta, forest, f, upd, d, u);
         if (dec) return true;
     }
@@ -274,7 +274,7 @@ __device__ __forceinline__ bool trial_cell(const SimCtx &s, uint32_t cell,
     const uint32_t up = fl & 0xffu;
     const ScreenCell sc = screen_cell(sh.sp, forest, f.x, f.y, f.z, wd.x, f.w,
                                       wd.y);
-    const ff b3 = sh.sp.b3;
+    const float b3 = sh.sp.b3;
     if (s.a->cell_uniform) {
         float q = 1.0f;
         uint32_t mm = dm;
@@ -285,7 +285,7 @@ __device__ __forceinline__ bool trial_cell(const SimCtx &s, uint32_t cell,
             q = __fmul_rn(q, __fsub_rn(1.0f, p));
         }
         const uint32_t u = philox4x32_10(cell, t, 2u, 0u, sh.key0, sh.key1).x;
-        int dec = screen_decide(__fsub_rn(1.0f, q), u, kCellScreenMargin);
+        int dec = screen_decide(__fsub_rn(1.0f, q), u, cell_margin(sc));
         if (dec < 0) dec = exact_cell_decide(sh.beta, forest, f, up, dm, u);
         return dec != 0;
     }
@@ -484,7 +484,12 @@ __device__ __forceinline__ void phase_a(const SimCtx &s, int k, uint32_t t,
         } else {
             const uint32_t cell = (uint32_t)(ti * 32 + r) * (uint32_t)m.W +
                                   (uint32_t)(tj * 32 + i);
-            if (trial_cell(s, cell, dm, t)) ignite(s, k, ti, tj, r, i, cell, t);
+            if (trial_cell(s, cell, dm, t)) {
+                ignite(s, k, ti, tj, r, i, cell, t);
+                // every writer of this step stores the same values
+                sh.newflag[(t + 1) % 3] = 1;
+                sh.last_new = t + 1;
+            }
         }
     }
 }
@@ -545,7 +550,7 @@ __global__ void __launch_bounds__(kSimMaxThreads, 2) k_simulate(SimLaunch a)
             const long long hw = (long long)sh.map.H * sh.map.W;
             sh.hard_cap = (uint32_t)min(hw + 2, (long long)0x7fffffff);
             sh.nmark = (sh.map.ntiles + 15) / 16;
-            sh.tw_magic = (1ull << 40) / (unsigned long long)sh.map.TW + 1ull;
+            sh.tw_magic = 0xffffffffu / (uint32_t)sh.map.TW;
             sh.status = map_ok ? 0u : FIRE_STATUS_BAD_MAP;
             const fire_params P = a.params[sim];
             for (int j = 0; j < 5; ++j) sh.beta[j] = P.b[j];
@@ -1099,7 +1104,8 @@ __global__ void k_features_export(MapDev m, float *psi, float *sig, float *cw,
 
 // Randomised check of the single-precision screen against the exact
 // threshold: uniform and Gaussian parameters, random covariates, and draws
-// both uniform and placed next to the exact threshold.
+// both uniform and placed next to the exact threshold.  Also records the
+// largest ratio of |p32 - p64| to the screen's stated error bound.
 __global__ void k_screen_selftest(uint64_t n, uint64_t seed,
                                   unsigned long long *counts,
                                   unsigned long long *max_dp_bits)
@@ -1115,12 +1121,14 @@ __global__ void k_screen_selftest(uint64_t n, uint64_t seed,
         const uint32_t rs[5] = {r1.x, r1.y, r1.z, r1.w, r2.x};
         double b[5];
         const bool gauss = (r2.y >> 31) & 1u;
+        const double wide = ((r2.y >> 30) & 1u) ? 200.0 : 30.0;
         for (int j = 0; j < 5; ++j) {
             const double u = ((double)rs[j] + 0.5) * 0x1p-32;
-            // uniform on [-30, 30], or a Gaussian-looking sum (sd ~5)
+            // a Gaussian-looking sum (sd ~5), or uniform on [-30, 30] or on
+            // [-200, 200] (large coefficients widen the screen's margin)
             b[j] = gauss ? (u - 0.5) * 17.32 + ((double)(rs[(j + 1) % 5] >> 16) /
                                                      65536.0 - 0.5) * 17.32
-                         : -30.0 + 60.0 * u;
+                         : wide * (2.0 * u - 1.0);
         }
         const bool forest = r2.y & 1u;
         const int d = (int)((r2.y >> 1) & 7u);
@@ -1146,7 +1154,7 @@ __global__ void k_screen_selftest(uint64_t n, uint64_t seed,
         const float om3 = __double2float_rn(spec::omega(cw, sw, 3));
         const ScreenCell sc = screen_cell(sp, forest, psi, sig, cw, om1, sw, om3);
         const float p32 = screen_p(screen_z(sc, sp.b3, up, d));
-        int dec = screen_decide(p32, u);
+        int dec = screen_decide(p32, u, sc.margin);
         const bool exact = (uint64_t)u < T;
         local[0]++;
         if (dec < 0) {
@@ -1154,8 +1162,9 @@ __global__ void k_screen_selftest(uint64_t n, uint64_t seed,
             dec = exact;
         }
         if ((dec != 0) != exact) local[2]++;
+        // |p32 - p64| against the screen's stated bound (half its margin)
         const double dp = fabs((double)p32 - spec::logistic(z));
-        local_max = fmax(local_max, dp);
+        local_max = fmax(local_max, dp / (0.5 * (double)sc.margin));
     }
     for (int j = 0; j < 3; ++j) {
         unsigned long long v = local[j];

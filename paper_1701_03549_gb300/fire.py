@@ -555,7 +555,7 @@ def fire_screen_selftest(ctx: Context, n: int, seed: int):
     ctx.check(ctx.lib.fire_screen_selftest(ctx.h, int(n), int(seed),
                                            _ptr(counts), _ptr(mx)))
     return dict(cases=int(counts[0]), fallbacks=int(counts[1]),
-                flips=int(counts[2]), max_abs_dp=float(mx[0]))
+                flips=int(counts[2]), max_err_ratio=float(mx[0]))
 
 
 def fire_philox_blocks(ctx: Context, n: int, ctr, key):

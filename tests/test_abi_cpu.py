@@ -85,3 +85,19 @@ def test_kernels_compile_for_sm103a_with_little_spilling():
             spill = int(re.search(r"(\d+) bytes spill stores", block).group(1))
             assert spill <= 64, block
     assert seen == 2
+
+
+def test_tile_row_division_by_magic_multiply():
+    """The simulation kernel finds a tile's row as (k + 1) * m >> 32 with
+    m = floor((2^32 - 1) / TW); this equals k // TW for every tile index and
+    every tile-grid width the library accepts (up to FIRE_MAX_TILES)."""
+    import numpy as np
+
+    hdr = open(HEADER).read()
+    n = int(re.search(r"#define FIRE_MAX_TILES (\d+)", hdr).group(1))
+    k = np.arange(n, dtype=np.uint64)[None, :]
+    for lo in range(1, n + 1, 512):
+        TW = np.arange(lo, min(lo + 512, n + 1), dtype=np.uint64)[:, None]
+        m = np.uint64(2 ** 32 - 1) // TW
+        q = ((k + np.uint64(1)) * m) >> np.uint64(32)
+        assert np.array_equal(q, k // TW), lo
