@@ -35,9 +35,11 @@ METRIC = "CA sims/s"
 UNIT = "sims/s"
 POP, REPS = 256, 16
 SIMS = POP * REPS
-# Algorithmic operations of one trial (one Philox4x32-10 output word plus the
-# screened threshold decision): see the roofline section of the design notes.
-OPS_PER_TRIAL = 37
+# Algorithmic operations of one trial: one Philox4x32-10 output word (10
+# rounds of 8 integer operations per 4-word block: 20) plus Eq. 1 for one
+# direction and its comparison with the draw (the five-term sum as 4 FMAs,
+# exponential 2, 1 + e 1, reciprocal 1, draw to float 2, compare 1: 11).
+OPS_PER_TRIAL = 31
 ALU_LANES_PER_SM = 128
 WORKLOAD = ("ga_generation_512: 512x512 map, 256 Gauss(0,5) parameter "
             "vectors x 16 replicates = 4096 simulations/step, centre "

@@ -352,8 +352,8 @@ FIRE_API int fire_map_features(fire_ctx *ctx, const fire_map *map, uint32_t flag
  * writes counts[0] = cases, counts[1] = cases sent to double precision,
  * counts[2] = cases where the two decisions differ (must be 0), and
  * max_err_ratio[0] = the largest |p32 - p64| seen, each divided by the
- * screen's error bound for its case (6e-8 A + 5e-7, A the sum of the
- * magnitudes of the Eq. 1 terms; must stay below 1).  Host outputs. */
+ * screen's error bound for its case (7.5e-9 |b3| + 5e-7, within 1e-6 for
+ * |b3| <= 66; must stay below 1).  Host outputs. */
 FIRE_API int fire_screen_selftest(fire_ctx *ctx, uint64_t n, uint64_t seed,
                          uint64_t counts[3], double max_err_ratio[1]);
 

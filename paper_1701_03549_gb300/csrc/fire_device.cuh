@@ -223,55 +223,105 @@ __device__ __forceinline__ double z_of(const double b[5], bool forest,
 }  // namespace spec
 
 // ---------------------------------------------------------------------------
-// Single-precision screen of a trial.  z is evaluated in float by three fused
-// multiply-adds from the Eq. 1 coefficients rounded to float:
-//   base  = b2 psi + K        (K = b0, or b0 + b1 on forest cells),
-//   baseG = b4 sig + base     (the slope term, uphill targets only),
-//   z     = b3 om_d + (up ? baseG : base),
-// om_d = +-cos / sin of the wind bearing or the diagonal cosines rounded to
-// float at upload.  Error against the double-precision z of Eq. 1, with
-// A = |K| + |b2 psi| + |b4 sig| + |b3| (|om_d| <= 1): each coefficient rounds
-// once (2^-24 of its term), each FMA rounds once (2^-24 of a result bounded
-// by the running sum of term magnitudes), the diagonal cosines carry 2^-25;
-// the sum stays below 4 A 2^-24 = 2^-22 A, and the double-precision
-// evaluation of Eq. 1 below 2^-50 A.  p = 1 / (1 + e^-z) then moves by at
-// most a quarter of that (p(1-p) <= 1/4): 6e-8 A.  The rest is independent
-// of A: the argument scaling of the hardware exponential (max_z z p(1-p) <
-// 0.23, times 2^-24), the exponential itself (relative 2^-21 at most, times
-// p(1-p)), the rounding of 1 + e (2^-24) and the approximate reciprocal
-// (2^-23), plus the float conversion of the draw (below 2^-24): 3.7e-7 in
-// all, taken as 5e-7.  A trial is decided in single precision when
-// |p32 - (u + 1) 2^-32| exceeds twice that bound and otherwise re-decided
+// Single-precision screen.  z is accumulated as an unevaluated float pair
+// (hi + lo, error-free products by FMA and two-sums, error below 2^-44 of
+// the term magnitudes), so the roundings left are that of the diagonal wind
+// cosines (|b3| 2^-25 in z), of z to float (relative 2^-24), of the
+// exponential and of the reciprocal.  p = 1 / (1 + e^-z) moves by p(1-p)
+// times the z error, p(1-p) <= 1/4 and max_z z p(1-p) < 0.23: |b3| 2^-27
+// plus 0.23 2^-24.  The hardware exponential (its argument scaling 0.23
+// 2^-24, relative error 2^-21 times p(1-p)), the rounding of 1 + e (2^-24),
+// the approximate reciprocal (2^-23) and the float conversion of the draw
+// (2^-24) add 3.1e-7.  So |p32 - p64| <= kScreenErrB3 |b3| + kScreenErr0,
+// within 1e-6 for |b3| <= 66.  A trial is decided in single precision when
+// |p32 - (u + 1) 2^-32| exceeds the simulation's margin, twice that bound
+// and at least 4e-6 (4e-6 for every |b3| <= 200), and otherwise re-decided
 // through the exact double-precision threshold (success <=> u <
 // floor(p 2^32) <=> (u + 1) 2^-32 <= p64).
-constexpr float kScreenErrA = 6.0e-8f;   // per unit of A
+constexpr float kScreenErrB3 = 7.5e-9f;   // per unit of |b3|
 constexpr float kScreenErr0 = 5.0e-7f;
+constexpr float kScreenMarginMin = 4.0e-6f;
+
+struct ff { float h, l; };
+
+__device__ __forceinline__ ff ff_from_double(double x)
+{
+    const float h = __double2float_rn(x);
+    const float l = __double2float_rn(__dsub_rn(x, (double)h));
+    return {h, l};
+}
+
+// (a.h + a.l) * b, unnormalised; error below 2^-46 |a b|.
+__device__ __forceinline__ ff ff_mul_f(ff a, float b)
+{
+    const float h = __fmul_rn(a.h, b);
+    float l = __fmaf_rn(a.h, b, -h);
+    l = __fmaf_rn(a.l, b, l);
+    return {h, l};
+}
+
+__device__ __forceinline__ ff ff_add(ff a, ff b)
+{
+    const float s = __fadd_rn(a.h, b.h);
+    const float bb = __fsub_rn(s, a.h);
+    const float e = __fadd_rn(__fsub_rn(a.h, __fsub_rn(s, bb)),
+                              __fsub_rn(b.h, bb));
+    const float l = __fadd_rn(e, __fadd_rn(a.l, b.l));
+    const float h = __fadd_rn(s, l);
+    return {h, __fsub_rn(l, __fsub_rn(h, s))};
+}
+
+__device__ __forceinline__ ff ff_neg(ff a) { return {-a.h, -a.l}; }
+
+// (a.h + a.l) * (sqrt(2) / 2) with the constant as a float pair.
+__device__ __forceinline__ ff ff_mul_r2(ff a)
+{
+    constexpr float r2h = 0x1.6a09e6p-1f;
+    constexpr float r2l = 0x1.9fcef4p-27f;  // sqrt(2)/2 - r2h
+    const float h = __fmul_rn(a.h, r2h);
+    float l = __fmaf_rn(a.h, r2h, -h);
+    l = __fmaf_rn(a.h, r2l, l);
+    l = __fmaf_rn(a.l, r2h, l);
+    return {h, l};
+}
 
 // Per-parameter-set constants of the screen.
 struct ScreenParams {
-    float K[2];   // b0 + b1 * If for If = 0, 1 (the sum in double, then rounded)
-    float b2, b3, b4;
+    ff K[2];   // b0 + b1 * If for If = 0, 1
+    ff b2, b3, b4;
+    float margin;        // trial margin: max(2 err, 4e-6)
+    float cell_margin;   // one-uniform-per-cell margin (below)
 };
 
 __device__ __forceinline__ ScreenParams screen_params(const double b[5])
 {
     ScreenParams s;
-    s.K[0] = __double2float_rn(b[0]);
-    s.K[1] = __double2float_rn(__dadd_rn(b[0], b[1]));
-    s.b2 = __double2float_rn(b[2]);
-    s.b3 = __double2float_rn(b[3]);
-    s.b4 = __double2float_rn(b[4]);
+    s.K[0] = ff_from_double(b[0]);
+    s.K[1] = ff_from_double(__dadd_rn(b[0], b[1]));
+    s.b2 = ff_from_double(b[2]);
+    s.b3 = ff_from_double(b[3]);
+    s.b4 = ff_from_double(b[4]);
+    // err = kScreenErrB3 |b3| + kScreenErr0, rounded upwards
+    const float err = __fmaf_ru(kScreenErrB3, __double2float_ru(fabs(b[3])),
+                                kScreenErr0);
+    s.margin = fmaxf(2.0f * err, kScreenMarginMin);
+    // 1 - prod(1 - p_d) over up to 8 directions accumulates at most 8
+    // per-direction errors and 17 float roundings of values at most 1 (below
+    // 1.1e-6); doubled like the trial margin, and at least 2.5e-5
+    s.cell_margin = fmaxf(__fmaf_ru(16.0f, err, 2.2e-6f), 2.5e-5f);
+    if (err != err) s.margin = s.cell_margin = INFINITY;   // NaN b3: never decide
     return s;
 }
 
-// Per-target-cell part of the screen: the direction-independent sums with
-// and without the slope term, the wind cosines of directions 0..3
-// (directions 4..7 use their negatives) and the decision margin
-// 2 (kScreenErrA A + kScreenErr0).
+// Per-target-cell partial sums of z: the direction-independent part with and
+// without the slope term, and cos(phi_w - 45 j) for j = 0..3 (directions
+// 4..7 use their negatives).  The diagonal cosines are the double-precision
+// omega of the threshold definition rounded to float at upload, which adds at
+// most |b3| 2^-25 to z.
 struct ScreenCell {
-    float base, baseG;
+    ff base;    // b0 + b1 If + b2 psi
+    ff baseG;   // base + b4 sig
     float om0, om1, om2, om3;
-    float margin;
 };
 
 __device__ __forceinline__ ScreenCell screen_cell(const ScreenParams &sp,
@@ -281,46 +331,33 @@ __device__ __forceinline__ ScreenCell screen_cell(const ScreenParams &sp,
                                                   float om3)
 {
     ScreenCell c;
-    const float K = forest ? sp.K[1] : sp.K[0];
-    c.base = __fmaf_rn(sp.b2, psi, K);
-    c.baseG = __fmaf_rn(sp.b4, sig, c.base);
+    c.base = ff_add(sp.K[forest ? 1 : 0], ff_mul_f(sp.b2, psi));
+    c.baseG = ff_add(c.base, ff_mul_f(sp.b4, sig));
     c.om0 = cw;
     c.om1 = om1;
     c.om2 = sw;
     c.om3 = om3;
-    // three roundings of A (relative 2^-22 at most) are within the factor 2
-    const float A = __fadd_rn(__fmaf_rn(fabsf(sp.b2), fabsf(psi), fabsf(K)),
-                              __fmaf_rn(fabsf(sp.b4), fabsf(sig), fabsf(sp.b3)));
-    c.margin = __fmaf_rn(2.0f * kScreenErrA, A, 2.0f * kScreenErr0);
     return c;
 }
 
-// z of direction d (up: target above the source).
-__device__ __forceinline__ float screen_z(const ScreenCell &c, float b3,
+// z of direction d (up: target above the source), rounded to float.
+__device__ __forceinline__ float screen_z(const ScreenCell &c, const ff &b3,
                                          bool up, int d)
 {
     const int j = d & 3;
     float om = j == 0 ? c.om0 : (j == 1 ? c.om1 : (j == 2 ? c.om2 : c.om3));
     if (d & 4) om = -om;
-    return __fmaf_rn(b3, om, up ? c.baseG : c.base);
+    return ff_add(up ? c.baseG : c.base, ff_mul_f(b3, om)).h;
 }
 
-// p = 1 / (1 + e^-z) with the hardware exponential and reciprocal.
+// p = 1 / (1 + e^-z) with the hardware exponential and reciprocal (each
+// within a few ulp; the margin above covers them with a factor 10).
 __device__ __forceinline__ float screen_p(float z)
 {
     const float e = __expf(-z);
     float r;
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(__fadd_rn(1.0f, e)));
     return r;
-}
-
-// Margin of the one-uniform-per-cell rule: 1 - prod(1 - p_d) over up to 8
-// directions accumulates at most 8 per-direction errors (each below half the
-// trial margin) and 17 float roundings of values at most 1 (below 1.1e-6),
-// doubled like the trial margin.
-__device__ __forceinline__ float cell_margin(const ScreenCell &c)
-{
-    return __fmaf_rn(8.0f, c.margin, 2.2e-6f);
 }
 
 // Decision of the trial with draw u.  Returns 1 success, 0 failure, -1 when

@@ -224,9 +224,10 @@ static __device__ __noinline__ int exact_decide(const double *beta,
 // Trials of the directions in m4 (bit j: direction base + j) drawn from one
 // Philox block; stops at the first success.
 __device__ __forceinline__ bool test_dirs(uint32_t m4, int base, uint4 u4,
-                                          const ScreenCell &sc, float b3,
-                                          uint32_t up, const double *beta,
-                                          bool forest, const float4 &f)
+                                          const ScreenCell &sc, const ff &b3,
+                                          float margin, uint32_t up,
+                                          const double *beta, bool forest,
+                                          const float4 &f)
 {
     while (m4) {
         const int j = __ffs(m4) - 1;
@@ -235,7 +236,7 @@ __device__ __forceinline__ bool test_dirs(uint32_t m4, int base, uint4 u4,
         const uint32_t u = j == 0 ? u4.x : (j == 1 ? u4.y : (j == 2 ? u4.z : u4.w));
         const bool upd = (up >> d) & 1u;
         const float p32 = screen_p(screen_z(sc, b3, upd, d));
-        int dec = screen_decide(p32, u, sc.margin);
+        int dec = screen_decide(p32, u, margin);
         if (dec < 0) dec = exact_decide(beta, forest, f, upd, d, u);
         if (dec) return true;
     }
@@ -274,7 +275,7 @@ __device__ __forceinline__ bool trial_cell(const SimCtx &s, uint32_t cell,
     const uint32_t up = fl & 0xffu;
     const ScreenCell sc = screen_cell(sh.sp, forest, f.x, f.y, f.z, wd.x, f.w,
                                       wd.y);
-    const float b3 = sh.sp.b3;
+    const ff b3 = sh.sp.b3;
     if (s.a->cell_uniform) {
         float q = 1.0f;
         uint32_t mm = dm;
@@ -285,7 +286,7 @@ __device__ __forceinline__ bool trial_cell(const SimCtx &s, uint32_t cell,
             q = __fmul_rn(q, __fsub_rn(1.0f, p));
         }
         const uint32_t u = philox4x32_10(cell, t, 2u, 0u, sh.key0, sh.key1).x;
-        int dec = screen_decide(__fsub_rn(1.0f, q), u, cell_margin(sc));
+        int dec = screen_decide(__fsub_rn(1.0f, q), u, sh.sp.cell_margin);
         if (dec < 0) dec = exact_cell_decide(sh.beta, forest, f, up, dm, u);
         return dec != 0;
     }
@@ -300,7 +301,8 @@ __device__ __forceinline__ bool trial_cell(const SimCtx &s, uint32_t cell,
         const uint32_t m4 = half ? hi : lo;
         if (!m4) continue;
         const uint4 u = philox4x32_10(cell, t, half, 0u, sh.key0, sh.key1);
-        ign = test_dirs(m4, (int)(half * 4), u, sc, b3, up, sh.beta, forest, f);
+        ign = test_dirs(m4, (int)(half * 4), u, sc, b3, sh.sp.margin, up,
+                        sh.beta, forest, f);
     }
     return ign;
 }
@@ -772,11 +774,13 @@ __device__ __forceinline__ bool burnout_decide(const MapDev &m,
     bool ign = false;
     if (dm & 0x0fu) {
         const uint4 u = philox4x32_10(cell, t, 0u, 0u, key0, key1);
-        ign = test_dirs(dm & 0x0fu, 0, u, sc, sp.b3, up, beta, forest, f);
+        ign = test_dirs(dm & 0x0fu, 0, u, sc, sp.b3, sp.margin, up, beta,
+                        forest, f);
     }
     if (!ign && (dm & 0xf0u)) {
         const uint4 u = philox4x32_10(cell, t, 1u, 0u, key0, key1);
-        ign = test_dirs(dm >> 4, 4, u, sc, sp.b3, up, beta, forest, f);
+        ign = test_dirs(dm >> 4, 4, u, sc, sp.b3, sp.margin, up, beta,
+                        forest, f);
     }
     return ign;
 }
@@ -1125,7 +1129,7 @@ __global__ void k_screen_selftest(uint64_t n, uint64_t seed,
         for (int j = 0; j < 5; ++j) {
             const double u = ((double)rs[j] + 0.5) * 0x1p-32;
             // a Gaussian-looking sum (sd ~5), or uniform on [-30, 30] or on
-            // [-200, 200] (large coefficients widen the screen's margin)
+            // [-200, 200] (a large |b3| widens the screen's margin)
             b[j] = gauss ? (u - 0.5) * 17.32 + ((double)(rs[(j + 1) % 5] >> 16) /
                                                      65536.0 - 0.5) * 17.32
                          : wide * (2.0 * u - 1.0);
@@ -1154,7 +1158,7 @@ __global__ void k_screen_selftest(uint64_t n, uint64_t seed,
         const float om3 = __double2float_rn(spec::omega(cw, sw, 3));
         const ScreenCell sc = screen_cell(sp, forest, psi, sig, cw, om1, sw, om3);
         const float p32 = screen_p(screen_z(sc, sp.b3, up, d));
-        int dec = screen_decide(p32, u, sc.margin);
+        int dec = screen_decide(p32, u, sp.margin);
         const bool exact = (uint64_t)u < T;
         local[0]++;
         if (dec < 0) {
@@ -1162,9 +1166,10 @@ __global__ void k_screen_selftest(uint64_t n, uint64_t seed,
             dec = exact;
         }
         if ((dec != 0) != exact) local[2]++;
-        // |p32 - p64| against the screen's stated bound (half its margin)
+        // |p32 - p64| against the screen's stated bound
         const double dp = fabs((double)p32 - spec::logistic(z));
-        local_max = fmax(local_max, dp / (0.5 * (double)sc.margin));
+        local_max = fmax(local_max,
+                         dp / ((double)kScreenErrB3 * fabs(b[3]) + kScreenErr0));
     }
     for (int j = 0; j < 3; ++j) {
         unsigned long long v = local[j];
