@@ -357,7 +357,7 @@ __device__ __forceinline__ uint32_t dir_bits(const uint32_t md[8], int i)
 // previous step's burning cells, find the targets with a burning source in
 // each direction, count the trials and queue the candidates for phase B.
 __device__ __forceinline__ void phase_a(const SimCtx &s, int k, uint32_t t,
-                                        int lane)
+                                        int lane, uint32_t &ntrials)
 {
     const SimLaunch &a = *s.a;
     const MapDev &m = *s.map;
@@ -431,15 +431,12 @@ __device__ __forceinline__ void phase_a(const SimCtx &s, int k, uint32_t t,
     md[5] = (bu >> 1) | (bru << 31);          // SW: source above-right
     md[6] = (b >> 1) | (br << 31);            // W : source right
     md[7] = (bd >> 1) | (brd << 31);          // NW: source below-right
-    uint32_t cand = 0, ntr = 0;
+    uint32_t cand = 0;
 #pragma unroll
     for (int d = 0; d < 8; ++d) {
         md[d] &= avail;
         cand |= md[d];
-        ntr += __popc(md[d]);
     }
-    const uint32_t trw = __reduce_add_sync(kFull, ntr);
-    if (lane == 0 && trw) atomicAdd(&sh.trials, trw);
     const uint32_t c = __popc(cand);
     uint32_t incl = c;
 #pragma unroll
@@ -486,6 +483,7 @@ __device__ __forceinline__ void phase_a(const SimCtx &s, int k, uint32_t t,
         } else {
             const uint32_t cell = (uint32_t)(ti * 32 + r) * (uint32_t)m.W +
                                   (uint32_t)(tj * 32 + i);
+            ntrials += (uint32_t)__popc(dm);
             if (trial_cell(s, cell, dm, t)) {
                 ignite(s, k, ti, tj, r, i, cell, t);
                 // every writer of this step stores the same values
@@ -500,10 +498,10 @@ template <bool kSmemState>
 __global__ void __launch_bounds__(kSimMaxThreads, 2) k_simulate(SimLaunch a)
 {
     extern __shared__ __align__(128) unsigned char smem[];
-    const int nwarps = blockDim.x >> 5;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int ntiles_max = a.ntiles_max;
     const SimLayout L = sim_layout(ntiles_max, a.qcap, kSmemState);
+    const int nwarps = blockDim.x >> 5;
     SimShared &sh = *reinterpret_cast<SimShared *>(smem + L.header);
     const MapDev &m = sh.map;
     SimCtx s;
@@ -661,6 +659,9 @@ __global__ void __launch_bounds__(kSimMaxThreads, 2) k_simulate(SimLaunch a)
         // --- steps: phase A (tiles) | barrier | phase B (trials) | barrier
         uint32_t t = 0;
         bool capped = false;
+        // trials of the candidates this thread decides (each candidate is
+        // decided once, in phase B or, after a queue overflow, in phase A)
+        uint32_t ntrials = 0;
         for (;; ++t) {
             __syncthreads();
             const uint32_t nA = sh.count[t % 3];
@@ -676,7 +677,7 @@ __global__ void __launch_bounds__(kSimMaxThreads, 2) k_simulate(SimLaunch a)
             }
             const uint16_t *list = s.lists + (t % 3) * ntiles_max;
             for (uint32_t li = warp; li < nA; li += nwarps)
-                phase_a(s, list[li], t, lane);
+                phase_a(s, list[li], t, lane, ntrials);
             __syncthreads();
             const uint32_t par = t & 1u;
             const uint32_t nq = min(sh.qcount[par], sh.qvalid[par]);
@@ -693,6 +694,7 @@ __global__ void __launch_bounds__(kSimMaxThreads, 2) k_simulate(SimLaunch a)
                 const int ti = tile_row(sh, k), tj = k - ti * m.TW;
                 const uint32_t cell = (uint32_t)(ti * 32 + r) * (uint32_t)m.W +
                                       (uint32_t)(tj * 32 + i);
+                ntrials += (uint32_t)__popc(e & 0xffu);
                 if (trial_cell(s, cell, e & 0xffu, t)) {
                     ignite(s, k, ti, tj, r, i, cell, t);
                     any = true;
@@ -724,8 +726,10 @@ __global__ void __launch_bounds__(kSimMaxThreads, 2) k_simulate(SimLaunch a)
         }
         nb = __reduce_add_sync(kFull, nb);
         ni = __reduce_add_sync(kFull, ni);
+        ntrials = __reduce_add_sync(kFull, ntrials);
         border = __any_sync(kFull, border);
         if (lane == 0) {
+            if (ntrials) atomicAdd(&sh.trials, ntrials);
             if (nb) atomicAdd(&sh.burnt, nb);
             if (ni) atomicAdd(&sh.inter, ni);
             if (border) atomicOr(&sh.status, FIRE_STATUS_BORDER);
