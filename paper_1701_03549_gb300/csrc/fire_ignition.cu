@@ -46,7 +46,10 @@ __global__ void k_snap(MapDev m, const int *__restrict__ bbox, int LH, int LW,
     const int r0 = bbox[0], r1 = bbox[1], c0 = bbox[2], c1 = bbox[3];
     const long long R = r0 + ((2LL * a + 1) * (r1 - r0 + 1)) / (2LL * LH);
     const long long C = c0 + ((2LL * b + 1) * (c1 - c0 + 1)) / (2LL * LW);
-    unsigned long long best = ~0ull;   // (distance^2 << 32) | cell index
+    // nearest = least (squared distance, row-major index); the distance can
+    // exceed 32 bits on wide maps, so the pair is compared field by field
+    unsigned long long bd = ~0ull;
+    uint32_t bi = 0xffffffffu;
     const int nw = m.ntiles * 32;
     for (int w = threadIdx.x; w < nw; w += blockDim.x) {
         uint32_t t = m.tgt[w] & ~m.blk[w];
@@ -59,26 +62,36 @@ __global__ void k_snap(MapDev m, const int *__restrict__ bbox, int LH, int LW,
             const long long Cc = tj * 32 + i;
             const unsigned long long d = (unsigned long long)(
                 (Rw - R) * (Rw - R) + (Cc - C) * (Cc - C));
-            const unsigned long long key =
-                (d << 32) | (unsigned long long)(Rw * m.W + Cc);
-            if (key < best) best = key;
+            const uint32_t idx = (uint32_t)(Rw * m.W + Cc);
+            if (d < bd || (d == bd && idx < bi)) {
+                bd = d;
+                bi = idx;
+            }
         }
     }
-    __shared__ unsigned long long red[256];
-    red[threadIdx.x] = best;
+    __shared__ unsigned long long rd[256];
+    __shared__ uint32_t ri[256];
+    rd[threadIdx.x] = bd;
+    ri[threadIdx.x] = bi;
     __syncthreads();
     for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s && red[threadIdx.x + s] < red[threadIdx.x])
-            red[threadIdx.x] = red[threadIdx.x + s];
+        if (threadIdx.x < s) {
+            const unsigned long long d2 = rd[threadIdx.x + s];
+            const uint32_t i2 = ri[threadIdx.x + s];
+            if (d2 < rd[threadIdx.x] ||
+                (d2 == rd[threadIdx.x] && i2 < ri[threadIdx.x])) {
+                rd[threadIdx.x] = d2;
+                ri[threadIdx.x] = i2;
+            }
+        }
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        const unsigned long long key = red[0];
-        if (key == ~0ull) {
+        if (rd[0] == ~0ull) {
             atomicOr(fail, 1);
             cells[2 * cidx] = cells[2 * cidx + 1] = 0;
         } else {
-            const long long cell = (long long)(key & 0xffffffffull);
+            const long long cell = (long long)ri[0];
             cells[2 * cidx] = (int32_t)(cell / m.W);
             cells[2 * cidx + 1] = (int32_t)(cell % m.W);
         }

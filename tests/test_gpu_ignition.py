@@ -57,3 +57,26 @@ def test_ignition_search_rejects_empty_target(env):
         fire.ignition_search(ctx, m, synth.TRUTH_BETA, 2, 2, 1, 1)
     assert e.value.code == fire.FIRE_EINVAL
     m.free()
+
+
+def test_nearest_cell_on_a_wide_map(env):
+    """On a 32 x 131072 map the squared distance from the lattice point to a
+    target cell exceeds 2^32: the nearest burnt cell must still win (a 64-bit
+    key holding the distance above the cell index would wrap here)."""
+    fire, oracle, ctx = env
+    H, W = 32, 131072
+    land = synth.uniform_landscape(H, W)
+    target = np.zeros((H, W), bool)
+    target[5, 0] = True          # distance^2 = 8^2 + 65536^2 > 2^32
+    target[20, W - 1] = True     # distance^2 = 7^2 + 65535^2 < 2^32
+    beta = np.array([-1000.0, 0.0, 0.0, 0.0, 0.0])   # burns the ignition only
+    m = ctx.landscape_upload(land)
+    m.target_upload(target)
+    fm, cells, xy = fire.ignition_search(ctx, m, beta, 1, 1, 1, 5, 0, 1.5)
+    assert cells[0, 0].tolist() == [20, W - 1]
+    F = oracle.Features(land)
+    ofm, ocells, oxy = F.ignition_search(target, beta, 1, 1, 1, 5, 0, 1.5)
+    assert np.array_equal(cells, ocells)
+    assert np.array_equal(fm, ofm)
+    assert np.array_equal(xy, oxy)
+    m.free()
