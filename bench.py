@@ -278,10 +278,11 @@ def run_native(args):
 
     tseed, target = workloads.pick_target(sim_target, burnable)
     m.target_upload(target)
-    # launch shape: the autotuner times its candidate shapes on this batch
-    # (outside the timed region) and the library uses the fastest
+    # launch shape: the autotuner times its candidate shapes on this batch in
+    # the step's longest-first order (outside the timed region) and the
+    # library uses the fastest
     tuned = fire.fire_autotune(ctx, [m], None, wl.params, wl.ignitions,
-                               wl.seeds)
+                               wl.seeds, longest_first=True)
 
     nsteps = args.warmup + args.steps
     p_dev = torch.tensor(wl.params, dtype=torch.float64, device=dev)

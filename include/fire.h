@@ -264,8 +264,12 @@ typedef struct {
  * fixed list of launch shapes (warps per block, blocks per SM, queue
  * capacity, state placement), record the fastest for this largest-map tile
  * count in the context, and return it.  Later calls without an explicit
- * fire_set_launch override use it; results never depend on it.  Runs the
- * batch about twenty times. */
+ * fire_set_launch override use it; results never depend on it.  flags:
+ * FIRE_DEVICE_PTRS, and FIRE_LONGEST_FIRST (nmaps = 1 only, else FIRE_EINVAL;
+ * map_of_sim is then ignored) to time the shapes as fire_simulate_batch runs
+ * with that flag.  Each shape
+ * runs once untimed and twice timed (the better time counts): the batch runs
+ * about thirty times. */
 FIRE_API int fire_autotune(fire_ctx *ctx, int nmaps, const fire_map *const *maps,
                            const int32_t *map_of_sim, int n,
                            const fire_params *params, const fire_cell *ignitions,

@@ -443,17 +443,20 @@ def fire_simulate_multi(ctx: Context, maps, map_of_sim, params, ignitions,
 
 
 def fire_autotune(ctx: Context, maps, map_of_sim, params, ignitions, seeds,
-                  device=False):
-    """Pick and record the fastest launch shape for this batch; returns it as
-    a dict (warps_per_block, blocks_per_sm, queue_entries, state_mode, ms)."""
+                  device=False, longest_first=False):
+    """Pick and record the fastest launch shape for this batch (timed in
+    longest-first order with longest_first, one map only); returns it as a
+    dict (warps_per_block, blocks_per_sm, queue_entries, state_mode, ms)."""
     lib = ctx.lib
     handles = _map_handles(maps)
     best = FireLaunch()
+    lpt = FIRE_LONGEST_FIRST if longest_first else 0
     if device:
         n = int(params.shape[0])
         ctx.check(lib.fire_autotune(
             ctx.h, len(maps), handles, _ptr(map_of_sim), n, _ptr(params),
-            _ptr(ignitions), _ptr(seeds), FIRE_DEVICE_PTRS, C.byref(best)))
+            _ptr(ignitions), _ptr(seeds), FIRE_DEVICE_PTRS | lpt,
+            C.byref(best)))
     else:
         p = _host(params, np.float64).reshape(-1, 5)
         n = p.shape[0]
@@ -462,7 +465,7 @@ def fire_autotune(ctx: Context, maps, map_of_sim, params, ignitions, seeds,
         s = _host(seeds, np.uint64).reshape(n)
         ctx.check(lib.fire_autotune(
             ctx.h, len(maps), handles, _ptr(mi), n, _ptr(p), _ptr(g), _ptr(s),
-            0, C.byref(best)))
+            lpt, C.byref(best)))
     return {f: getattr(best, f) for f, _ in FireLaunch._fields_}
 
 

@@ -132,6 +132,31 @@ def test_autotuned_shape_gives_identical_results(env, uneven):
     assert np.array_equal(before, after)
 
 
+def test_autotune_in_longest_first_order(env, uneven):
+    """Tuning one map in longest-first order (host and device arguments)
+    records a shape that leaves fire_simulate_batch's results unchanged;
+    longest-first tuning over several maps is rejected."""
+    torch, fire, oracle, ctx = env
+    lands, maps, targets = uneven
+    m = maps[1]
+    mi, params, ign, seeds = _batch(lands[1:2], 300, 6)
+    before, _ = m.simulate_batch(params, ign, seeds, longest_first=True)
+    best = fire.fire_autotune(ctx, [m], None, params, ign, seeds,
+                              longest_first=True)
+    assert best["warps_per_block"] > 0 and best["ms"] > 0
+    after, _ = m.simulate_batch(params, ign, seeds, longest_first=True)
+    assert np.array_equal(before, after)
+    dev = torch.device("cuda")
+    best = fire.fire_autotune(ctx, [m], None, torch.tensor(params, device=dev),
+                              torch.tensor(ign, device=dev),
+                              torch.tensor(seeds.view(np.int64), device=dev),
+                              device=True, longest_first=True)
+    assert best["warps_per_block"] > 0
+    with pytest.raises(fire.FireError):
+        fire.fire_autotune(ctx, maps, mi, params, ign, seeds,
+                           longest_first=True)
+
+
 def test_multi_with_a_global_state_map(env):
     """A 1024 x 1024 map (state beyond shared memory) in the same launch as
     small maps: each simulation equals its single-map batch result."""
