@@ -4,6 +4,8 @@ Covariates, thresholds and trajectories must match bit for bit; the
 single-precision screen's probabilities must agree with double precision to
 1e-6 absolute and never change a decision.
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -104,8 +106,8 @@ def test_single_precision_probabilities_within_1e6(ctx, orc):
 def test_screen_never_flips_a_decision(ctx):
     from paper_1701_03549_gb300 import fire
 
-    r = fire.fire_screen_selftest(ctx, 1 << 26, 12345)
-    assert r["cases"] == 1 << 26
+    r = fire.fire_screen_selftest(ctx, 1 << 30, 12345)
+    assert r["cases"] == 1 << 30
     assert r["flips"] == 0
     assert r["max_err_ratio"] < 1.0
     # the double-precision fallback stays rare for uniform draws
@@ -125,6 +127,52 @@ def test_philox_blocks_match_oracle(ctx, orc):
             c = ctr.copy()
             c[0] += i
             assert np.array_equal(got[i], orc.philox4x32_10(c, key))
+
+
+def test_philox_matches_curand_raw_blocks(ctx, orc, tmp_path):
+    """Known-answer check of Philox4x32-10 against a third-party
+    implementation: cuRAND's public raw block function, built here into a
+    small test library.  The oracle's generator and the library's must both
+    equal it on random counters and keys."""
+    import ctypes
+    import subprocess
+
+    from paper_1701_03549_gb300 import build, fire
+
+    src = os.path.join(os.path.dirname(__file__), "curand_philox_ref.cu")
+    so = str(tmp_path / "libcurand_ref.so")
+    r = subprocess.run([build._nvcc(), *build.ARCH, "-O2", "-std=c++17",
+                        "-Xcompiler", "-fPIC", "-shared", src, "-o", so],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    ref = ctypes.CDLL(so)
+    n = 4096
+    rng = np.random.default_rng(17)
+    ctr = rng.integers(0, 2 ** 32, (n, 4), dtype=np.uint64).astype(np.uint32)
+    key = rng.integers(0, 2 ** 32, (n, 2), dtype=np.uint64).astype(np.uint32)
+    ctr[:8] = 0
+    key[:4] = 0
+    key[4:8] = 0xFFFFFFFF
+    out = np.zeros((n, 4), np.uint32)
+    assert ref.curand_philox_blocks(
+        n, ctr.ctypes.data_as(ctypes.c_void_p),
+        key.ctypes.data_as(ctypes.c_void_p),
+        out.ctypes.data_as(ctypes.c_void_p)) == 0
+    for i in range(0, n, 7):
+        assert np.array_equal(orc.philox4x32_10(ctr[i], key[i]), out[i]), i
+    # the library's device generator on consecutive counters
+    base = np.array([5, 0xDEADBEEF, 1, 0], np.uint32)
+    k = np.array([0x12345678, 0x9ABCDEF0], np.uint32)
+    got = fire.fire_philox_blocks(ctx, 512, base, k)
+    cs = np.tile(base, (512, 1))
+    cs[:, 0] += np.arange(512, dtype=np.uint32)
+    ks = np.tile(k, (512, 1))
+    out2 = np.zeros((512, 4), np.uint32)
+    assert ref.curand_philox_blocks(
+        512, np.ascontiguousarray(cs).ctypes.data_as(ctypes.c_void_p),
+        np.ascontiguousarray(ks).ctypes.data_as(ctypes.c_void_p),
+        out2.ctypes.data_as(ctypes.c_void_p)) == 0
+    assert np.array_equal(got, out2)
 
 
 def _check_batch(ctx, orc, land, params, ignitions, seeds, target=None,
