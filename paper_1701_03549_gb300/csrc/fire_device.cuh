@@ -271,20 +271,6 @@ __device__ __forceinline__ ff ff_add(ff a, ff b)
     return {h, __fsub_rn(l, __fsub_rn(h, s))};
 }
 
-__device__ __forceinline__ ff ff_neg(ff a) { return {-a.h, -a.l}; }
-
-// (a.h + a.l) * (sqrt(2) / 2) with the constant as a float pair.
-__device__ __forceinline__ ff ff_mul_r2(ff a)
-{
-    constexpr float r2h = 0x1.6a09e6p-1f;
-    constexpr float r2l = 0x1.9fcef4p-27f;  // sqrt(2)/2 - r2h
-    const float h = __fmul_rn(a.h, r2h);
-    float l = __fmaf_rn(a.h, r2h, -h);
-    l = __fmaf_rn(a.h, r2l, l);
-    l = __fmaf_rn(a.l, r2h, l);
-    return {h, l};
-}
-
 // Per-parameter-set constants of the screen.
 struct ScreenParams {
     ff K[2];   // b0 + b1 * If for If = 0, 1

@@ -345,14 +345,6 @@ __device__ __forceinline__ int nth_set_bit(uint32_t m, uint32_t n)
     return pos;
 }
 
-__device__ __forceinline__ uint32_t dir_bits(const uint32_t md[8], int i)
-{
-    uint32_t dm = 0;
-#pragma unroll
-    for (int d = 0; d < 8; ++d) dm |= ((md[d] >> i) & 1u) << d;
-    return dm;
-}
-
 // Phase A of step t for active tile k, one warp (lane = tile row): retire the
 // previous step's burning cells, find the targets with a burning source in
 // each direction, count the trials and queue the candidates for phase B.
