@@ -260,13 +260,15 @@ def test_bad_arguments_are_rejected(ctx):
     net.free()
 
 
-def test_full_row_tiles_and_batch_consistency():
-    """At S >= 128 a 128-pixel tile is one image row (at S = 32 it spans four
-    rows, as in the tests above), so the TMA boxes take another shape: the
-    first two layers against the oracle (same criteria as above), and the
-    whole gradient of a 5-sample batch against the sample-weighted gradients
-    of 2- and 3-sample batches (the gradient is a mean over pixels)."""
-    S5, n = 128, 5
+@pytest.mark.parametrize("S5,n,splits", [(128, 5, ((0, 2), (2, 5))),
+                                         (256, 3, ((0, 1), (1, 3)))])
+def test_row_tiles_and_batch_consistency(S5, n, splits):
+    """At S = 128 a 128-pixel tile is one image row and at S = 256 (the
+    benchmark's size) half a row (at S = 32 it spans four rows, as in the
+    tests above), so the TMA boxes take other shapes: the first two layers
+    against the oracle (same criteria as above), and the whole gradient of
+    the batch against the sample-weighted gradients of two sub-batches (the
+    gradient is a mean over pixels)."""
     ctx = fire.fire_create(0, torch.cuda.current_stream())
     rng = np.random.default_rng(11)
     land = synth.landscape(2 * S5, 2 * S5, seed=12, wind_seed=12)
@@ -294,7 +296,7 @@ def test_full_row_tiles_and_batch_consistency():
     _close_layer(_bf(h), a2)
     net.free()
     gs = []
-    for lo, hi in ((0, 2), (2, 5)):
+    for lo, hi in splits:
         sub = fire.Net(ctx, S5, hi - lo)
         sub.set_params(theta)
         sub.backward(xd[lo:hi].contiguous(), td[lo:hi].contiguous(), sync=True)
