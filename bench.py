@@ -103,6 +103,21 @@ def _memory_roofs(kernel_s, peaks, peaks_kind, name="k_simulate_traffic.json"):
             "l2_peak_source": "ncu lts__t_sectors peak"}
 
 
+def _dense_sweep_roof(cell_updates_per_s, peaks, peaks_kind):
+    """Cell-updates/s (dense-equivalent: steps x H x W per second) against
+    what a dense sweep of the whole grid every step could reach at the
+    measured HBM bandwidth, streaming only the 2-bit state (2 bits read and 2
+    written per cell-update, 0.5 B) and nothing else.  A reference point for
+    the rate, not this kernel's bound: the worklists skip quiet tiles, so
+    the kernel moves far fewer bytes than such a sweep."""
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    peak = hbm * 1e9 / 0.5
+    return {"model": "dense 2-bit-state sweep, 0.5 B per cell-update",
+            "achieved": cell_updates_per_s, "peak": peak,
+            "unit": "cell-updates/s", "frac": cell_updates_per_s / peak,
+            "peak_source": f"hbm_gbs ({peaks_kind})"}
+
+
 class Clocks:
     """nvidia-smi sampling during the timed region."""
 
@@ -402,6 +417,8 @@ def run_native(args):
                            "warps_per_block", "blocks_per_sm",
                            "queue_entries", "state_mode")}},
             "cell_updates_per_s": steps_sum * H * W * world / total_s,
+            "cell_updates_roofline": _dense_sweep_roof(
+                steps_sum * H * W * world / total_s, peaks, peaks_kind),
             "trials_per_s": trials_sum * world / total_s,
             "mean_steps_per_sim": steps_sum / (SIMS * args.steps),
             "roofline": {"bound": "alu", "achieved": achieved / 1e12,
@@ -544,6 +561,8 @@ def run_uneven(args):
                            "warps_per_block", "blocks_per_sm",
                            "queue_entries", "state_mode")}},
             "cell_updates_per_s": cells * world / total_s,
+            "cell_updates_roofline": _dense_sweep_roof(
+                cells * world / total_s, peaks, peaks_kind),
             "trials_per_s": trials_sum * world / total_s,
             "mean_steps_per_sim": steps_sum / (n * args.steps),
             "roofline": {"bound": "alu", "achieved": achieved / 1e12,
