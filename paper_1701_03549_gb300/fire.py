@@ -14,6 +14,7 @@ from __future__ import annotations
 
 import ctypes as C
 import os
+import weakref
 
 import numpy as np
 
@@ -198,6 +199,9 @@ class Context:
             raise FireError(rc, "fire_create failed")
         self.h = h
         self.device = device
+        # maps and networks of this context: the library requires them freed
+        # before the context, so close() frees the ones still alive
+        self._owned = weakref.WeakSet()
 
     # -- errors
     def check(self, rc):
@@ -208,6 +212,8 @@ class Context:
 
     def close(self):
         if self.h:
+            for obj in list(self._owned):
+                obj.free()
             self.lib.fire_destroy(self.h)
             self.h = None
 
@@ -254,8 +260,10 @@ class Map:
 
     def __init__(self, ctx: Context, h, H: int, W: int):
         self.ctx, self.h, self.H, self.W = ctx, h, H, W
+        ctx._owned.add(self)
 
     def free(self):
+        # after the context's close() the map is already freed (h is None)
         if self.h:
             self.ctx.lib.fire_map_free(self.h)
             self.h = None
@@ -613,6 +621,7 @@ class Net:
                                           C.byref(h)))
         self.h = h
         self.P = fire_net_param_count()
+        ctx._owned.add(self)
 
     def free(self):
         if self.h:

@@ -1,0 +1,207 @@
+"""Parity at the benchmark's full sizes and launch configurations, on sampled
+outputs the oracle computes one by one:
+
+* the nine-fire uneven batch (100,000 simulations on grids up to 2000 x 1500)
+  in one graph-replayed fire_simulate_multi launch at the autotuned shape;
+* the 1024 x 1024 ignition search (32 x 32 candidates x 64 replicates =
+  65,536 simulations): candidate cells against the nearest-cell definition,
+  the fitness map against the replicate means of the batch's own results,
+  and sampled simulations of that batch against the oracle.
+
+The oracle runs in a spawn process pool (started before any GPU call).
+"""
+import multiprocessing as mp
+import os
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+_W = {}
+
+
+def _init_uneven():
+    import oracle
+
+    from paper_1701_03549_gb300 import workloads
+
+    wl = workloads.uneven_fires()
+    _W["wl"] = wl
+    _W["F"] = [oracle.Features(L) for L in wl.lands]
+
+
+def _run_uneven(args):
+    i, target_seed = args
+    wl = _W["wl"]
+    j = int(wl.map_of_sim[i])
+    tgt = _uneven_target(wl.lands[j], target_seed + j)
+    r, _ = _W["F"][j].simulate(wl.params[i], tuple(wl.ignitions[i]),
+                               int(wl.seeds[i]), target=tgt, want_steps=False)
+    return i, r
+
+
+def _uneven_target(land, seed):
+    rng = np.random.default_rng(seed)
+    return rng.random(land.veg.shape) < 0.2
+
+
+def _init_ign(H, W, map_seed, wind_seed):
+    import oracle
+
+    from paper_1701_03549_gb300 import synth
+
+    land = synth.landscape(H, W, seed=map_seed, wind_seed=wind_seed)
+    _W["F"] = oracle.Features(land)
+
+
+def _run_ign(args):
+    beta, ign, seed, target = args
+    r, _ = _W["F"].simulate(beta, ign, int(seed), target=target,
+                            want_steps=False)
+    return r
+
+
+def _pool(init, initargs=()):
+    return mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1),
+                                        initializer=init, initargs=initargs)
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    import oracle
+
+    __graft_entry__.build()
+    oracle.build()
+    return torch
+
+
+def test_uneven_batch_full_size_sample(env):
+    torch = env
+    from paper_1701_03549_gb300 import fire, workloads
+
+    target_seed = 500
+    pool = _pool(_init_uneven)   # before the first GPU call
+    try:
+        wl = workloads.uneven_fires()
+        ctx = fire.Context(0)
+        maps = [ctx.landscape_upload(L) for L in wl.lands]
+        for j, (m, L) in enumerate(zip(maps, wl.lands)):
+            m.target_upload(_uneven_target(L, target_seed + j))
+        sub = np.arange(0, wl.n, 10)
+        fire.fire_autotune(ctx, maps, wl.map_of_sim[sub], wl.params[sub],
+                           wl.ignitions[sub], wl.seeds[sub])
+        dev = torch.device("cuda")
+        t_mi = torch.tensor(wl.map_of_sim, device=dev)
+        t_p = torch.tensor(wl.params, dtype=torch.float64, device=dev)
+        t_g = torch.tensor(wl.ignitions, device=dev)
+        t_s = torch.tensor(wl.seeds.view(np.int64), device=dev)
+        out = torch.zeros((wl.n, 6), dtype=torch.int32, device=dev)
+        outs = []
+        for _ in range(2):   # capture, then replay of the same graph
+            out.zero_()
+            fire.fire_simulate_multi(ctx, maps, t_mi, t_p, t_g, t_s,
+                                     device=True, out=out, graph=True,
+                                     sync=True)
+            outs.append(fire.results_view(out).copy())
+        assert np.array_equal(outs[0], outs[1])
+        res = outs[0]
+        ctx.close()
+        # samples, in index order per map: the first fire that dies within
+        # 20 steps, the first two longer ones the oracle finishes within a
+        # bounded time (steps x cells), and on every third map one larger
+        sizes = np.array([L.veg.size for L in wl.lands], np.int64)
+        steps = res["steps"].astype(np.int64)
+        cost = steps * sizes[wl.map_of_sim]
+        picks = []
+        for j in range(len(wl.lands)):
+            on = wl.map_of_sim == j
+            picks += list(np.flatnonzero(on & (steps < 20))[:1])
+            picks += list(np.flatnonzero(on & (steps >= 20) &
+                                         (cost <= 2_000_000_000))[:2])
+            big = np.flatnonzero(on & (cost > 2_000_000_000) &
+                                 (cost <= 4_000_000_000))
+            if j % 3 == 0 and len(big):
+                picks.append(big[0])
+        assert len(picks) >= 18
+        checked = pool.map(_run_uneven, [(int(i), target_seed) for i in picks],
+                           chunksize=1)
+    finally:
+        pool.close()
+        pool.join()
+    for i, o in checked:
+        for k in ("burnt", "inter", "target", "steps", "status", "trials"):
+            assert int(res[k][i]) == o[k], (i, k, int(res[k][i]), o[k])
+
+
+def test_ignition_search_full_size_sample(env):
+    torch = env
+    import oracle
+
+    from paper_1701_03549_gb300 import fire, synth
+
+    p = synth.PRESETS["ignition_search_1024"]
+    H, W = p["H"], p["W"]
+    pool = _pool(_init_ign, (H, W, p["map_seed"], p["wind_seed"]))
+    try:
+        land = synth.preset_landscape("ignition_search_1024")
+        ign0 = synth.centre_ignition(land.veg)
+        beta = np.asarray(synth.TRUTH_BETA, np.float64)
+        F = oracle.Features(land)
+        _, tb = F.simulate(beta, ign0, synth.TARGET_SEED)
+        target = tb >= 0
+        ctx = fire.Context(0)
+        m = ctx.landscape_upload(land)
+        m.target_upload(target)
+        LH = LW = p["lattice"]
+        reps, seed = p["replicates"], 7
+        fm, cells, xy = fire.ignition_search(ctx, m, beta, LH, LW, reps, seed,
+                                             kind=fire.FITNESS_JACCARD,
+                                             cutoff=0.3)
+        # the same 65,536 simulations as one batch
+        cl = cells.reshape(-1, 2)
+        n = LH * LW * reps
+        params = np.tile(beta, (n, 1))
+        ign = np.repeat(cl, reps, axis=0).astype(np.int32)
+        seeds = np.arange(seed, seed + n, dtype=np.uint64)
+        res, _ = m.simulate_batch(params, ign, seeds)
+        m.free()
+        ctx.close()
+        rng = np.random.default_rng(3)
+        picks = sorted(set(rng.integers(0, n, 10).tolist()) | {0, n - 1})
+        checked = pool.map(_run_ign, [(beta, tuple(ign[i]), int(seeds[i]),
+                                       target) for i in picks], chunksize=1)
+    finally:
+        pool.close()
+        pool.join()
+    for i, o in zip(picks, checked):
+        for k in ("burnt", "inter", "target", "steps", "status", "trials"):
+            assert int(res[k][i]) == o[k], (i, k)
+    # candidate cells: the burnable burnt cell nearest each lattice point
+    # (squared distance, ties to the lower row-major index)
+    rows, cols = np.nonzero(target & (land.veg != 0))
+    r0, r1 = np.nonzero(target)[0].min(), np.nonzero(target)[0].max()
+    c0, c1 = np.nonzero(target)[1].min(), np.nonzero(target)[1].max()
+    for a in range(LH):
+        for b in range(LW):
+            R = r0 + ((2 * a + 1) * (r1 - r0 + 1)) // (2 * LH)
+            C = c0 + ((2 * b + 1) * (c1 - c0 + 1)) // (2 * LW)
+            d = (rows - R) ** 2 + (cols - C) ** 2
+            best = np.flatnonzero(d == d.min())
+            k = best[np.argmin(rows[best] * W + cols[best])]
+            assert cells[a, b].tolist() == [rows[k], cols[k]], (a, b)
+    # fitness map: replicate means (index order) of the batch's fitness
+    f = np.array([oracle.fitness(int(r["burnt"]), int(r["inter"]),
+                                 int(r["target"]), fire.FITNESS_JACCARD)
+                  for r in res])
+    want = np.zeros(LH * LW)
+    for c in range(LH * LW):
+        s = 0.0
+        for v in f[c * reps:(c + 1) * reps]:
+            s = s + v
+        want[c] = s / reps
+    assert np.array_equal(fm.reshape(-1), want)

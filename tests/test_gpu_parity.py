@@ -451,3 +451,28 @@ def test_longest_first_order_changes_no_result():
     assert torch.equal(a, b)
     m.free()
     ctx.close()
+
+
+def test_closing_a_context_frees_its_maps_and_networks_first():
+    """The library wants maps and networks freed before their context: the
+    binding's close() frees the live ones, and dropping them afterwards is a
+    no-op (no use of the destroyed context, no stale CUDA error for the next
+    context)."""
+    import gc
+
+    from paper_1701_03549_gb300 import fire
+
+    land = synth.landscape(40, 50, seed=1)
+    c1 = fire.Context(0)
+    m = c1.landscape_upload(land)
+    net = fire.Net(c1, 16, 1)
+    c1.close()
+    assert m.h is None and net.h is None
+    del m, net
+    gc.collect()
+    c2 = fire.Context(0)
+    m2 = c2.landscape_upload(land)
+    ign = np.array([synth.centre_ignition(land.veg)], np.int32)
+    res, _ = m2.simulate_batch(np.array([TRUTH]), ign, np.array([3], np.uint64))
+    assert res["status"][0] & fire.STATUS_BAD_IGNITION == 0
+    c2.close()
