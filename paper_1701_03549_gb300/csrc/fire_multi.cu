@@ -210,9 +210,15 @@ int fire_simulate_multi(fire_ctx *ctx, int nmaps, const fire_map *const *maps,
             (unsigned long long)(uintptr_t)dseeds, (unsigned long long)(uintptr_t)dmap,
             (unsigned long long)(uintptr_t)dout, max_steps,
             (unsigned long long)plan.nwarps, (unsigned long long)plan.qcap,
-            (unsigned long long)plan.smem_state, (unsigned long long)plan.grid};
-        for (int j = 0; j < nmaps; ++j)
+            (unsigned long long)plan.smem_state, (unsigned long long)plan.grid,
+            (unsigned long long)a.cell_uniform};
+        // a map's memory may be reused by a later map of another shape, and
+        // the launch bakes in the largest map's tile count
+        for (int j = 0; j < nmaps; ++j) {
             key.push_back((unsigned long long)(uintptr_t)maps[j]->feat);
+            key.push_back(((unsigned long long)(uint32_t)maps[j]->dev.H << 32) |
+                          (uint32_t)maps[j]->dev.W);
+        }
         rc = run_graph(ctx, key, issue);
     } else {
         rc = issue();

@@ -96,6 +96,39 @@ def test_multi_graph_replay_with_new_inputs(env, uneven):
                                  out=out, graph=True, sync=True)
         want = fire.fire_simulate_multi(ctx, maps, mi, params, ign, seeds)
         assert np.array_equal(fire.results_view(out), want), rep
+    # the same buffers with the one-uniform-per-cell rule: a new graph, not
+    # a replay of the per-neighbour one
+    fire.fire_simulate_multi(ctx, maps, t_mi, t_p, t_g, t_s, device=True,
+                             out=out, graph=True, sync=True, cell_uniform=True)
+    want = fire.fire_simulate_multi(ctx, maps, mi, params, ign, seeds,
+                                    cell_uniform=True)
+    assert np.array_equal(fire.results_view(out), want)
+    assert not np.array_equal(
+        want, fire.fire_simulate_multi(ctx, maps, mi, params, ign, seeds))
+
+
+def test_multi_graph_after_a_map_is_replaced(env):
+    """A freed map's memory can come back for a new map of another shape
+    (whether it does is up to the allocator): a graph call on the new map
+    must give the new map's results, never a replay of the old launch."""
+    torch, fire, oracle, ctx = env
+    dev = torch.device("cuda", 0)
+    results = []
+    for shape in ((40, 40), (150, 170)):
+        land = synth.landscape(*shape, seed=9, wind_seed=9)
+        m = ctx.landscape_upload(land)
+        mi, params, ign, seeds = _batch([land], 64, 8)
+        t = [torch.tensor(mi, device=dev),
+             torch.tensor(params, dtype=torch.float64, device=dev),
+             torch.tensor(ign, device=dev),
+             torch.tensor(seeds.view(np.int64), device=dev)]
+        out = torch.zeros((64, 6), dtype=torch.int32, device=dev)
+        torch.cuda.synchronize()
+        fire.fire_simulate_multi(ctx, [m], t[0], t[1], t[2], t[3], device=True,
+                                 out=out, graph=True, sync=True)
+        want = fire.fire_simulate_multi(ctx, [m], mi, params, ign, seeds)
+        assert np.array_equal(fire.results_view(out), want), shape
+        m.free()
 
 
 def test_multi_reports_bad_map_index(env, uneven):
