@@ -53,6 +53,18 @@ def build_library(force: bool = False, verbose: bool = False) -> str:
     if not force and not stale():
         return LIB
     os.makedirs(BUILD, exist_ok=True)
+    # one build at a time (ranks of one job start together): the first
+    # holder builds, the others find the library up to date
+    import fcntl
+
+    with open(os.path.join(BUILD, ".lock"), "w") as lk:
+        fcntl.flock(lk, fcntl.LOCK_EX)
+        if not force and not stale():
+            return LIB
+        return _build_locked(verbose)
+
+
+def _build_locked(verbose: bool) -> str:
     nvcc = _nvcc()
 
     def compile_one(src):
