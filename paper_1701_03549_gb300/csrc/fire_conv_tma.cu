@@ -12,13 +12,16 @@
 //   * another thread waits for the slab, issues four 128 x 128 x 16 MMAs into
 //     the tensor-memory accumulator and commits them to the slab's "empty"
 //     barrier, which hands the stage back to the loader.
-// Two stages (64 KB) let three CTAs share an SM, so the epilogues of some
-// (tensor memory -> registers -> bias/ReLU or ReLU mask -> BF16 stores)
-// overlap the main loops of the others; on a GB300 this beat three stages
-// with two CTAs per SM by 5-10 % and four or more stages with one CTA per SM
-// by about 50 %.  Every wait is bounded; on a timeout the
-// CTA records an error, waits (bounded) for its own copies in flight, frees
-// its tensor memory and returns.
+// k_conv_tma runs one tile per CTA: two stages (64 KB) let three CTAs share
+// an SM, so the epilogues of some (tensor memory -> registers -> bias/ReLU or
+// ReLU mask -> BF16 stores) overlap the main loops of the others.
+// k_conv_tma_p, the default, is persistent: two CTAs per SM loop over tiles
+// with three stages and two tensor-memory accumulators, the loads and MMAs
+// of the next tile overlapping the epilogue of the previous one within the
+// CTA (on a GB300, 9 % more training throughput than k_conv_tma; a single
+// persistent CTA per SM was slower than either).  Every wait is bounded; on a
+// timeout the CTA records an error, waits (bounded) for its own copies and
+// MMAs in flight, frees its tensor memory and returns.
 #include "fire_internal.h"
 #include "fire_tc.cuh"
 
@@ -26,6 +29,7 @@
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <mutex>
 
 namespace fire {
@@ -33,6 +37,9 @@ namespace convtma {
 
 #ifndef FIRE_CONV_STAGES
 #define FIRE_CONV_STAGES 2
+#endif
+#ifndef FIRE_CONV_PERSISTENT
+#define FIRE_CONV_PERSISTENT 1   // 0: one tile per CTA (k_conv_tma)
 #endif
 constexpr int kStages = FIRE_CONV_STAGES;       // shared-memory stages per CTA
 constexpr int kTileBytes = 128 * 128;           // 128 rows x 64 BF16
@@ -228,6 +235,203 @@ __global__ void __launch_bounds__(128, kCtasPerSm)
     tc::fence_before_sync();
     __syncthreads();
     if (warp == 0) tc::tmem_dealloc(tmem, 128);
+}
+
+// Persistent variant of k_conv_tma: two CTAs per SM, each looping over tiles
+// (tile = blockIdx.x, blockIdx.x + gridDim.x, ...) with three shared-memory
+// stages and two 128-column tensor-memory accumulators, so that the next
+// tile's loads and MMAs run while the previous tile's epilogue drains its
+// accumulator.  Warp 0 (one thread) issues the TMA loads, warp 1 (one thread)
+// the MMAs, warps 2..5 run the epilogue (warp w reads tensor-memory lanes
+// 32 (w mod 4) .. 32 (w mod 4) + 31, as tcgen05.ld requires).  Every wait is
+// bounded; on a timeout the CTA records an error, lets its copies and MMAs in
+// flight finish (bounded), frees its tensor memory and returns.
+constexpr int kPStages = 3;
+constexpr int kPSmem = kPStages * kStageBytes + 1024;
+constexpr int kPThreads = 192;
+
+__device__ __forceinline__ void mbar_arrive(void *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(
+                     tc::smem_addr(bar))
+                 : "memory");
+}
+
+__global__ void __launch_bounds__(kPThreads, 2)
+    k_conv_tma_p(const __grid_constant__ CUtensorMap act,
+                 const __grid_constant__ CUtensorMap wts, Epi epi, int S, int lgS,
+                 int d, int sign, int ntiles, uint32_t *err)
+{
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    __shared__ __align__(8) unsigned long long full[kPStages], empty[kPStages];
+    __shared__ __align__(8) unsigned long long tfull[2], tempty[2], done;
+    __shared__ uint32_t tmem_slot;
+    __shared__ int s_fail, s_issued, s_consumed;
+    __shared__ float s_bias[128];
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t base = (tc::smem_addr(smem_raw) + 1023u) & ~1023u;
+    if (epi.mode == 0 && tid < 128) s_bias[tid] = epi.bias[tid];
+    if (warp == 0) {
+        tc::tmem_alloc(&tmem_slot, 256);
+        tc::tmem_relinquish();
+    }
+    if (tid == 0) {
+        for (int i = 0; i < kPStages; ++i) {
+            tc::mbar_init(&full[i], 1);
+            tc::mbar_init(&empty[i], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            tc::mbar_init(&tfull[i], 1);
+            tc::mbar_init(&tempty[i], 128);   // every epilogue thread arrives
+        }
+        tc::mbar_init(&done, 1);
+        s_fail = 0;
+        s_issued = 0;
+        s_consumed = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // loader: slab g of the CTA's sequence uses stage g mod kPStages
+            int g = 0;
+            bool ok = true;
+            for (int tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
+                const int m0 = tile * 128;
+                const int b = m0 >> (2 * lgS);
+                const int y0 = (m0 >> lgS) & (S - 1), x0 = m0 & (S - 1);
+                for (int s = 0; s < kSlabs; ++s, ++g) {
+                    const int st = g % kPStages;
+                    if (g >= kPStages &&
+                        !tc::mbar_wait_bounded(&empty[st],
+                                               ((g / kPStages) - 1) & 1)) {
+                        atomicOr(&s_fail, 1);
+                        ok = false;
+                        break;
+                    }
+                    if (*(volatile int *)&s_fail) {
+                        ok = false;
+                        break;
+                    }
+                    const int tap = s >> 1, c0 = (s & 1) * 64;
+                    const int dy = sign * (tap / 3 - 1) * d;
+                    const int dx = sign * (tap % 3 - 1) * d;
+                    const uint32_t sa = base + st * kStageBytes;
+                    expect_tx(&full[st], kStageBytes);
+                    tma_4d(sa, &act, c0, x0 + dx, y0 + dy, b, &full[st]);
+                    tma_2d(sa + kTileBytes, &wts, s * 64, 0, &full[st]);
+                }
+            }
+            s_issued = g;
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // MMA issuer: tile number `it` of this CTA accumulates in buffer
+            // it & 1, once the epilogue has drained that buffer's last use
+            constexpr uint32_t idesc = tc::idesc_bf16(128, 128);
+            int g = 0, it = 0;
+            bool ok = true;
+            for (int tile = blockIdx.x; ok && tile < ntiles;
+                 tile += gridDim.x, ++it) {
+                const int acc = it & 1;
+                if (it >= 2 &&
+                    !tc::mbar_wait_bounded(&tempty[acc], ((it >> 1) - 1) & 1)) {
+                    atomicOr(&s_fail, 1);
+                    break;
+                }
+                tc::fence_after_sync();
+                const uint32_t td = tmem + (uint32_t)(acc * 128);
+                for (int s = 0; s < kSlabs; ++s, ++g) {
+                    const int st = g % kPStages;
+                    if (!tc::mbar_wait_bounded(&full[st], (g / kPStages) & 1)) {
+                        atomicOr(&s_fail, 1);
+                        ok = false;
+                        break;
+                    }
+                    tc::fence_after_sync();
+                    const uint32_t sa = base + st * kStageBytes, sb = sa + kTileBytes;
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk)
+                        tc::mma_bf16(td, desc_sw128(sa + kk * 32),
+                                     desc_sw128(sb + kk * 32), idesc,
+                                     s > 0 || kk > 0);
+                    tc::mma_commit(&empty[st]);
+                }
+                if (ok) tc::mma_commit(&tfull[acc]);
+            }
+            s_consumed = g;
+            tc::mma_commit(&done);   // arrives once every issued MMA is done
+        }
+    } else {
+        // epilogue: tile number `it` is read from buffer it & 1
+        const int q = warp & 3;   // tensor-memory lane quarter of this warp
+        int it = 0;
+        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+            const int acc = it & 1;
+            if (*(volatile int *)&s_fail) break;
+            if (!tc::mbar_wait_bounded(&tfull[acc], (it >> 1) & 1)) {
+                atomicOr(&s_fail, 1);
+                break;
+            }
+            tc::fence_after_sync();
+            const int p = tile * 128 + q * 32 + lane;
+            uint16_t *orow = epi.out + (size_t)p * 128;
+            const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * 128);
+#pragma unroll 1
+            for (int c0 = 0; c0 < 128; c0 += 32) {
+                float v[32];
+                tc::tmem_ld32(ta + (uint32_t)c0, v);
+                uint32_t pk[16];
+                if (epi.mode == 0) {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                        pk[j] = pack2(fmaxf(v[2 * j] + s_bias[c0 + 2 * j], 0.0f),
+                                      fmaxf(v[2 * j + 1] + s_bias[c0 + 2 * j + 1], 0.0f));
+                } else {
+                    const uint4 *hp = reinterpret_cast<const uint4 *>(
+                        epi.hprev + (size_t)p * 128 + c0);
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const uint4 h = hp[u];
+                        const uint32_t hw[4] = {h.x, h.y, h.z, h.w};
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            const int e = 2 * (4 * u + j);
+                            pk[4 * u + j] = pack2(pos16(hw[j] & 0xffffu) ? v[e] : 0.0f,
+                                                  pos16(hw[j] >> 16) ? v[e + 1] : 0.0f);
+                        }
+                    }
+                }
+                uint4 *o = reinterpret_cast<uint4 *>(orow + c0);
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    o[u] = make_uint4(pk[4 * u], pk[4 * u + 1], pk[4 * u + 2],
+                                      pk[4 * u + 3]);
+            }
+            tc::fence_before_sync();
+            mbar_arrive(&tempty[acc]);
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        if (s_fail) {
+            atomicOr(err, 1u);
+            // copies issued but never consumed must land before the CTA leaves
+            for (int g = s_consumed; g < s_issued; ++g)
+                tc::mbar_wait_bounded(&full[g % kPStages], (g / kPStages) & 1);
+        }
+        // every MMA this CTA issued has completed
+        tc::mbar_wait_bounded(&done, 0);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (warp == 0) tc::tmem_dealloc(tmem, 256);
 }
 
 // Weight gradient of a 128 -> 128 layer: D[o][(t, i)] = sum_p dz[p, o]
@@ -576,13 +780,28 @@ cudaError_t launch_conv_tma(int mode, const uint16_t *in, const uint16_t *w,
         return cudaErrorInvalidValue;
     CUtensorMap ma, mw;
     if (!map_act(&ma, in, n, S) || !map_wts(&mw, w)) return cudaErrorInvalidValue;
+    Epi e{mode, bias, hprev, out};
+    const long long P = (long long)n * S * S;
+    const int ntiles = (int)(P / 128);
+#if FIRE_CONV_PERSISTENT
+    int dev = 0, nsm = 0;
+    cudaError_t attr = cudaGetDevice(&dev);
+    if (attr == cudaSuccess)
+        attr = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (attr == cudaSuccess)
+        attr = cudaFuncSetAttribute(k_conv_tma_p,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, kPSmem);
+    if (attr != cudaSuccess) return attr;
+    const int grid = std::min(ntiles, 2 * nsm);
+    k_conv_tma_p<<<grid, kPThreads, kPSmem, st>>>(ma, mw, e, S, lgS, d,
+                                                  mode == 0 ? 1 : -1, ntiles, err);
+#else
     cudaError_t attr = cudaFuncSetAttribute(
         k_conv_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
     if (attr != cudaSuccess) return attr;
-    Epi e{mode, bias, hprev, out};
-    const long long P = (long long)n * S * S;
-    k_conv_tma<<<(unsigned)(P / 128), 128, kSmem, st>>>(ma, mw, e, S, lgS, d,
-                                                         mode == 0 ? 1 : -1, err);
+    k_conv_tma<<<(unsigned)ntiles, 128, kSmem, st>>>(ma, mw, e, S, lgS, d,
+                                                     mode == 0 ? 1 : -1, err);
+#endif
     return cudaGetLastError();
 }
 
