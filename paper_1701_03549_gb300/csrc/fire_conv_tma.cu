@@ -50,6 +50,14 @@ constexpr int kSlabs = 18;                      // 9 taps x 2 channel halves
 // columns each, so at most four).
 constexpr int kCtasPerSm =
     (227 * 1024) / (kSmem + 2048) > 4 ? 4 : (227 * 1024) / (kSmem + 2048);
+// The weight-gradient kernel's own stage count and residency.
+#ifndef FIRE_WGRAD_STAGES
+#define FIRE_WGRAD_STAGES 2
+#endif
+constexpr int kWStages = FIRE_WGRAD_STAGES;
+constexpr int kWSmem = kWStages * kStageBytes + 1024;
+constexpr int kWCtasPerSm =
+    (227 * 1024) / (kWSmem + 2048) > 4 ? 4 : (227 * 1024) / (kWSmem + 2048);
 
 struct Epi {
     int mode;                 // 0 forward (bias + ReLU), 1 input gradient (mask)
@@ -451,13 +459,13 @@ __device__ __forceinline__ uint64_t desc_sw128_mn(uint32_t saddr)
     return d;
 }
 
-__global__ void __launch_bounds__(128, kCtasPerSm)
+__global__ void __launch_bounds__(128, kWCtasPerSm)
     k_wgrad_tma(const __grid_constant__ CUtensorMap dzm,
                 const __grid_constant__ CUtensorMap inm, float *dw, int S, int lgS,
                 int d, int slabs_total, int slabs_per, uint32_t *err)
 {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    __shared__ __align__(8) unsigned long long full[kStages], empty[kStages], done;
+    __shared__ __align__(8) unsigned long long full[kWStages], empty[kWStages], done;
     __shared__ uint32_t tmem_slot;
     __shared__ int s_fail, s_issued, s_consumed;
 
@@ -473,7 +481,7 @@ __global__ void __launch_bounds__(128, kCtasPerSm)
         tc::tmem_relinquish();
     }
     if (tid == 0) {
-        for (int i = 0; i < kStages; ++i) {
+        for (int i = 0; i < kWStages; ++i) {
             tc::mbar_init(&full[i], 1);
             tc::mbar_init(&empty[i], 1);
         }
@@ -491,9 +499,9 @@ __global__ void __launch_bounds__(128, kCtasPerSm)
     if (ns > 0 && warp == 0 && lane == 0) {
         int s = 0;
         for (; s < ns; ++s) {
-            const int st = s % kStages;
-            if (s >= kStages &&
-                !tc::mbar_wait_bounded(&empty[st], ((s / kStages) - 1) & 1)) {
+            const int st = s % kWStages;
+            if (s >= kWStages &&
+                !tc::mbar_wait_bounded(&empty[st], ((s / kWStages) - 1) & 1)) {
                 atomicOr(&s_fail, 1);
                 break;
             }
@@ -514,8 +522,8 @@ __global__ void __launch_bounds__(128, kCtasPerSm)
             tc::idesc_bf16(128, 128) | (1u << 15) | (1u << 16);   // both MN-major
         int s = 0;
         for (; s < ns; ++s) {
-            const int st = s % kStages;
-            if (!tc::mbar_wait_bounded(&full[st], (s / kStages) & 1)) {
+            const int st = s % kWStages;
+            if (!tc::mbar_wait_bounded(&full[st], (s / kWStages) & 1)) {
                 atomicOr(&s_fail, 1);
                 break;
             }
@@ -552,7 +560,7 @@ __global__ void __launch_bounds__(128, kCtasPerSm)
     } else if (s_fail && tid == 0) {
         atomicOr(err, 1u);
         for (int s = s_consumed; s < s_issued; ++s)
-            tc::mbar_wait_bounded(&full[s % kStages], (s / kStages) & 1);
+            tc::mbar_wait_bounded(&full[s % kWStages], (s / kWStages) & 1);
     }
     tc::fence_before_sync();
     __syncthreads();
@@ -805,6 +813,9 @@ cudaError_t launch_conv_tma(int mode, const uint16_t *in, const uint16_t *w,
     return cudaGetLastError();
 }
 
+// CTAs of the weight-gradient kernel resident per SM.
+int wgrad_ctas_per_sm() { return convtma::kWCtasPerSm; }
+
 // Weight gradient of a 128 -> 128 layer, added into dw[128][1152] (FP32,
 // cleared by the caller): dz and in are [n][S][S][128] BF16, S a power of two
 // >= 16; the pixel range is split `split` ways.
@@ -820,13 +831,13 @@ cudaError_t launch_wgrad_tma(const uint16_t *dz, const uint16_t *in, float *dw, 
     if (!map_act(&mz, dz, n, S, 64) || !map_act(&mi, in, n, S, 64))
         return cudaErrorInvalidValue;
     cudaError_t attr = cudaFuncSetAttribute(
-        k_wgrad_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+        k_wgrad_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, kWSmem);
     if (attr != cudaSuccess) return attr;
     const int total = (int)((long long)n * S * S / 64);
     if (split > total) split = total;
     const int per = (total + split - 1) / split;
     dim3 grid(1, 9, (total + per - 1) / per);
-    k_wgrad_tma<<<grid, 128, kSmem, st>>>(mz, mi, dw, S, lgS, d, total, per, err);
+    k_wgrad_tma<<<grid, 128, kWSmem, st>>>(mz, mi, dw, S, lgS, d, total, per, err);
     return cudaGetLastError();
 }
 

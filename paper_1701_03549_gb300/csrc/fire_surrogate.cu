@@ -509,9 +509,9 @@ cudaError_t net_forward(fire_net *net, int n, const uint16_t *x, uint32_t *err,
     return cudaSuccess;
 }
 
-int wgrad_split(int nt_n, int kslabs)
+int wgrad_split(int nt_n, int kslabs, int ctas_per_sm = 3)
 {
-    int s = (152 * 3) / nt_n;
+    int s = (152 * ctas_per_sm) / nt_n;
     if (s < 1) s = 1;
     if (s > kslabs) s = kslabs;
     return s;
@@ -689,7 +689,8 @@ int fire_net_backward(fire_ctx *ctx, fire_net *net, int n, const uint16_t *x,
             e = tc::launch_tc_tile<64>(p, wgrad_split(3, kslabs), err, st);
         } else if (S >= 16) {
             e = launch_wgrad_tma(net->dz[l], net->h[l - 1], net->grad + w_off(l), n, S,
-                                 lgS, kDil[l], wgrad_split(9, kslabs), err, st);
+                                 lgS, kDil[l],
+                                 wgrad_split(9, kslabs, wgrad_ctas_per_sm()), err, st);
         } else {
             ConvWgrad<kC> p{net->dz[l], net->h[l - 1], net->grad + w_off(l), kC,
                             9 * kC, P, S, lgS, kDil[l]};
