@@ -770,7 +770,7 @@ def run_surrogate(args):
         "roofline": {"bound": "tensor", "achieved": fwd_tflops, "peak": peak,
                      "unit": "TFLOP/s", "frac": fwd_tflops / peak,
                      "traffic": None, "kernel": "surrogate forward "
-                     "(k_conv_tma x7 + layer-1 tile + head), batch 8 x 256^2",
+                     "(k_conv_tma_p x7 + layer-1 k_conv1_tma + head), batch 8 x 256^2",
                      "peak_source": f"bf16_tflops ({kind})"},
         "cpu_baseline": None, "e2e": None, "gpu_launches": None,
         "clocks": ck,
@@ -849,7 +849,7 @@ def run_surrogate_step(args):
             "forward_ms": fwd_ms, "forward_tflops": fwd,
             "roofline": {"bound": "tensor", "achieved": trn, "peak": peak,
                          "unit": "TFLOP/s", "frac": trn / peak,
-                         "traffic": None, "kernel": "training step (k_conv_tma "
+                         "traffic": None, "kernel": "training step (k_conv_tma_p "
                          "forward and input gradient, k_wgrad_tma, layer-1 "
                          "tile, head, Adam)",
                          "peak_source": f"bf16_tflops ({kind})"},
