@@ -217,36 +217,82 @@ __global__ void k_head(const uint16_t *__restrict__ h, const float *__restrict__
 
 // dz of the top layer, head weight and bias gradients.  Block = 128 threads,
 // thread c = channel; each block walks `per` pixels.
-__global__ void k_head_grad(const uint16_t *__restrict__ h, const float *__restrict__ wh,
-                            const float *__restrict__ g, int P, int per,
-                            uint16_t *__restrict__ dz, float *__restrict__ dwh)
+// Head gradient: dz[p, c] = g[p] wh[c] where h[p, c] > 0 (else 0), dwh[c] =
+// sum_p g[p] h[p, c], dwh[kC] = sum_p g[p]; threads as in k_bias_grad.
+__global__ void __launch_bounds__(256)
+    k_head_grad(const uint16_t *__restrict__ h, const float *__restrict__ wh,
+                const float *__restrict__ g, int P, int per,
+                uint16_t *__restrict__ dz, float *__restrict__ dwh)
 {
-    const int c = threadIdx.x;
+    __shared__ float red[16][kC + 2];
+    const int cg = threadIdx.x & 15, pl = threadIdx.x >> 4;
     const int p0 = blockIdx.x * per, p1 = min(P, p0 + per);
-    const float w = wh[c];
-    float aw = 0.0f, ab = 0.0f;
-    for (int p = p0; p < p1; ++p) {
+    float w[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) w[j] = wh[cg * 8 + j];
+    float aw[8] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+    float ab = 0.0f;
+    for (int p = p0 + pl; p < p1; p += 16) {
         const float gp = g[p];
-        const uint16_t hv = h[(size_t)p * kC + c];
-        const float hf = bf16_to_f(hv);
-        dz[(size_t)p * kC + c] =
-            __bfloat16_as_ushort(__float2bfloat16_rn(bf16_pos(hv) ? gp * w : 0.0f));
-        aw = fmaf(gp, hf, aw);
+        const size_t off = (size_t)p * kC + cg * 8;
+        const uint4 u = *reinterpret_cast<const uint4 *>(h + off);
+        const uint32_t w4[4] = {u.x, u.y, u.z, u.w};
+        uint32_t o4[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const uint16_t lo = (uint16_t)(w4[j] & 0xffffu), hi = (uint16_t)(w4[j] >> 16);
+            aw[2 * j] = fmaf(gp, bf16_to_f(lo), aw[2 * j]);
+            aw[2 * j + 1] = fmaf(gp, bf16_to_f(hi), aw[2 * j + 1]);
+            const uint32_t dl = __bfloat16_as_ushort(
+                __float2bfloat16_rn(bf16_pos(lo) ? gp * w[2 * j] : 0.0f));
+            const uint32_t dh = __bfloat16_as_ushort(
+                __float2bfloat16_rn(bf16_pos(hi) ? gp * w[2 * j + 1] : 0.0f));
+            o4[j] = dl | (dh << 16);
+        }
+        *reinterpret_cast<uint4 *>(dz + off) = make_uint4(o4[0], o4[1], o4[2], o4[3]);
         ab += gp;
     }
-    atomicAdd(dwh + c, aw);
-    if (c == 0) atomicAdd(dwh + kC, ab);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) red[pl][cg * 8 + j] = aw[j];
+    if (cg == 0) red[pl][kC] = ab;
+    __syncthreads();
+    if (threadIdx.x <= kC) {
+        float sum = 0.0f;
+#pragma unroll
+        for (int r = 0; r < 16; ++r) sum += red[r][threadIdx.x];
+        atomicAdd(dwh + threadIdx.x, sum);
+    }
 }
 
-// Bias gradient: db[o] = sum_p dz[p, o].
-__global__ void k_bias_grad(const uint16_t *__restrict__ dz, int P, int per,
-                            float *__restrict__ db)
+// Bias gradient: db[o] = sum_p dz[p, o].  A block of 256 threads takes
+// `per` pixels, 16 at a time: thread (pl, cg) reads channels 8 cg .. 8 cg + 7
+// of pixel pl with one 16-byte load; the 16 pixel lanes' partial sums are
+// added in shared memory and once per block into db.
+__global__ void __launch_bounds__(256)
+    k_bias_grad(const uint16_t *__restrict__ dz, int P, int per, float *__restrict__ db)
 {
-    const int c = threadIdx.x;
+    __shared__ float red[16][kC + 1];
+    const int cg = threadIdx.x & 15, pl = threadIdx.x >> 4;
     const int p0 = blockIdx.x * per, p1 = min(P, p0 + per);
-    float a = 0.0f;
-    for (int p = p0; p < p1; ++p) a += bf16_to_f(dz[(size_t)p * kC + c]);
-    atomicAdd(db + c, a);
+    float a[8] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+    for (int p = p0 + pl; p < p1; p += 16) {
+        const uint4 u = *reinterpret_cast<const uint4 *>(dz + (size_t)p * kC + cg * 8);
+        const uint32_t w4[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            a[2 * j] += bf16_to_f(w4[j] & 0xffffu);
+            a[2 * j + 1] += bf16_to_f(w4[j] >> 16);
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) red[pl][cg * 8 + j] = a[j];
+    __syncthreads();
+    if (threadIdx.x < kC) {
+        float sum = 0.0f;
+#pragma unroll
+        for (int r = 0; r < 16; ++r) sum += red[r][threadIdx.x];
+        atomicAdd(db + threadIdx.x, sum);
+    }
 }
 
 // BF16 copies of parameter i: the flat copy and, for the weights of layers
@@ -677,7 +723,7 @@ int fire_net_backward(fire_ctx *ctx, fire_net *net, int n, const uint16_t *x,
     CUDA_TRY(ctx, cudaGetLastError(), "surrogate head");
     const int per = 256;
     const int nblk = (P + per - 1) / per;
-    k_head_grad<<<nblk, kC, 0, st>>>(net->h[kL - 1], net->theta + kHead, net->g, P,
+    k_head_grad<<<nblk, 256, 0, st>>>(net->h[kL - 1], net->theta + kHead, net->g, P,
                                      per, net->dz[kL - 1], net->grad + kHead);
     CUDA_TRY(ctx, cudaGetLastError(), "head gradient");
     const int kslabs = P / 64;
@@ -697,7 +743,7 @@ int fire_net_backward(fire_ctx *ctx, fire_net *net, int n, const uint16_t *x,
             e = tc::launch_tc_tile<128>(p, wgrad_split(9, kslabs), err, st);
         }
         CUDA_TRY(ctx, e, "weight gradient");
-        k_bias_grad<<<nblk, kC, 0, st>>>(net->dz[l], P, per, net->grad + b_off(l));
+        k_bias_grad<<<nblk, 256, 0, st>>>(net->dz[l], P, per, net->grad + b_off(l));
         CUDA_TRY(ctx, cudaGetLastError(), "bias gradient");
         if (l > 0) {
             const uint16_t *wt = net->wt + (size_t)(l - 1) * kWl;
