@@ -216,7 +216,10 @@ template <int BN> struct TcShape {
     static constexpr int kBStage = BN * kTcBK * 2;
     static constexpr int kStage = kAStage + kBStage;
     static constexpr int kSmem = 2 * kStage;
-    static constexpr int kCols = BN < 32 ? 32 : BN;
+    // tensor-memory columns: a power of two >= 32 holding BN
+    static constexpr int kCols =
+        BN <= 32 ? 32 : (BN <= 64 ? 64 : (BN <= 128 ? 128 : 256));
+    static_assert(BN % 16 == 0 && BN <= 256, "MMA N: a multiple of 16, at most 256");
 };
 
 __device__ __forceinline__ void st_shared16(uint32_t saddr, uint4 v)
