@@ -245,7 +245,6 @@ cudaError_t launch_conv_tma(int mode, const uint16_t *in, const uint16_t *w,
 cudaError_t launch_conv1_tma(const uint16_t *x, const uint16_t *w, const float *bias,
                              uint16_t *out, int n, int S, int lgS, uint32_t *err,
                              cudaStream_t st);
-int wgrad_ctas_per_sm();
 cudaError_t launch_wgrad_tma(const uint16_t *dz, const uint16_t *in, float *dw, int n,
                              int S, int lgS, int d, int split, uint32_t *err,
                              cudaStream_t st);

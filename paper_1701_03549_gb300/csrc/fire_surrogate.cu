@@ -31,6 +31,11 @@
 #include <cmath>
 #include <cstring>
 
+namespace fire {
+// CTAs of the weight-gradient kernel resident per SM (fire_conv_tma.cu).
+int wgrad_ctas_per_sm();
+}  // namespace fire
+
 using namespace fire;
 
 namespace {
