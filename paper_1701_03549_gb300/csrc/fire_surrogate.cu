@@ -186,35 +186,51 @@ template <int Cin> struct ConvWgrad {
 };
 
 // --- head: logits, probabilities, loss and the per-pixel gradient ---------
-__global__ void k_head(const uint16_t *__restrict__ h, const float *__restrict__ wh,
-                       int P, const float *__restrict__ target, float inv_count,
-                       float *__restrict__ prob, float *__restrict__ g,
-                       double *__restrict__ loss)
+// Head: z = wh[kC] + sum_c wh[c] h[p, c], prob = sigmoid(z), the mean BCE
+// loss and its per-pixel gradient g.  16 threads per pixel, each taking 8
+// channels with one 16-byte load; the partial sums meet by shuffles within
+// the 16 lanes (blockDim: a multiple of 32).
+__global__ void __launch_bounds__(256)
+    k_head(const uint16_t *__restrict__ h, const float *__restrict__ wh, int P,
+           const float *__restrict__ target, float inv_count, float *__restrict__ prob,
+           float *__restrict__ g, double *__restrict__ loss)
 {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    const int cg = threadIdx.x & 15;
+    float w[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) w[j] = wh[cg * 8 + j];
+    const float bias = wh[kC];
+    // warp-wide pixel pairs: lanes 0..15 take pixel 2 pp, lanes 16..31 pixel
+    // 2 pp + 1; the loop bound is the same for the whole warp
+    const int nw = (gridDim.x * blockDim.x) >> 5;
     float l = 0.0f;
-    if (p < P) {
-        const uint4 *hp = reinterpret_cast<const uint4 *>(h + (size_t)p * kC);
-        float z = wh[kC];
-        for (int c8 = 0; c8 < kC / 8; ++c8) {
-            const uint4 u = hp[c8];
+    for (int pp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; 2 * pp < P;
+         pp += nw) {
+        const int p = 2 * pp + ((threadIdx.x >> 4) & 1);
+        float z = 0.0f;
+        if (p < P) {
+            const uint4 u = *reinterpret_cast<const uint4 *>(h + (size_t)p * kC + cg * 8);
             const uint32_t w4[4] = {u.x, u.y, u.z, u.w};
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                z = fmaf(bf16_to_f(w4[j] & 0xffffu), wh[c8 * 8 + 2 * j], z);
-                z = fmaf(bf16_to_f(w4[j] >> 16), wh[c8 * 8 + 2 * j + 1], z);
+                z = fmaf(bf16_to_f(w4[j] & 0xffffu), w[2 * j], z);
+                z = fmaf(bf16_to_f(w4[j] >> 16), w[2 * j + 1], z);
             }
         }
-        const float y = 1.0f / (1.0f + expf(-z));
-        prob[p] = y;
-        if (target) {
-            const float t = target[p];
-            l = (fmaxf(z, 0.0f) - t * z + log1pf(expf(-fabsf(z)))) * inv_count;
-            g[p] = (y - t) * inv_count;
+#pragma unroll
+        for (int o = 8; o; o >>= 1) z += __shfl_xor_sync(0xffffffffu, z, o);
+        if (cg == 0 && p < P) {
+            z += bias;
+            const float y = 1.0f / (1.0f + expf(-z));
+            prob[p] = y;
+            if (target) {
+                const float t = target[p];
+                l += (fmaxf(z, 0.0f) - t * z + log1pf(expf(-fabsf(z)))) * inv_count;
+                g[p] = (y - t) * inv_count;
+            }
         }
     }
     if (target) {
-        // blockDim is a multiple of 32 and no thread returned early
         for (int o = 16; o; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
         if ((threadIdx.x & 31) == 0 && l != 0.0f) atomicAdd(loss, (double)l);
     }
