@@ -117,6 +117,45 @@ __device__ __forceinline__ bool pos16(uint32_t u)
     return !(u & 0x8000u) && (u & 0x7fffu);
 }
 
+// Epilogue of one accumulator row (pixel p, 128 channels in tensor memory at
+// taddr): forward, bias and ReLU; input gradient, zero where the layer
+// below's activation is not positive; BF16 stores.
+__device__ __forceinline__ void conv_epilogue(const Epi &epi, const float *s_bias,
+                                              uint32_t taddr, int p)
+{
+    uint16_t *orow = epi.out + (size_t)p * 128;
+#pragma unroll 1
+    for (int c0 = 0; c0 < 128; c0 += 32) {
+        float v[32];
+        tc::tmem_ld32(taddr + (uint32_t)c0, v);
+        uint32_t pk[16];
+        if (epi.mode == 0) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+                pk[j] = pack2(fmaxf(v[2 * j] + s_bias[c0 + 2 * j], 0.0f),
+                              fmaxf(v[2 * j + 1] + s_bias[c0 + 2 * j + 1], 0.0f));
+        } else {
+            const uint4 *hp =
+                reinterpret_cast<const uint4 *>(epi.hprev + (size_t)p * 128 + c0);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const uint4 h = hp[q];
+                const uint32_t hw[4] = {h.x, h.y, h.z, h.w};
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int e = 2 * (4 * q + j);
+                    pk[4 * q + j] = pack2(pos16(hw[j] & 0xffffu) ? v[e] : 0.0f,
+                                          pos16(hw[j] >> 16) ? v[e + 1] : 0.0f);
+                }
+            }
+        }
+        uint4 *o = reinterpret_cast<uint4 *>(orow + c0);
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            o[q] = make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
+    }
+}
+
 // sign = +1: forward (source pixel p + off(t)); -1: input gradient (p - off(t)).
 __global__ void __launch_bounds__(128, kCtasPerSm)
     k_conv_tma(const __grid_constant__ CUtensorMap act,
@@ -202,38 +241,8 @@ __global__ void __launch_bounds__(128, kCtasPerSm)
     tc::fence_after_sync();
 
     if (!s_fail) {
-        const int p = m0 + warp * 32 + lane;
-        uint16_t *orow = epi.out + (size_t)p * 128;
-#pragma unroll 1
-        for (int c0 = 0; c0 < 128; c0 += 32) {
-            float v[32];
-            tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-            uint32_t pk[16];
-            if (epi.mode == 0) {
-#pragma unroll
-                for (int j = 0; j < 16; ++j)
-                    pk[j] = pack2(fmaxf(v[2 * j] + s_bias[c0 + 2 * j], 0.0f),
-                                  fmaxf(v[2 * j + 1] + s_bias[c0 + 2 * j + 1], 0.0f));
-            } else {
-                const uint4 *hp =
-                    reinterpret_cast<const uint4 *>(epi.hprev + (size_t)p * 128 + c0);
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const uint4 h = hp[q];
-                    const uint32_t hw[4] = {h.x, h.y, h.z, h.w};
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        const int e = 2 * (4 * q + j);
-                        pk[4 * q + j] = pack2(pos16(hw[j] & 0xffffu) ? v[e] : 0.0f,
-                                              pos16(hw[j] >> 16) ? v[e + 1] : 0.0f);
-                    }
-                }
-            }
-            uint4 *o = reinterpret_cast<uint4 *>(orow + c0);
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-                o[q] = make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
-        }
+        conv_epilogue(epi, s_bias, tmem + ((uint32_t)(warp * 32) << 16),
+                      m0 + warp * 32 + lane);
     } else if (tid == 0) {
         atomicOr(err, 1u);
         // copies issued but never consumed must land before the CTA leaves
@@ -387,40 +396,9 @@ __global__ void __launch_bounds__(kPThreads, 2)
                 break;
             }
             tc::fence_after_sync();
-            const int p = tile * 128 + q * 32 + lane;
-            uint16_t *orow = epi.out + (size_t)p * 128;
-            const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * 128);
-#pragma unroll 1
-            for (int c0 = 0; c0 < 128; c0 += 32) {
-                float v[32];
-                tc::tmem_ld32(ta + (uint32_t)c0, v);
-                uint32_t pk[16];
-                if (epi.mode == 0) {
-#pragma unroll
-                    for (int j = 0; j < 16; ++j)
-                        pk[j] = pack2(fmaxf(v[2 * j] + s_bias[c0 + 2 * j], 0.0f),
-                                      fmaxf(v[2 * j + 1] + s_bias[c0 + 2 * j + 1], 0.0f));
-                } else {
-                    const uint4 *hp = reinterpret_cast<const uint4 *>(
-                        epi.hprev + (size_t)p * 128 + c0);
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const uint4 h = hp[u];
-                        const uint32_t hw[4] = {h.x, h.y, h.z, h.w};
-#pragma unroll
-                        for (int j = 0; j < 4; ++j) {
-                            const int e = 2 * (4 * u + j);
-                            pk[4 * u + j] = pack2(pos16(hw[j] & 0xffffu) ? v[e] : 0.0f,
-                                                  pos16(hw[j] >> 16) ? v[e + 1] : 0.0f);
-                        }
-                    }
-                }
-                uint4 *o = reinterpret_cast<uint4 *>(orow + c0);
-#pragma unroll
-                for (int u = 0; u < 4; ++u)
-                    o[u] = make_uint4(pk[4 * u], pk[4 * u + 1], pk[4 * u + 2],
-                                      pk[4 * u + 3]);
-            }
+            conv_epilogue(epi, s_bias,
+                          tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * 128),
+                          tile * 128 + q * 32 + lane);
             tc::fence_before_sync();
             mbar_arrive(&tempty[acc]);
         }
