@@ -435,7 +435,9 @@ def run_native(args):
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "gpu_launches": 2 * args.steps,
+            # per step: k_spread_key and k_rank_desc (longest-first order),
+            # k_simulate, k_fitness
+            "gpu_launches": 4 * args.steps,
             "clocks": ck,
         }
         print(json.dumps(line))
@@ -853,7 +855,12 @@ def run_surrogate_step(args):
                          "forward and input gradient, k_wgrad_tma, layer-1 "
                          "tile, head, Adam)",
                          "peak_source": f"bf16_tflops ({kind})"},
-            "cpu_baseline": None, "e2e": None, "gpu_launches": None,
+            "cpu_baseline": None, "e2e": None,
+            # per training step: the forward pass (first layer + seven
+            # 128 -> 128 convolutions), head and head gradient, per layer a
+            # weight gradient and a bias gradient (8 each) and, above the
+            # first, an input gradient (7), and Adam
+            "gpu_launches": 34 * args.steps,
             "clocks": ck}))
     net.free()
     ctx.close()
