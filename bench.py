@@ -353,6 +353,9 @@ def run_native(args):
     res = [fire.results_view(outs[args.warmup + j]) for j in range(args.steps)]
     steps_sum = sum(int(r["steps"].astype(np.int64).sum()) for r in res)
     trials_sum = sum(int(r["trials"].astype(np.int64).sum()) for r in res)
+    # all ranks' counts (each rank simulates its own seeds)
+    steps_all = parallel.sum_over_ranks(steps_sum, world, dev)
+    trials_all = parallel.sum_over_ranks(trials_sum, world, dev)
     assert all(int((r["status"] & (fire.STATUS_BAD_IGNITION
                                     | fire.STATUS_TIMEOUT)).max()) == 0
                for r in res)
@@ -416,11 +419,11 @@ def run_native(args):
                        "launch": {k: tuned[k] for k in (
                            "warps_per_block", "blocks_per_sm",
                            "queue_entries", "state_mode")}},
-            "cell_updates_per_s": steps_sum * H * W * world / total_s,
+            "cell_updates_per_s": steps_all * H * W / total_s,
             "cell_updates_vs_dense_sweep": _dense_sweep_roof(
-                steps_sum * H * W * world / total_s, peaks, peaks_kind),
-            "trials_per_s": trials_sum * world / total_s,
-            "mean_steps_per_sim": steps_sum / (SIMS * args.steps),
+                steps_all * H * W / total_s, peaks, peaks_kind),
+            "trials_per_s": trials_all / total_s,
+            "mean_steps_per_sim": steps_all / (SIMS * args.steps * world),
             "roofline": {"bound": "alu", "achieved": achieved / 1e12,
                          "peak": peak_ops / 1e12, "unit": "Tops/s",
                          "frac": achieved / peak_ops, "traffic": traffic,
@@ -542,6 +545,8 @@ def run_uneven(args):
     ck = clocks.stop()
     total_s = parallel.max_over_ranks(total_ms / 1e3, world, dev)
     value = n * args.steps * world / total_s
+    cells_all = parallel.sum_over_ranks(cells, world, dev)
+    trials_all = parallel.sum_over_ranks(trials_sum, world, dev)
     if rank == 0:
         peaks, peaks_kind = _peaks()
         sm_max = float(peaks.get("sm_max_mhz", 2070.0))
@@ -562,10 +567,10 @@ def run_uneven(args):
                        "launch": {k: tuned[k] for k in (
                            "warps_per_block", "blocks_per_sm",
                            "queue_entries", "state_mode")}},
-            "cell_updates_per_s": cells * world / total_s,
+            "cell_updates_per_s": cells_all / total_s,
             "cell_updates_vs_dense_sweep": _dense_sweep_roof(
-                cells * world / total_s, peaks, peaks_kind),
-            "trials_per_s": trials_sum * world / total_s,
+                cells_all / total_s, peaks, peaks_kind),
+            "trials_per_s": trials_all / total_s,
             "mean_steps_per_sim": steps_sum / (n * args.steps),
             "roofline": {"bound": "alu", "achieved": achieved / 1e12,
                          "peak": peak_ops / 1e12, "unit": "Tops/s",

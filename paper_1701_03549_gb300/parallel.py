@@ -61,6 +61,20 @@ def gather_results(results: np.ndarray, world: int):
     return np.concatenate(parts)
 
 
+def sum_over_ranks(x: int, world: int, device=None) -> int:
+    """Sum of an integer count over all ranks (a collective: every rank
+    calls it)."""
+    if world == 1:
+        return int(x)
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([int(x)], dtype=torch.int64,
+                     device=device if device is not None else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return int(t.item())
+
+
 def max_over_ranks(x: float, world: int, device=None) -> float:
     if world == 1:
         return float(x)

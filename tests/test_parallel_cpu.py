@@ -55,12 +55,13 @@ def _worker(rank, world, port, q):
         mine["steps"] = rank + 1
         allr = parallel.gather_results(mine, world)
         t = parallel.max_over_ranks(0.5 + rank, world)
-        q.put((rank, allr["burnt"].tolist(), allr["steps"].tolist(), t))
+        c = parallel.sum_over_ranks(10 ** 12 + rank, world)
+        q.put((rank, allr["burnt"].tolist(), allr["steps"].tolist(), (t, c)))
     finally:
         dist.destroy_process_group()
 
 
-def test_gather_and_max_over_two_gloo_ranks():
+def test_gather_max_and_sum_over_two_gloo_ranks():
     import torch.multiprocessing as mp
 
     ctx = mp.get_context("spawn")
@@ -77,7 +78,7 @@ def test_gather_and_max_over_two_gloo_ranks():
     for rank, burnt, steps, t in out:
         assert burnt == [3 * i for i in range(11)]
         assert steps == [1] * 6 + [2] * 5
-        assert t == 1.5
+        assert t == (1.5, 2 * 10 ** 12 + 1)
 
 
 def _shard_worker(rank, world, port, q):
