@@ -281,7 +281,8 @@ FIRE_API int fire_autotune(fire_ctx *ctx, int nmaps, const fire_map *const *maps
  * tournament selection between two individuals drawn at random (one draw per
  * new individual), one-point crossover of consecutive pairs, and per-gene
  * mutation whose probability decreases as the generations advance.
- *   genes_in[pop*genes], genes_out[pop*genes]  row-major individuals
+ *   genes_in[pop*genes], genes_out[pop*genes]  row-major individuals; the
+ *                  two must not overlap (FIRE_EINVAL)
  *   fitness[pop]   lower is better; NaN ranks last; ties go to the lower index
  *   generation / total_gens   g and NG of the schedule below
  *   ga_seed        Philox key of this GA run
@@ -320,7 +321,8 @@ FIRE_API int ignition_search(fire_ctx *ctx, const fire_map *map,
 
 /* Mean of each of `groups` runs of per_group consecutive values (the fitness
  * of a GA individual over its replicate simulations), summed in index order
- * in double precision: out[groups]. */
+ * in double precision: out[groups].  With FIRE_DEVICE_PTRS, out must not
+ * overlap values (FIRE_EINVAL); host buffers may, as they are staged. */
 FIRE_API int fire_group_mean(fire_ctx *ctx, const double *values, int groups,
                              int per_group, uint32_t flags, double *out);
 

@@ -158,9 +158,16 @@ int ga_step(fire_ctx *ctx, int pop, int genes, const double *genes_in,
     if (pop <= 0 || genes <= 0 || total_gens <= 0 || generation < 0 ||
         !genes_in || !fitness || !lo || !hi || !genes_out)
         return set_err(ctx, FIRE_EINVAL, "bad ga_step arguments");
+    const bool dev = flags & FIRE_DEVICE_PTRS;
+    {
+        // children are written while parents are read: no overlap
+        const char *a = (const char *)genes_in, *b = (const char *)genes_out;
+        const size_t len = (size_t)pop * genes * sizeof(double);
+        if (a < b + len && b < a + len)
+            return set_err(ctx, FIRE_EINVAL, "genes_out overlaps genes_in");
+    }
     int rc = ensure_device(ctx);
     if (rc) return rc;
-    const bool dev = flags & FIRE_DEVICE_PTRS;
     const size_t bg = round16((size_t)pop * genes * sizeof(double));
     const size_t bf = round16((size_t)pop * sizeof(double));
     const size_t bb = round16((size_t)genes * sizeof(double));
@@ -221,9 +228,15 @@ int fire_group_mean(fire_ctx *ctx, const double *values, int groups,
     if (groups < 0 || per_group <= 0 || !values || !out)
         return set_err(ctx, FIRE_EINVAL, "bad group-mean arguments");
     if (groups == 0) return FIRE_OK;
+    const size_t n = (size_t)groups * per_group;
+    if (flags & FIRE_DEVICE_PTRS) {
+        // one thread reads a group while another writes its mean: no overlap
+        const char *a = (const char *)values, *b = (const char *)out;
+        if (a < b + (size_t)groups * 8 && b < a + n * 8)
+            return set_err(ctx, FIRE_EINVAL, "device out overlaps values");
+    }
     int rc = ensure_device(ctx);
     if (rc) return rc;
-    const size_t n = (size_t)groups * per_group;
     const double *dv = values;
     double *dout = out;
     if (!(flags & FIRE_DEVICE_PTRS)) {

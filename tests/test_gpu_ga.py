@@ -42,11 +42,44 @@ def test_ga_step_matches_oracle(env, P, G):
         assert np.array_equal(got.view(np.uint64), want.view(np.uint64))
 
 
+def test_ga_step_rejects_overlapping_genes(env):
+    """Children are written while parents are read: an output buffer that
+    overlaps the input is an error, not a race."""
+    torch, fire, oracle, ctx = env
+    dev = torch.device("cuda")
+    genes = torch.zeros((8, 5), dtype=torch.float64, device=dev)
+    f = torch.zeros(8, dtype=torch.float64, device=dev)
+    lo = torch.full((5,), -30.0, dtype=torch.float64, device=dev)
+    hi = torch.full((5,), 30.0, dtype=torch.float64, device=dev)
+    with pytest.raises(fire.FireError):
+        fire.ga_step(ctx, genes, f, 0, 10, 1, lo, hi, device=True, out=genes)
+    with pytest.raises(fire.FireError):
+        fire.ga_step(ctx, genes[:6], f[:6], 0, 10, 1, lo, hi, device=True,
+                     out=genes[2:])
+    out = torch.empty_like(genes)
+    fire.ga_step(ctx, genes, f, 0, 10, 1, lo, hi, device=True, out=out)
+    ctx.sync()
+
+
 def test_group_mean_matches_oracle(env):
     torch, fire, oracle, ctx = env
     v = np.random.default_rng(1).normal(0, 10, 256 * 16)
     assert np.array_equal(fire.fire_group_mean(ctx, v, 16),
                           oracle.group_mean(v, 16))
+
+
+def test_group_mean_rejects_overlapping_device_buffers(env):
+    torch, fire, oracle, ctx = env
+    v = torch.arange(64, dtype=torch.float64, device="cuda")
+    with pytest.raises(fire.FireError):
+        fire.fire_group_mean(ctx, v, 4, device=True, out=v)
+    with pytest.raises(fire.FireError):
+        fire.fire_group_mean(ctx, v[:32], 4, device=True, out=v[30:38])
+    out = torch.empty(16, dtype=torch.float64, device="cuda")
+    fire.fire_group_mean(ctx, v, 4, device=True, out=out)
+    ctx.sync()
+    want = v.view(16, 4).cpu().numpy().sum(axis=1) / 4
+    assert np.array_equal(out.cpu().numpy(), want)
 
 
 def test_ga_run_matches_oracle_driven_run(env):
