@@ -327,7 +327,8 @@ FIRE_API int fire_group_mean(fire_ctx *ctx, const double *values, int groups,
                              int per_group, uint32_t flags, double *out);
 
 /* Fitness of n results (Eq. 2 or the Jaccard distance), double precision,
- * computed on the device.  A zero denominator gives NaN. */
+ * computed on the device.  A zero denominator gives NaN.  With
+ * FIRE_DEVICE_PTRS, out must not overlap results (FIRE_EINVAL). */
 FIRE_API int fire_fitness(fire_ctx *ctx, const fire_result *results, int n, int kind,
                  uint32_t flags, double *out);
 

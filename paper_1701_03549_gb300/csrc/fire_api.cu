@@ -564,6 +564,12 @@ int fire_fitness(fire_ctx *ctx, const fire_result *results, int n, int kind,
     if (n < 0 || !results || !out || (kind != 0 && kind != 1))
         return set_err(ctx, FIRE_EINVAL, "bad fitness arguments");
     if (n == 0) return FIRE_OK;
+    if (flags & FIRE_DEVICE_PTRS) {
+        // out[i] would land inside results[i / 3], read by another thread
+        const char *a = (const char *)results, *b = (const char *)out;
+        if (a < b + (size_t)n * 8 && b < a + (size_t)n * sizeof(fire_result))
+            return set_err(ctx, FIRE_EINVAL, "device out overlaps results");
+    }
     int rc = ensure_device(ctx);
     if (rc) return rc;
     if (flags & FIRE_DEVICE_PTRS) {

@@ -355,6 +355,22 @@ def test_fitness_matches_oracle(ctx, orc):
         assert np.array_equal(got, np.asarray(want))
 
 
+def test_fitness_rejects_overlapping_device_buffers(ctx):
+    import torch
+
+    from paper_1701_03549_gb300 import fire
+
+    res = torch.ones((12, 6), dtype=torch.int32, device="cuda")
+    res[:, 0] = 2   # |A*| = 2, |A n A*| = 1, |A| = 1: delta = 1
+    alias = res.view(torch.float64).view(-1)[:12]   # same bytes as res
+    with pytest.raises(fire.FireError):
+        fire.fire_fitness(ctx, res, 0, device=True, out=alias)
+    out = torch.empty(12, dtype=torch.float64, device="cuda")
+    fire.fire_fitness(ctx, res, 0, device=True, out=out)
+    ctx.sync()
+    assert torch.all(out == 1.0)
+
+
 def test_bad_host_ignition_is_rejected(ctx):
     from paper_1701_03549_gb300 import fire
 
