@@ -149,17 +149,24 @@ class Clocks:
             self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
-        rows = []
         with open(self.path) as f:
-            for line in f:
-                parts = [x.strip() for x in line.split(",")]
-                if len(parts) != 7:
-                    continue
-                try:
-                    rows.append((float(parts[0]), float(parts[1]), parts[3:]))
-                except ValueError:
-                    continue
+            lines = f.readlines()
         os.unlink(self.path)
+        return self.summarise(lines)
+
+    @staticmethod
+    def summarise(lines):
+        """Median and maximum SM clock and the throttle reasons seen, from
+        the sampler's CSV rows (malformed rows are skipped)."""
+        rows = []
+        for line in lines:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) != 7:
+                continue
+            try:
+                rows.append((float(parts[0]), float(parts[1]), parts[3:]))
+            except ValueError:
+                continue
         if not rows:
             return None
         names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
