@@ -180,6 +180,60 @@ def _host(a, dtype):
     return np.ascontiguousarray(a, dtype=dtype)
 
 
+# torch dtype names accepted for each device-buffer type of fire.h
+_F64, _F32, _I32, _U8 = ("float64",), ("float32",), ("int32",), ("uint8",)
+_RES = ("int32", "uint32")       # fire_result words (bit patterns)
+_SEED = ("int64", "uint64")      # uint64 seeds (bit patterns)
+_BF16 = ("bfloat16",)
+
+
+def _dev(ctx, t, name, dtypes, numel, allow_none=False):
+    """Pointer of a device-mode argument, after the checks the library cannot
+    make through a plain pointer: a contiguous CUDA tensor on the context's
+    device, of one of `dtypes` (torch dtype names), holding exactly `numel`
+    elements, the count the call reads or writes.  Any other tensor would be
+    accessed past its end; it raises FireError(FIRE_EINVAL) instead."""
+    def bad(msg):
+        return FireError(FIRE_EINVAL, f"{name}: {msg}")
+    if t is None:
+        if allow_none:
+            return None
+        raise bad("a CUDA tensor is required")
+    if not _is_tensor(t) or not t.is_cuda:
+        raise bad("expected a CUDA tensor")
+    if t.device.index != ctx.device:
+        raise bad(f"on cuda:{t.device.index}, the context is on "
+                  f"cuda:{ctx.device}")
+    dt = str(t.dtype).rpartition(".")[2]
+    if dt not in dtypes:
+        raise bad(f"dtype {dt}, expected {' or '.join(dtypes)}")
+    if t.numel() != numel:
+        raise bad(f"{t.numel()} elements, expected {numel}")
+    if not t.is_contiguous():
+        raise bad("tensor must be contiguous")
+    return t.data_ptr()
+
+
+def _rows(ctx, t, name, width):
+    """Leading dimension n of a device tensor of n rows of `width` values."""
+    if not _is_tensor(t) or t.dim() < 1:
+        raise FireError(FIRE_EINVAL, f"{name}: expected a CUDA tensor")
+    n = int(t.shape[0])
+    if t.numel() != n * width:
+        raise FireError(FIRE_EINVAL, f"{name}: expected {width} values per "
+                        f"row, got shape {tuple(t.shape)}")
+    return n
+
+
+def _host_plane(a, dtype, H, W, name):
+    """A host raster as a C-contiguous (H, W) array of `dtype`."""
+    a = _host(a, dtype)
+    if a.shape != (H, W):
+        raise FireError(FIRE_EINVAL, f"{name}: shape {a.shape}, expected "
+                        f"{(H, W)}")
+    return a
+
+
 class Context:
     """A libfire context (fire_create) bound to one device and stream."""
 
@@ -234,20 +288,22 @@ class Context:
     # -- maps
     def maps_upload(self, veg, elev, slope, aspect, wind, cell_m=30.0,
                     device=False):
+        names = ("veg", "elev", "slope", "aspect", "wind")
         if device:
-            arrs = (veg, elev, slope, aspect, wind)
             H, W = veg.shape
+            ptrs = [_dev(self, a, nm, _U8 if nm == "veg" else _F32, H * W)
+                    for nm, a in zip(names, (veg, elev, slope, aspect, wind))]
             flags = FIRE_DEVICE_PTRS
         else:
-            arrs = (_host(veg, np.uint8), _host(elev, np.float32),
-                    _host(slope, np.float32), _host(aspect, np.float32),
-                    _host(wind, np.float32))
-            H, W = arrs[0].shape
+            H, W = np.shape(veg)
+            arrs = [_host_plane(a, np.uint8 if nm == "veg" else np.float32,
+                                H, W, nm)
+                    for nm, a in zip(names, (veg, elev, slope, aspect, wind))]
+            ptrs = [_ptr(a) for a in arrs]
             flags = 0
         h = C.c_void_p()
         self.check(self.lib.fire_maps_upload(
-            self.h, H, W, float(cell_m), *[_ptr(a) for a in arrs], flags,
-            C.byref(h)))
+            self.h, H, W, float(cell_m), *ptrs, flags, C.byref(h)))
         return Map(self, h, H, W)
 
     def landscape_upload(self, land):
@@ -274,12 +330,29 @@ class Map:
         except Exception:
             pass
 
+    def _sim_args(self, params, ignitions, seeds, out, burn_step, want_steps):
+        """Checked device pointers of a batch of n = params rows: params (n,
+        5) float64, ignitions (n, 2) int32, seeds (n,) int64 or uint64, out
+        (n, 6) int32 or uint32, burn_step (n, H, W) int32 (required with
+        want_steps)."""
+        ctx = self.ctx
+        n = _rows(ctx, params, "params", 5)
+        return n, (_dev(ctx, params, "params", _F64, 5 * n),
+                   _dev(ctx, ignitions, "ignitions", _I32, 2 * n),
+                   _dev(ctx, seeds, "seeds", _SEED, n),
+                   _dev(ctx, out, "out", _RES, 6 * n),
+                   _dev(ctx, burn_step, "burn_step", _I32,
+                        n * self.H * self.W, allow_none=not want_steps))
+
     def target_upload(self, burnt, device=False):
         if device:
             self.ctx.check(self.ctx.lib.fire_target_upload(
-                self.ctx.h, self.h, _ptr(burnt), FIRE_DEVICE_PTRS))
+                self.ctx.h, self.h,
+                _dev(self.ctx, burnt, "burnt", ("uint8", "bool"),
+                     self.H * self.W), FIRE_DEVICE_PTRS))
         else:
-            b = _host(np.asarray(burnt) != 0, np.uint8)
+            b = _host_plane(np.asarray(burnt) != 0, np.uint8, self.H, self.W,
+                            "burnt")
             self.ctx.check(self.ctx.lib.fire_target_upload(
                 self.ctx.h, self.h, _ptr(b), 0))
 
@@ -300,12 +373,12 @@ class Map:
         flags |= FIRE_CELL_UNIFORM if cell_uniform else 0
         flags |= FIRE_LONGEST_FIRST if longest_first else 0
         if device:
-            n = int(params.shape[0])
+            n, (pp, pg, ps, po, pb) = self._sim_args(
+                params, ignitions, seeds, out, burn_step, want_steps)
             flags |= FIRE_DEVICE_PTRS | (FIRE_SYNC if sync else 0)
             self.ctx.check(lib.fire_simulate_batch(
-                self.ctx.h, self.h, n, _ptr(params), _ptr(ignitions),
-                _ptr(seeds), int(max_steps), flags, _ptr(out),
-                _ptr(burn_step)))
+                self.ctx.h, self.h, n, pp, pg, ps, int(max_steps), flags, po,
+                pb))
             return out, burn_step
         p = _host(params, np.float64).reshape(-1, 5)
         n = p.shape[0]
@@ -326,12 +399,13 @@ class Map:
         lib = self.ctx.lib
         flags = FIRE_WANT_STEPS if want_steps else 0
         if device:
-            n = int(params.shape[0])
+            n, (pp, pg, ps, po, pb) = self._sim_args(
+                params, ignitions, seeds, out, burn_step, want_steps)
+            pt = _dev(self.ctx, burn_time, "burn_time", _U8, self.H * self.W)
             flags |= FIRE_DEVICE_PTRS | (FIRE_SYNC if sync else 0)
             self.ctx.check(lib.fire_simulate_burnout(
-                self.ctx.h, self.h, n, _ptr(params), _ptr(ignitions),
-                _ptr(seeds), _ptr(burn_time), int(max_steps), flags, _ptr(out),
-                _ptr(burn_step)))
+                self.ctx.h, self.h, n, pp, pg, ps, pt, int(max_steps), flags,
+                po, pb))
             return out, burn_step
         p = _host(params, np.float64).reshape(-1, 5)
         n = p.shape[0]
@@ -352,10 +426,10 @@ class Map:
         mode of simulate_batch); the library allocates nothing."""
         flags = (FIRE_WANT_STEPS if want_steps else 0) | FIRE_DEVICE_PTRS
         flags |= FIRE_SYNC if sync else 0
+        n, (pp, pg, ps, po, pb) = self._sim_args(
+            params, ignitions, seeds, out, burn_step, want_steps)
         self.ctx.check(self.ctx.lib.fire_simulate_batch_noalloc(
-            self.ctx.h, self.h, int(params.shape[0]), _ptr(params),
-            _ptr(ignitions), _ptr(seeds), int(max_steps), flags, _ptr(out),
-            _ptr(burn_step)))
+            self.ctx.h, self.h, n, pp, pg, ps, int(max_steps), flags, po, pb))
         return out, burn_step
 
     def thresholds(self, beta):
@@ -430,13 +504,18 @@ def fire_simulate_multi(ctx: Context, maps, map_of_sim, params, ignitions,
     lib = ctx.lib
     handles = _map_handles(maps)
     if device:
-        n = int(params.shape[0])
+        n = _rows(ctx, params, "params", 5)
+        ptrs = (_dev(ctx, map_of_sim, "map_of_sim", _I32, n),
+                _dev(ctx, params, "params", _F64, 5 * n),
+                _dev(ctx, ignitions, "ignitions", _I32, 2 * n),
+                _dev(ctx, seeds, "seeds", _SEED, n),
+                _dev(ctx, out, "out", _RES, 6 * n))
         flags = FIRE_DEVICE_PTRS | (FIRE_GRAPH if graph else 0)
         flags |= FIRE_SYNC if sync else 0
         flags |= FIRE_CELL_UNIFORM if cell_uniform else 0
         ctx.check(lib.fire_simulate_multi(
-            ctx.h, len(maps), handles, _ptr(map_of_sim), n, _ptr(params),
-            _ptr(ignitions), _ptr(seeds), int(max_steps), flags, _ptr(out)))
+            ctx.h, len(maps), handles, ptrs[0], n, *ptrs[1:4],
+            int(max_steps), flags, ptrs[4]))
         return out
     p = _host(params, np.float64).reshape(-1, 5)
     n = p.shape[0]
@@ -460,15 +539,19 @@ def fire_autotune(ctx: Context, maps, map_of_sim, params, ignitions, seeds,
     best = FireLaunch()
     lpt = FIRE_LONGEST_FIRST if longest_first else 0
     if device:
-        n = int(params.shape[0])
+        n = _rows(ctx, params, "params", 5)
         ctx.check(lib.fire_autotune(
-            ctx.h, len(maps), handles, _ptr(map_of_sim), n, _ptr(params),
-            _ptr(ignitions), _ptr(seeds), FIRE_DEVICE_PTRS | lpt,
+            ctx.h, len(maps), handles,
+            _dev(ctx, map_of_sim, "map_of_sim", _I32, n, allow_none=True), n,
+            _dev(ctx, params, "params", _F64, 5 * n),
+            _dev(ctx, ignitions, "ignitions", _I32, 2 * n),
+            _dev(ctx, seeds, "seeds", _SEED, n), FIRE_DEVICE_PTRS | lpt,
             C.byref(best)))
     else:
         p = _host(params, np.float64).reshape(-1, 5)
         n = p.shape[0]
-        mi = None if map_of_sim is None else _host(map_of_sim, np.int32)
+        mi = (None if map_of_sim is None
+              else _host(map_of_sim, np.int32).reshape(n))
         g = _host(ignitions, np.int32).reshape(n, 2)
         s = _host(seeds, np.uint64).reshape(n)
         ctx.check(lib.fire_autotune(
@@ -484,10 +567,16 @@ def ga_step(ctx: Context, genes, fitness, generation, total_gens, ga_seed,
     preallocated `out` like genes."""
     lib = ctx.lib
     if device:
+        if not _is_tensor(genes) or genes.dim() != 2:
+            raise FireError(FIRE_EINVAL, "genes: expected a (P, G) tensor")
         P, G = int(genes.shape[0]), int(genes.shape[1])
-        ctx.check(lib.ga_step(ctx.h, P, G, _ptr(genes), _ptr(fitness),
+        ctx.check(lib.ga_step(ctx.h, P, G,
+                              _dev(ctx, genes, "genes", _F64, P * G),
+                              _dev(ctx, fitness, "fitness", _F64, P),
                               int(generation), int(total_gens), int(ga_seed),
-                              _ptr(lo), _ptr(hi), FIRE_DEVICE_PTRS, _ptr(out)))
+                              _dev(ctx, lo, "lo", _F64, G),
+                              _dev(ctx, hi, "hi", _F64, G), FIRE_DEVICE_PTRS,
+                              _dev(ctx, out, "out", _F64, P * G)))
         return out
     g = _host(genes, np.float64)
     P, G = g.shape
@@ -520,10 +609,15 @@ def ignition_search(ctx: Context, m: Map, beta, lat_h, lat_w, reps, seed,
 def fire_group_mean(ctx: Context, values, per_group, device=False, out=None):
     lib = ctx.lib
     if device:
-        groups = int(values.numel()) // int(per_group)
-        ctx.check(lib.fire_group_mean(ctx.h, _ptr(values), groups,
-                                      int(per_group), FIRE_DEVICE_PTRS,
-                                      _ptr(out)))
+        nv = int(values.numel()) if _is_tensor(values) else -1
+        if per_group <= 0 or nv % int(per_group):
+            raise FireError(FIRE_EINVAL, f"values: {nv} values are not whole "
+                            f"groups of {per_group}")
+        groups = nv // int(per_group)
+        ctx.check(lib.fire_group_mean(ctx.h,
+                                      _dev(ctx, values, "values", _F64, nv),
+                                      groups, int(per_group), FIRE_DEVICE_PTRS,
+                                      _dev(ctx, out, "out", _F64, groups)))
         return out
     v = _host(values, np.float64).ravel()
     groups = v.size // int(per_group)
@@ -537,9 +631,11 @@ def fire_fitness(ctx: Context, results, kind=FITNESS_PAPER_DELTA,
                  device=False, out=None):
     lib = ctx.lib
     if device:
-        n = int(results.shape[0])
-        ctx.check(lib.fire_fitness(ctx.h, _ptr(results), n, int(kind),
-                                   FIRE_DEVICE_PTRS, _ptr(out)))
+        n = _rows(ctx, results, "results", 6)
+        ctx.check(lib.fire_fitness(ctx.h,
+                                   _dev(ctx, results, "results", _RES, 6 * n),
+                                   n, int(kind), FIRE_DEVICE_PTRS,
+                                   _dev(ctx, out, "out", _F64, n)))
         return out
     r = np.ascontiguousarray(results, RESULT_DTYPE)
     o = np.zeros(r.shape[0], np.float64)
@@ -591,8 +687,12 @@ def fire_tc_gemm(ctx: Context, A, B, M: int, N: int, K: int, out,
     A[K, M]; B[N, K] or, b_mn, B[K, N]); out float32 [M, N]."""
     flags = FIRE_DEVICE_PTRS | (FIRE_SYNC if sync else 0)
     flags |= (FIRE_TC_A_MN if a_mn else 0) | (FIRE_TC_B_MN if b_mn else 0)
-    ctx.check(ctx.lib.fire_tc_gemm(ctx.h, int(M), int(N), int(K), _ptr(A),
-                                   _ptr(B), int(ksplit), flags, _ptr(out)))
+    M, N, K = int(M), int(N), int(K)
+    ctx.check(ctx.lib.fire_tc_gemm(ctx.h, M, N, K,
+                                   _dev(ctx, A, "A", _BF16, M * K),
+                                   _dev(ctx, B, "B", _BF16, N * K),
+                                   int(ksplit), flags,
+                                   _dev(ctx, out, "out", _F32, M * N)))
     return out
 
 
@@ -638,10 +738,13 @@ class Net:
         """theta: float32 numpy array or CUDA tensor of param_count."""
         if _is_tensor(theta):
             self.ctx.check(self.ctx.lib.fire_net_set_params(
-                self.ctx.h, self.h, _ptr(theta), FIRE_DEVICE_PTRS))
+                self.ctx.h, self.h, _dev(self.ctx, theta, "theta", _F32,
+                                         self.P), FIRE_DEVICE_PTRS))
         else:
             t = _host(theta, np.float32).ravel()
-            assert t.size == self.P
+            if t.size != self.P:
+                raise FireError(FIRE_EINVAL, f"theta: {t.size} values, "
+                                f"expected {self.P}")
             self.ctx.check(self.ctx.lib.fire_net_set_params(
                 self.ctx.h, self.h, _ptr(t), 0))
 
@@ -651,18 +754,26 @@ class Net:
                                                  int(which), 0, _ptr(out)))
         return out
 
+    def _x(self, x):
+        """Sample count and pointer of inputs x (n, S, S, 16) bfloat16."""
+        n = _rows(self.ctx, x, "x", self.S * self.S * NET_CIN)
+        return n, _dev(self.ctx, x, "x", _BF16, n * self.S * self.S * NET_CIN)
+
     def forward(self, x, prob, sync=False):
-        n = int(x.shape[0])
+        n, px = self._x(x)
         self.ctx.check(self.ctx.lib.fire_net_forward(
-            self.ctx.h, self.h, n, _ptr(x),
-            FIRE_DEVICE_PTRS | (FIRE_SYNC if sync else 0), _ptr(prob)))
+            self.ctx.h, self.h, n, px,
+            FIRE_DEVICE_PTRS | (FIRE_SYNC if sync else 0),
+            _dev(self.ctx, prob, "prob", _F32, n * self.S * self.S)))
         return prob
 
     def backward(self, x, target, loss=None, sync=False):
-        n = int(x.shape[0])
+        n, px = self._x(x)
         self.ctx.check(self.ctx.lib.fire_net_backward(
-            self.ctx.h, self.h, n, _ptr(x), _ptr(target),
-            FIRE_DEVICE_PTRS | (FIRE_SYNC if sync else 0), _ptr(loss)))
+            self.ctx.h, self.h, n, px,
+            _dev(self.ctx, target, "target", _F32, n * self.S * self.S),
+            FIRE_DEVICE_PTRS | (FIRE_SYNC if sync else 0),
+            _dev(self.ctx, loss, "loss", _F64, 1, allow_none=True)))
         return loss
 
     def adam(self, lr: float, sync=False):
@@ -670,54 +781,80 @@ class Net:
             self.ctx.h, self.h, float(lr), FIRE_SYNC if sync else 0))
 
     def buffer(self, which, layer, n, out):
+        px = int(n) * self.S * self.S
+        if which == BUF_PROB:
+            po = _dev(self.ctx, out, "out", _F32, px)
+        else:
+            po = _dev(self.ctx, out, "out", _BF16, px * NET_C)
         self.ctx.check(self.ctx.lib.fire_net_buffer(
             self.ctx.h, self.h, int(which), int(layer), int(n),
-            FIRE_DEVICE_PTRS, _ptr(out)))
+            FIRE_DEVICE_PTRS, po))
         return out
 
 
 def fire_net_planes(ctx: Context, S: int, veg, slope, aspect, wind, out,
                     sync=False):
-    H, W = veg.shape
+    H, W = int(veg.shape[0]), int(veg.shape[1])
+    S = int(S)
     ctx.check(ctx.lib.fire_net_planes(
-        ctx.h, int(H), int(W), int(S), _ptr(veg), _ptr(slope), _ptr(aspect),
-        _ptr(wind), FIRE_DEVICE_PTRS | (FIRE_SYNC if sync else 0), _ptr(out)))
+        ctx.h, H, W, S, _dev(ctx, veg, "veg", _U8, H * W),
+        _dev(ctx, slope, "slope", _F32, H * W),
+        _dev(ctx, aspect, "aspect", _F32, H * W),
+        _dev(ctx, wind, "wind", _F32, H * W),
+        FIRE_DEVICE_PTRS | (FIRE_SYNC if sync else 0),
+        _dev(ctx, out, "out", _F32, S * S * 10)))
     return out
 
 
 def fire_net_inputs(ctx: Context, S: int, H: int, W: int, planes, params,
                     ign, out, sync=False):
-    n = int(params.shape[0])
+    n = _rows(ctx, params, "params", 5)
+    S = int(S)
     ctx.check(ctx.lib.fire_net_inputs(
-        ctx.h, int(S), int(H), int(W), n, _ptr(planes), _ptr(params),
-        _ptr(ign), FIRE_DEVICE_PTRS | (FIRE_SYNC if sync else 0), _ptr(out)))
+        ctx.h, S, int(H), int(W), n,
+        _dev(ctx, planes, "planes", _F32, S * S * 10),
+        _dev(ctx, params, "params", _F64, 5 * n),
+        _dev(ctx, ign, "ign", _I32, 2 * n),
+        FIRE_DEVICE_PTRS | (FIRE_SYNC if sync else 0),
+        _dev(ctx, out, "out", _BF16, n * S * S * NET_CIN)))
     return out
 
 
 def fire_net_labels(ctx: Context, m: Map, S: int, params, ign, reps: int,
                     seed: int, labels, results=None, max_steps=0,
                     cell_uniform=False, sync=False):
-    groups = int(params.shape[0])
+    groups = _rows(ctx, params, "params", 5)
+    S, reps = int(S), int(reps)
     flags = FIRE_DEVICE_PTRS | (FIRE_SYNC if sync else 0)
     flags |= FIRE_CELL_UNIFORM if cell_uniform else 0
     ctx.check(ctx.lib.fire_net_labels(
-        ctx.h, m.h, int(S), groups, int(reps), _ptr(params), _ptr(ign),
-        int(seed), int(max_steps), flags, _ptr(labels), _ptr(results)))
+        ctx.h, m.h, S, groups, reps,
+        _dev(ctx, params, "params", _F64, 5 * groups),
+        _dev(ctx, ign, "ign", _I32, 2 * groups),
+        int(seed), int(max_steps), flags,
+        _dev(ctx, labels, "labels", _F32, groups * S * S),
+        _dev(ctx, results, "results", _RES, 6 * groups * max(reps, 0),
+             allow_none=True)))
     return labels
 
 
 def fire_net_target_frac(ctx: Context, m: Map, S: int, out, sync=False):
+    S = int(S)
     ctx.check(ctx.lib.fire_net_target_frac(
-        ctx.h, m.h, int(S), FIRE_DEVICE_PTRS | (FIRE_SYNC if sync else 0),
-        _ptr(out)))
+        ctx.h, m.h, S, FIRE_DEVICE_PTRS | (FIRE_SYNC if sync else 0),
+        _dev(ctx, out, "out", _F32, S * S)))
     return out
 
 
 def fire_net_screen(ctx: Context, S: int, prob, target_frac, cells: float,
                     kind: int, keep: int, pred, keep_idx=None, sync=False):
-    n = int(prob.shape[0])
+    S = int(S)
+    n = _rows(ctx, prob, "prob", S * S)
     ctx.check(ctx.lib.fire_net_screen(
-        ctx.h, int(S), n, _ptr(prob), _ptr(target_frac), float(cells),
+        ctx.h, S, n, _dev(ctx, prob, "prob", _F32, n * S * S),
+        _dev(ctx, target_frac, "target_frac", _F32, S * S), float(cells),
         int(kind), int(keep), FIRE_DEVICE_PTRS | (FIRE_SYNC if sync else 0),
-        _ptr(pred), _ptr(keep_idx)))
+        _dev(ctx, pred, "pred", _F64, n),
+        _dev(ctx, keep_idx, "keep_idx", _I32, max(int(keep), 0),
+             allow_none=True)))
     return pred, keep_idx

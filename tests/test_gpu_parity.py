@@ -371,6 +371,32 @@ def test_fitness_rejects_overlapping_device_buffers(ctx):
     assert torch.all(out == 1.0)
 
 
+def test_mistyped_device_buffers_are_rejected(ctx):
+    """A device buffer of the wrong dtype, size or place is refused by the
+    binding before any kernel could read past its end."""
+    import torch
+
+    from paper_1701_03549_gb300 import fire
+
+    land = synth.landscape(40, 40, seed=1)
+    m = ctx.landscape_upload(land)
+    n = 4
+    ign = synth.centre_ignition(land.veg)
+    p = torch.tensor(np.tile(TRUTH, (n, 1)), device="cuda")
+    g = torch.tensor(np.tile(np.asarray(ign, np.int32), (n, 1)), device="cuda")
+    s = torch.arange(n, dtype=torch.int64, device="cuda")
+    out = torch.zeros((n, 6), dtype=torch.int32, device="cuda")
+    for args in ((p.float(), g, s, out), (p, g.long(), s, out),
+                 (p, g, s[:3], out), (p, g, s, out[:3]),
+                 (p, g, s.cpu(), out), (p, g, s, out.t())):
+        with pytest.raises(fire.FireError):
+            m.simulate_batch(*args[:3], device=True, out=args[3], sync=True)
+    assert torch.all(out == 0)
+    m.simulate_batch(p, g, s, device=True, out=out, sync=True)
+    assert torch.all(out[:, 0] > 0)
+    m.free()
+
+
 def test_bad_host_ignition_is_rejected(ctx):
     from paper_1701_03549_gb300 import fire
 
