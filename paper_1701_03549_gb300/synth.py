@@ -156,6 +156,26 @@ def landscape(H: int, W: int, seed: int, wind_seed: int | None = None,
     )
 
 
+def noise_landscape(H: int, W: int, seed: int) -> Landscape:
+    """Independent random rasters (no spatial structure), cheap at any size:
+    fuel codes 1..4 with 10 % of cells non-burnable, elevation in [0, 2000)
+    m, slope in [0, 45) degrees, aspect and wind bearings in [0, 360).  For
+    size and edge cases, where the hills of landscape() would take longer
+    to generate than the fires take to run."""
+    rng = np.random.default_rng(seed)
+    veg = rng.integers(1, 5, (H, W), dtype=np.uint8)
+    veg[rng.random((H, W)) < 0.1] = 0
+    f32 = np.float32
+    return Landscape(
+        veg=veg,
+        elev=(rng.random((H, W), dtype=f32) * f32(2000.0)),
+        slope=(rng.random((H, W), dtype=f32) * f32(45.0)),
+        aspect=(rng.random((H, W), dtype=f32) * f32(360.0)),
+        wind=(rng.random((H, W), dtype=f32) * f32(360.0)),
+        meta={"H": H, "W": W, "seed": seed, "kind": "noise"},
+    )
+
+
 def uniform_landscape(H: int, W: int, veg_code: int = 2, wind_deg: float = 0.0,
                       elev: float = 100.0) -> Landscape:
     """Flat, fully burnable terrain (for closed-form checks)."""
