@@ -102,8 +102,8 @@ def _run_max(k):
     return r, idx, bs.ravel()[idx]
 
 
-def _pool(init, initargs=()):
-    return mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1),
+def _pool(init, initargs=(), procs=16):
+    return mp.get_context("spawn").Pool(min(procs, os.cpu_count() or 1),
                                         initializer=init, initargs=initargs)
 
 
@@ -258,7 +258,7 @@ def test_maximum_grid(env):
     from paper_1701_03549_gb300 import fire
 
     seed = 4242
-    pool = _pool(_init_max, (seed,))   # before the first GPU call
+    pool = _pool(_init_max, (seed,), len(MAX_SIMS))   # before any GPU call
     try:
         land, target = _max_land(seed)
         ctx = fire.Context(0)
