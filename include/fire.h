@@ -50,6 +50,8 @@
  *     may be used by one host thread at a time.
  *   Limits: H, W >= 1; the grid is processed in 32 x 32 tiles and at most
  *     FIRE_MAX_TILES tiles are supported; n <= 2^31 - 1 simulations per call.
+ *     A batch of n = 0 (simulations, results, groups) returns FIRE_OK at once
+ *     and touches no buffer, so its pointers may be NULL.
  */
 #ifndef FIRE_H
 #define FIRE_H

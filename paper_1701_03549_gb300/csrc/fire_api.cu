@@ -561,9 +561,10 @@ int fire_fitness(fire_ctx *ctx, const fire_result *results, int n, int kind,
                  uint32_t flags, double *out)
 {
     if (!ctx) return FIRE_EINVAL;
-    if (n < 0 || !results || !out || (kind != 0 && kind != 1))
+    if (n < 0 || (kind != 0 && kind != 1))
         return set_err(ctx, FIRE_EINVAL, "bad fitness arguments");
     if (n == 0) return FIRE_OK;
+    if (!results || !out) return set_err(ctx, FIRE_EINVAL, "NULL argument");
     if (flags & FIRE_DEVICE_PTRS) {
         // out[i] would land inside results[i / 3], read by another thread
         const char *a = (const char *)results, *b = (const char *)out;

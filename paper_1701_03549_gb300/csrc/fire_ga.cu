@@ -225,9 +225,10 @@ int fire_group_mean(fire_ctx *ctx, const double *values, int groups,
                     int per_group, uint32_t flags, double *out)
 {
     if (!ctx) return FIRE_EINVAL;
-    if (groups < 0 || per_group <= 0 || !values || !out)
+    if (groups < 0 || per_group <= 0)
         return set_err(ctx, FIRE_EINVAL, "bad group-mean arguments");
     if (groups == 0) return FIRE_OK;
+    if (!values || !out) return set_err(ctx, FIRE_EINVAL, "NULL argument");
     const size_t n = (size_t)groups * per_group;
     if (flags & FIRE_DEVICE_PTRS) {
         // one thread reads a group while another writes its mean: no overlap

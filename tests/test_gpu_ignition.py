@@ -27,7 +27,8 @@ def env():
 
 @pytest.mark.parametrize("shape,lat,reps,kind,cutoff", [
     ((60, 70), (4, 5), 3, 0, 1.5), ((96, 64), (6, 6), 2, 1, 0.4),
-    ((33, 47), (3, 2), 4, 0, -1.0), ((128, 128), (8, 8), 2, 0, np.inf)])
+    ((33, 47), (3, 2), 4, 0, -1.0), ((128, 128), (8, 8), 2, 0, np.inf),
+    ((40, 50), (1, 1), 1, 1, 0.5)])
 def test_ignition_search_matches_oracle(env, shape, lat, reps, kind, cutoff):
     fire, oracle, ctx = env
     H, W = shape
@@ -46,6 +47,26 @@ def test_ignition_search_matches_oracle(env, shape, lat, reps, kind, cutoff):
     assert np.array_equal(cells, ocells)
     assert np.array_equal(fm, ofm)
     assert np.array_equal(xy, oxy)
+    m.free()
+
+
+def test_single_cell_target(env):
+    """A target of one burnable cell: its bounding box is that cell, so
+    every lattice point snaps to it and every candidate is the same fire."""
+    fire, oracle, ctx = env
+    land = synth.landscape(48, 40, seed=5, wind_seed=5)
+    r, c = np.argwhere(land.veg != 0)[len(np.argwhere(land.veg != 0)) // 2]
+    target = np.zeros(land.veg.shape, bool)
+    target[r, c] = True
+    beta = np.array([-0.5, 0.5, 0.5, 1.0, -1.0])
+    m = ctx.landscape_upload(land)
+    m.target_upload(target)
+    fm, cells, xy = fire.ignition_search(ctx, m, beta, 3, 3, 2, 5, 0, 1.5)
+    F = oracle.Features(land)
+    ofm, ocells, oxy = F.ignition_search(target, beta, 3, 3, 2, 5, 0, 1.5)
+    assert np.array_equal(cells, ocells) and np.array_equal(fm, ofm)
+    assert np.array_equal(xy, oxy)
+    assert (cells.reshape(-1, 2) == [r, c]).all()
     m.free()
 
 

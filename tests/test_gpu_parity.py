@@ -397,6 +397,40 @@ def test_mistyped_device_buffers_are_rejected(ctx):
     m.free()
 
 
+def test_empty_batches(ctx):
+    """n = 0 on every batch entry point, host and device: nothing runs and
+    nothing is written."""
+    import torch
+
+    from paper_1701_03549_gb300 import fire
+
+    land = synth.landscape(40, 40, seed=2)
+    m = ctx.landscape_upload(land)
+    e = np.zeros((0, 5)), np.zeros((0, 2), np.int32), np.zeros(0, np.uint64)
+    res, _ = m.simulate_batch(*e)
+    assert res.shape == (0,)
+    res, _ = m.simulate_burnout(*e, np.ones((40, 40), np.uint8))
+    assert res.shape == (0,)
+    assert fire.fire_simulate_multi(ctx, [m], np.zeros(0, np.int32),
+                                    *e).shape == (0,)
+    assert fire.fire_fitness(ctx, np.zeros(0, fire.RESULT_DTYPE)).shape == (0,)
+    assert fire.fire_group_mean(ctx, np.zeros(0), 4).shape == (0,)
+    d = dict(device="cuda")
+    p = torch.zeros((0, 5), dtype=torch.float64, **d)
+    g = torch.zeros((0, 2), dtype=torch.int32, **d)
+    s = torch.zeros(0, dtype=torch.int64, **d)
+    out = torch.zeros((0, 6), dtype=torch.int32, **d)
+    m.simulate_batch(p, g, s, device=True, out=out, sync=True)
+    m.simulate_batch_noalloc(p, g, s, out)
+    fire.fire_simulate_multi(ctx, [m], torch.zeros(0, dtype=torch.int32, **d),
+                             p, g, s, device=True, out=out, graph=True,
+                             sync=True)
+    fire.fire_fitness(ctx, out, 0, device=True,
+                      out=torch.zeros(0, dtype=torch.float64, **d))
+    ctx.sync()
+    m.free()
+
+
 def test_bad_host_ignition_is_rejected(ctx):
     from paper_1701_03549_gb300 import fire
 
