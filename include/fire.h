@@ -412,6 +412,16 @@ FIRE_API int fire_simulate_burnout(fire_ctx *ctx, const fire_map *map, int n,
 FIRE_API int fire_tc_gemm(fire_ctx *ctx, int M, int N, int K, const uint16_t *A,
                           const uint16_t *B, int ksplit, uint32_t flags, float *C);
 
+/* Self-check of the device-side timeout path (no counterpart in the paper).
+ * One thread waits, with the bounded wait that every TMA and tensor-core
+ * pipeline of the library uses, on an mbarrier phase that nothing completes.
+ * The wait gives up after 2^31 SM clocks (about a second), sets the
+ * context's error word, and the call returns FIRE_ETIMEOUT, as fire_sync
+ * does after a real timeout, with the error word cleared and the context
+ * usable.  Blocks.  Any other return value means the path is broken (an
+ * error pending from earlier work is returned first, unchanged). */
+FIRE_API int fire_wait_selftest(fire_ctx *ctx);
+
 /* ---------------------------------------------------------------------------
  * Learned surrogate (no counterpart in the paper).  A BF16 convolutional
  * network maps one parameter vector, the landscape and the ignition to a

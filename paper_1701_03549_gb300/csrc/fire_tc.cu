@@ -50,6 +50,22 @@ cudaError_t gemm_launch(const uint16_t *A, const uint16_t *B, float *C, int M,
     return tc::launch_tc_tile<128>(p, ksplit, err, st);
 }
 
+// One thread waits, with the bounded wait that every TMA and tensor-core
+// pipeline of the library uses, for the first phase of an mbarrier that
+// nothing arrives at.  The wait gives up after 2^31 SM clocks and the error
+// word is set, as when a copy or an MMA never completes; `gave_up` records
+// that the wait ran out rather than completed.
+__global__ void k_wait_selftest(uint32_t *err, uint32_t *gave_up)
+{
+    __shared__ __align__(8) unsigned long long bar;
+    if (threadIdx.x != 0) return;
+    tc::mbar_init(&bar, 1);
+    if (!tc::mbar_wait_bounded(&bar, 0)) {
+        atomicOr(err, 1u);
+        *gave_up = 1u;
+    }
+}
+
 }  // namespace
 
 extern "C" int fire_tc_gemm(fire_ctx *ctx, int M, int N, int K,
@@ -78,4 +94,25 @@ extern "C" int fire_tc_gemm(fire_ctx *ctx, int M, int N, int K,
     CUDA_TRY(ctx, e, "tc gemm");
     if (flags & FIRE_SYNC) return fire_sync(ctx);
     return FIRE_OK;
+}
+
+extern "C" int fire_wait_selftest(fire_ctx *ctx)
+{
+    if (!ctx) return FIRE_EINVAL;
+    int rc = ensure_device(ctx);
+    if (rc) return rc;
+    // a clean error word first, so that only this wait can set it
+    rc = fire_sync(ctx);
+    if (rc) return rc;
+    uint32_t *gave_up = ctx->counter + 2;
+    CUDA_TRY(ctx, cudaMemsetAsync(gave_up, 0, 4, ctx->stream), "self-test flag");
+    k_wait_selftest<<<1, 32, 0, ctx->stream>>>(ctx->counter + 1, gave_up);
+    CUDA_TRY(ctx, cudaGetLastError(), "wait self-test");
+    uint32_t flag = 0;
+    CUDA_TRY(ctx, cudaMemcpyAsync(&flag, gave_up, 4, cudaMemcpyDeviceToHost,
+                                  ctx->stream), "self-test flag");
+    rc = fire_sync(ctx);   // FIRE_ETIMEOUT, clearing the error word
+    if (rc == FIRE_ETIMEOUT && flag != 1u)
+        return set_err(ctx, FIRE_ECUDA, "error word set without the wait");
+    return rc;
 }

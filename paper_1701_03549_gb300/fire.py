@@ -70,6 +70,7 @@ EXPORTED = (
     "fire_net_backward", "fire_net_adam", "fire_net_buffer",
     "fire_net_planes", "fire_net_inputs", "fire_net_labels",
     "fire_net_target_frac", "fire_net_screen", "fire_simulate_burnout",
+    "fire_wait_selftest",
 )
 
 
@@ -123,6 +124,7 @@ def load(path: str = LIB_PATH):
         "ignition_search": (i32, [vp, vp, vp, i32, i32, i32, u64, i32,
                                   C.c_double, u32, vp, vp, vp]),
         "fire_tc_gemm": (i32, [vp, i32, i32, i32, vp, vp, i32, u32, vp]),
+        "fire_wait_selftest": (i32, [vp]),
         "fire_simulate_burnout": (i32, [vp, vp, i32, vp, vp, vp, vp, u32,
                                         u32, vp, vp]),
         "fire_net_param_count": (C.c_int64, []),
@@ -694,6 +696,12 @@ def fire_tc_gemm(ctx: Context, A, B, M: int, N: int, K: int, out,
                                    int(ksplit), flags,
                                    _dev(ctx, out, "out", _F32, M * N)))
     return out
+
+
+def fire_wait_selftest(ctx: Context) -> int:
+    """Run the device-side timeout self-check; returns the library's code
+    (FIRE_ETIMEOUT when the timeout path works) instead of raising it."""
+    return int(ctx.lib.fire_wait_selftest(ctx.h))
 
 
 # ---------------------------------------------------------------------------

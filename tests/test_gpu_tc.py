@@ -1,6 +1,7 @@
 """Tensor-core tile (tcgen05, BF16 x BF16 -> FP32) against a float64 CPU
 matrix product of the same BF16 values: every majorness of A and B, ragged
-M and N, every tile width, and the split-K path."""
+M and N, every tile width, and the split-K path; and the bounded-wait timeout
+path the tile's pipelines rely on."""
 import numpy as np
 import pytest
 
@@ -62,3 +63,26 @@ def test_tc_gemm_rejects_bad_shapes(ctx):
     A2 = torch.zeros(64, 132, dtype=torch.bfloat16, device="cuda")
     with pytest.raises(fire.FireError):
         fire.fire_tc_gemm(ctx, A2, A2, 132, 128, 64, C, a_mn=True)  # M % 8
+
+
+def test_bounded_wait_runs_out_and_the_context_survives(ctx):
+    """The timeout path every TMA and tensor-core wait relies on: a wait on a
+    barrier phase nothing completes gives up after about a second, the call
+    reports FIRE_ETIMEOUT, and afterwards the error word is clear and the
+    tensor-core tile still computes correct products."""
+    import time
+
+    from paper_1701_03549_gb300 import fire
+    t0 = time.perf_counter()
+    rc = fire.fire_wait_selftest(ctx)
+    dt = time.perf_counter() - t0
+    assert rc == fire.FIRE_ETIMEOUT
+    assert 0.2 < dt < 30.0           # 2^31 SM clocks
+    assert ctx.sync() == fire.FIRE_OK
+    g = torch.Generator().manual_seed(5)
+    A = torch.randn(128, 64, generator=g).to(torch.bfloat16)
+    B = torch.randn(32, 64, generator=g).to(torch.bfloat16)
+    C = torch.full((128, 32), float("nan"), device="cuda")
+    fire.fire_tc_gemm(ctx, A.cuda(), B.cuda(), 128, 32, 64, C)
+    want = A.double() @ B.double().t()
+    assert torch.allclose(C.cpu().double(), want, rtol=0, atol=1e-4)
