@@ -86,6 +86,39 @@ def test_single_trial_probability_on_a_1x2_grid(oracle_mod):
     assert abs(cnt[0, 0] / n - p) <= 5 * math.sqrt(p * (1 - p) / n) + 1 / n
 
 
+def _z_with_threshold(oracle_mod, T):
+    """The least z whose threshold floor(p(z) 2^32) is >= T (bisection; the
+    threshold is non-decreasing in z)."""
+    lo, hi = -40.0, 40.0
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if oracle_mod.threshold_of_z(mid) >= T:
+            hi = mid
+        else:
+            lo = mid
+    return hi
+
+
+def test_a_draw_equal_to_its_threshold_fails(oracle_mod):
+    """A trial succeeds iff its draw is strictly below its threshold.  On a
+    1 x 2 flat grid (z = beta_0 exactly) beta_0 is set so that the only
+    trial's threshold equals its draw: the fire stays at the ignition; with
+    the threshold one above the draw it spreads.  (A statistical pin cannot
+    see this boundary: it decides one trial in 2^32.)"""
+    L = synth.uniform_landscape(1, 2)
+    F = oracle_mod.Features(L)
+    seed = 12345
+    # target (0, 1), burning source (0, 0) to its west: direction E, d = 2
+    u = oracle_mod.draw(seed, 1, 0, 2)
+    assert 1000 < u < 2 ** 32 - 1000
+    for T, burnt in ((u, 1), (u + 1, 2)):
+        z = _z_with_threshold(oracle_mod, T)
+        assert oracle_mod.threshold_of_z(z) == T
+        assert int(F.thresholds([z, 0, 0, 0, 0])[2, 0, 1]) == T
+        res, _ = F.simulate([z, 0, 0, 0, 0], (0, 0), seed)
+        assert res["burnt"] == burnt and res["trials"] == 1
+
+
 @pytest.mark.parametrize("shape,seed", [((1, 1), 0), ((1, 2), 1), ((2, 2), 2),
                                         ((2, 3), 3), ((3, 3), 4),
                                         ((3, 3), 5)])

@@ -1,0 +1,107 @@
+"""The oracle's pins catch plausible mistakes in it.
+
+Each case plants one mistake in a copy of ``oracle/fire_oracle.c`` (a dropped
+term of Eq. 1, a flipped sign, a reversed comparison, a swapped direction
+offset, an off-by-one, a wrong rounding), compiles the copy with the oracle's
+own flags, points the ``oracle`` module at it and runs the pins named for
+that mistake: at least one must fail.  The committed oracle is untouched; the
+same pins pass on it in the rest of the suite."""
+import os
+import subprocess
+
+import pytest
+
+from tests import test_oracle_ca as ca
+from tests import test_oracle_features as ft
+from tests import test_oracle_ga as ga
+
+_SRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(
+    __file__))), "oracle", "fire_oracle.c")
+
+# name: (original text, planted text, pins expected to catch it)
+MUTANTS = {
+    "aspect term dropped from Eq. 1": (
+        "    z = z + beta[2] * (double)m->psi[i];\n", "",
+        [ft.test_thresholds_aspect_term]),
+    "wind term with the wrong sign": (
+        "    case 0: return c;\n", "    case 0: return -c;\n",
+        [ft.test_relative_wind_equals_cosine_of_bearing_difference]),
+    "uphill test reversed": (
+        "if (elev[i] > elev[(long)sr * W + sc])",
+        "if (elev[i] < elev[(long)sr * W + sc])",
+        [ft.test_uphill_mask_on_an_eastward_ramp]),
+    "aspect measured from the wrong bearing": (
+        "aspect[i] - 315.0", "aspect[i] - 135.0",
+        [lambda o: ft.test_relative_aspect(o, 315.0, 1.0)]),
+    "slope term scaled by 1/10": (
+        "(double)slope[i] / 100.0", "(double)slope[i] / 10.0",
+        [ft.test_slope_term_is_slope_over_100]),
+    "forest indicator on the wrong code": (
+        "forest[i] = veg[i] == 1;", "forest[i] = veg[i] == 2;",
+        [ft.test_vegetation_indicator_and_burnable]),
+    "NE and NW offsets swapped": (
+        "static const int ORC_DC[8] = {0, 1, 1, 1, 0, -1, -1, -1};",
+        "static const int ORC_DC[8] = {0, -1, 1, 1, 0, -1, -1, 1};",
+        [ft.test_uphill_mask_on_an_eastward_ramp]),
+    "threshold rounded instead of floored": (
+        "return (uint64_t)floor(p * 4294967296.0);",
+        "return (uint64_t)floor(p * 4294967296.0 + 0.5);",
+        [ft.test_thresholds_baseline_only]),
+    "logistic of -z": (
+        "    double e = orc_exp(-z);\n    double p = 1.0 / (1.0 + e);\n"
+        "    return (uint64_t)floor",
+        "    double e = orc_exp(z);\n    double p = 1.0 / (1.0 + e);\n"
+        "    return (uint64_t)floor",
+        [ft.test_thresholds_baseline_only]),
+    "trial succeeds when the draw equals the threshold": (
+        "if ((uint64_t)u < T) ignite[i] = 1;",
+        "if ((uint64_t)u <= T) ignite[i] = 1;",
+        [ca.test_a_draw_equal_to_its_threshold_fails]),
+    "cells burn for two steps": (
+        "                left[i] = burn_time ? burn_time[i] : 1;\n"
+        "                any_burning = 1;",
+        "                left[i] = burn_time ? burn_time[i] : 2;\n"
+        "                any_burning = 1;",
+        [ca.test_p_one_chebyshev_distance_on_uniform_terrain]),
+    "intersection with the target not counted": (
+        "                if (target && target[i]) inter++;\n", "",
+        [ca.test_target_map_counts]),
+    "Eq. 2 numerator without the intersection": (
+        "    double sym = uni - (double)inter;", "    double sym = uni;",
+        [ca.test_fitness_golden_cases]),
+    "GA prefers the higher fitness": (
+        "if (!na && f[a] != f[b]) return f[a] < f[b];",
+        "if (!na && f[a] != f[b]) return f[a] > f[b];",
+        [ga.test_elites_are_the_two_best_with_nan_worst_and_ties_to_lower_index]),
+    "crossover cut off by one": (
+        "            ca[k] = k < cut ? pa[k] : pb[k];\n"
+        "            cb[k] = k < cut ? pb[k] : pa[k];",
+        "            ca[k] = k <= cut ? pa[k] : pb[k];\n"
+        "            cb[k] = k <= cut ? pb[k] : pa[k];",
+        [ga.test_crossover_children_are_prefix_suffix_swaps]),
+}
+
+
+@pytest.mark.parametrize("name", list(MUTANTS))
+def test_pins_catch_a_planted_mistake(name, tmp_path, monkeypatch):
+    import oracle
+
+    old, new, pins = MUTANTS[name]
+    src = open(_SRC).read()
+    assert src.count(old) == 1, "the planted text no longer matches the oracle"
+    c_path = tmp_path / "mutant.c"
+    so_path = str(tmp_path / "libmutant.so")
+    c_path.write_text(src.replace(old, new))
+    subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared",
+                    "-ffp-contract=off", "-fno-fast-math", "-o", so_path,
+                    str(c_path), "-lm"], check=True)
+    monkeypatch.setattr(oracle, "_LIB", so_path)
+    monkeypatch.setattr(oracle, "_lib", None)
+    monkeypatch.setattr(oracle, "build", lambda force=False: so_path)
+    caught = 0
+    for pin in pins:
+        try:
+            pin(oracle)
+        except AssertionError:
+            caught += 1
+    assert caught, f"no pin caught: {name}"
