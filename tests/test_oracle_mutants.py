@@ -6,6 +6,7 @@ offset, an off-by-one, a wrong rounding), compiles the copy with the oracle's
 own flags, points the ``oracle`` module at it and runs the pins named for
 that mistake: at least one must fail.  The committed oracle is untouched; the
 same pins pass on it in the rest of the suite."""
+import inspect
 import os
 import subprocess
 
@@ -14,6 +15,7 @@ import pytest
 from tests import test_oracle_ca as ca
 from tests import test_oracle_features as ft
 from tests import test_oracle_ga as ga
+from tests import test_oracle_rng_math as rm
 
 _SRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(
     __file__))), "oracle", "fire_oracle.c")
@@ -23,6 +25,16 @@ MUTANTS = {
     "aspect term dropped from Eq. 1": (
         "    z = z + beta[2] * (double)m->psi[i];\n", "",
         [ft.test_thresholds_aspect_term]),
+    "Philox4x32 multiplier mistyped": (
+        "{0xD2511F53u, 0xCD9E8D57u}", "{0xD2511F53u, 0xCD9E8D59u}",
+        [rm.test_philox4x32_equals_curand_on_the_host]),
+    "Philox4x32 Weyl increment mistyped": (
+        "{0x9E3779B9u, 0xBB67AE85u}", "{0x9E3779B9u, 0xBB67AE87u}",
+        [rm.test_philox4x32_equals_curand_on_the_host]),
+    "Philox4x32 with nine rounds": (
+        "philox4_generic(32, mul, weyl, 10, c, k, o);",
+        "philox4_generic(32, mul, weyl, 9, c, k, o);",
+        [rm.test_philox4x32_equals_curand_on_the_host]),
     "wind term with the wrong sign": (
         "    case 0: return c;\n", "    case 0: return -c;\n",
         [ft.test_relative_wind_equals_cosine_of_bearing_difference]),
@@ -100,8 +112,9 @@ def test_pins_catch_a_planted_mistake(name, tmp_path, monkeypatch):
     monkeypatch.setattr(oracle, "build", lambda force=False: so_path)
     caught = 0
     for pin in pins:
+        args = (oracle, tmp_path)[:len(inspect.signature(pin).parameters)]
         try:
-            pin(oracle)
+            pin(*args)
         except AssertionError:
             caught += 1
     assert caught, f"no pin caught: {name}"

@@ -1,10 +1,12 @@
 """Pins for the oracle's random numbers and elementary functions.
 
 Each check ties the oracle to something other than itself: numpy's Philox
-implementation, the platform libm, mpmath at high precision, closed forms
-and distributional properties.
+implementation, cuRAND's Philox4x32-10 block function compiled for the host,
+the platform libm, mpmath at high precision, closed forms and distributional
+properties.
 """
 import math
+import os
 
 import numpy as np
 import pytest
@@ -28,6 +30,52 @@ def test_philox_round_structure_matches_numpy_4x64(oracle_mod):
         c1[0] += np.uint64(1)
         got = oracle_mod.philox4x64_10(c1, key)
         assert np.array_equal(got, want)
+
+
+_CURAND_HDR = "/usr/local/cuda/include/curand_philox4x32_x.h"
+
+
+def _curand_host_blocks(tmp_path):
+    """cuRAND's public Philox4x32-10 block function compiled for the host
+    (tests/curand_philox_host.cpp): a third-party known answer, no GPU."""
+    import ctypes
+    import subprocess
+
+    if not os.path.exists(_CURAND_HDR):
+        pytest.skip("CUDA headers not installed")
+    src = os.path.join(os.path.dirname(os.path.abspath(__file__)),
+                       "curand_philox_host.cpp")
+    so = str(tmp_path / "libcurand_philox_host.so")
+    subprocess.run(["g++", "-O2", "-std=c++17", "-shared", "-fPIC",
+                    "-I" + os.path.dirname(_CURAND_HDR), src, "-o", so],
+                   check=True)
+    lib = ctypes.CDLL(so)
+
+    def blocks(ctr, key):
+        ctr = np.ascontiguousarray(ctr, np.uint32)
+        key = np.ascontiguousarray(key, np.uint32)
+        out = np.zeros((len(ctr), 4), np.uint32)
+        lib.curand_philox_blocks_host(len(ctr), ctr.ctypes.data,
+                                      key.ctypes.data, out.ctypes.data)
+        return out
+    return blocks
+
+
+def test_philox4x32_equals_curand_on_the_host(oracle_mod, tmp_path):
+    """Blocks equal those of cuRAND's raw block function (built for the CPU
+    from its public header) on 4096 random counters and keys and on the
+    all-zero and all-one corners: multipliers, Weyl increments and the
+    round count are pinned without a GPU."""
+    ref = _curand_host_blocks(tmp_path)
+    rng = np.random.default_rng(17)
+    ctr = rng.integers(0, 2 ** 32, (4096, 4), dtype=np.uint32)
+    key = rng.integers(0, 2 ** 32, (4096, 2), dtype=np.uint32)
+    ones = np.uint32(0xFFFFFFFF)
+    ctr[:4] = [[0, 0, 0, 0], [ones] * 4, [0, 0, 0, 0], [ones] * 4]
+    key[:4] = [[0, 0], [0, 0], [ones, ones], [ones, ones]]
+    want = ref(ctr, key)
+    got = np.array([oracle_mod.philox4x32_10(c, k) for c, k in zip(ctr, key)])
+    assert np.array_equal(got, want)
 
 
 def test_philox4x32_outputs_are_uniform(oracle_mod):
