@@ -4,11 +4,15 @@ Each case plants one mistake in a copy of ``oracle/fire_oracle.c`` (a dropped
 term of Eq. 1, a flipped sign, a reversed comparison, a swapped direction
 offset, an off-by-one, a wrong rounding), compiles the copy with the oracle's
 own flags, points the ``oracle`` module at it and runs the pins named for
-that mistake: at least one must fail.  The committed oracle is untouched; the
-same pins pass on it in the rest of the suite."""
+that mistake: at least one must fail.  The surrogate's oracle
+(``oracle/surrogate.py``) gets the same treatment: a mistake is planted in a
+copy of its source, the copy is loaded as a module in its place, and the
+named pins must fail.  The committed oracle is untouched; the same pins pass
+on it in the rest of the suite."""
 import inspect
 import os
 import subprocess
+import types
 
 import pytest
 
@@ -16,6 +20,7 @@ from tests import test_oracle_ca as ca
 from tests import test_oracle_features as ft
 from tests import test_oracle_ga as ga
 from tests import test_oracle_rng_math as rm
+from tests import test_oracle_surrogate as so
 
 _SRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(
     __file__))), "oracle", "fire_oracle.c")
@@ -115,6 +120,72 @@ def test_pins_catch_a_planted_mistake(name, tmp_path, monkeypatch):
         args = (oracle, tmp_path)[:len(inspect.signature(pin).parameters)]
         try:
             pin(*args)
+        except AssertionError:
+            caught += 1
+    assert caught, f"no pin caught: {name}"
+
+
+_SURR = os.path.join(os.path.dirname(_SRC), "surrogate.py")
+
+# name: (original text, planted text, pins expected to catch it)
+SURROGATE_MUTANTS = {
+    "convolution taps transposed": (
+        "return [((t // 3 - 1) * d, (t % 3 - 1) * d) for t in range(9)]",
+        "return [((t % 3 - 1) * d, (t // 3 - 1) * d) for t in range(9)]",
+        [lambda o: so.test_conv_matches_correlate2d(2)]),
+    "input gradient shifted the wrong way": (
+        "        da += _shift(dz @ Wt[:, t, :], -dy, -dx)",
+        "        da += _shift(dz @ Wt[:, t, :], dy, dx)",
+        [lambda o: so.test_conv_input_and_weight_gradients(2)]),
+    "weight gradient with transposed tap offsets": (
+        "        dW[:, t, :] = dzf.T @ _shift(a, dy, dx).reshape(-1, ci)",
+        "        dW[:, t, :] = dzf.T @ _shift(a, dx, dy).reshape(-1, ci)",
+        [lambda o: so.test_conv_input_and_weight_gradients(2)]),
+    "ReLU mask of the wrong layer": (
+        "            dz = rnd(da * (hs[l - 1] > 0))",
+        "            dz = rnd(da * (hs[l] > 0))",
+        [lambda o: so.test_backward_matches_finite_differences()]),
+    "bias gradient halved": (
+        '        grads[f"b{l}"] = dz.sum(axis=(0, 1, 2))',
+        '        grads[f"b{l}"] = 0.5 * dz.sum(axis=(0, 1, 2))',
+        [lambda o: so.test_backward_matches_finite_differences()]),
+    "loss gradient not divided by the pixel count": (
+        "    g = (sigmoid(logits) - t) / logits.size",
+        "    g = (sigmoid(logits) - t)",
+        [lambda o: so.test_backward_matches_finite_differences()]),
+    "BCE with the wrong sign of t z": (
+        "    return float(np.mean(np.maximum(z, 0.0) - t * z +",
+        "    return float(np.mean(np.maximum(z, 0.0) + t * z +",
+        [lambda o: so.test_bce_closed_forms()]),
+    "sigmoid of 2z": (
+        "    return 0.5 * (1.0 + np.tanh(0.5 * z))",
+        "    return 0.5 * (1.0 + np.tanh(z))",
+        [lambda o: so.test_backward_matches_finite_differences()]),
+    "Adam without bias correction": (
+        "    mh = m / (1.0 - ADAM_B1 ** step)", "    mh = m",
+        [lambda o: so.test_adam_bias_corrected_steps()]),
+    "expected Jaccard distance over the wrong union": (
+        "    den = tgt if kind == 0 else sim + tgt - inter",
+        "    den = tgt if kind == 0 else sim + tgt",
+        [so.test_predicted_fitness_on_hard_maps_is_eq2]),
+}
+
+
+@pytest.mark.parametrize("name", list(SURROGATE_MUTANTS))
+def test_surrogate_pins_catch_a_planted_mistake(name, monkeypatch):
+    import oracle
+
+    old, new, pins = SURROGATE_MUTANTS[name]
+    src = open(_SURR).read()
+    assert src.count(old) == 1, "the planted text no longer matches the oracle"
+    mod = types.ModuleType("oracle.surrogate")
+    mod.__file__ = _SURR
+    exec(compile(src.replace(old, new), _SURR, "exec"), mod.__dict__)
+    monkeypatch.setattr(so, "sg", mod)
+    caught = 0
+    for pin in pins:
+        try:
+            pin(oracle)
         except AssertionError:
             caught += 1
     assert caught, f"no pin caught: {name}"
