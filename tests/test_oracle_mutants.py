@@ -16,9 +16,11 @@ import types
 
 import pytest
 
+from tests import test_oracle_burnout as bo
 from tests import test_oracle_ca as ca
 from tests import test_oracle_features as ft
 from tests import test_oracle_ga as ga
+from tests import test_oracle_ignition as ig
 from tests import test_oracle_rng_math as rm
 from tests import test_oracle_surrogate as so
 
@@ -40,6 +42,33 @@ MUTANTS = {
         "philox4_generic(32, mul, weyl, 10, c, k, o);",
         "philox4_generic(32, mul, weyl, 9, c, k, o);",
         [rm.test_philox4x32_equals_curand_on_the_host]),
+    "Philox key bumped before the first round": (
+        "        if (r > 0) {\n            k0 = (k0 + weyl[0]) & mask;",
+        "        if (r >= 0) {\n            k0 = (k0 + weyl[0]) & mask;",
+        [rm.test_philox_round_structure_matches_numpy_4x64]),
+    "cosine series missing its 4! term": (
+        "    c = c * s2 + 1.0 / 24.0;                       /* +1/4!  */\n", "",
+        [rm.test_degree_trig_against_libm_and_exact_points]),
+    "angle reduced with floor instead of nearest": (
+        "double k = rint(deg / 90.0);", "double k = floor(deg / 90.0);",
+        [rm.test_degree_trig_against_libm_and_exact_points]),
+    "cell-uniform rule multiplies p instead of 1 - p": (
+        "        q = q * (1.0 - p);", "        q = q * p;",
+        [ca.test_cell_uniform_p_zero_and_p_one]),
+    "replicate mean over one too many": (
+        "        out[i] = s / (double)per_group;",
+        "        out[i] = s / (double)(per_group + 1);",
+        [ga.test_group_mean_against_exact_sum]),
+    "ensemble y mean taken from x": (
+        "const double mx = sx / (double)k, my = sy / (double)k;",
+        "const double mx = sx / (double)k, my = sx / (double)k;",
+        [ig.test_ensemble_statistics]),
+    "burn-out time one step too long": (
+        "                left[i] = burn_time ? burn_time[i] : 1;\n"
+        "                any_burning = 1;",
+        "                left[i] = burn_time ? burn_time[i] + 1 : 1;\n"
+        "                any_burning = 1;",
+        [bo.test_p_zero_and_p_one]),
     "wind term with the wrong sign": (
         "    case 0: return c;\n", "    case 0: return -c;\n",
         [ft.test_relative_wind_equals_cosine_of_bearing_difference]),
