@@ -69,6 +69,21 @@ MUTANTS = {
         "                left[i] = burn_time ? burn_time[i] + 1 : 1;\n"
         "                any_burning = 1;",
         [bo.test_p_zero_and_p_one]),
+    "exp series missing its 1/3! term": (
+        "    s = s * r + 1.0 / 6.0;\n", "",
+        [rm.test_spec_exp_within_two_ulp_of_libm]),
+    "exp reduction without the ln 2 tail": (
+        "double r = (x - k * ORC_LN2_HEAD) - k * ORC_LN2_TAIL;",
+        "double r = x - k * ORC_LN2_HEAD;",
+        [rm.test_spec_exp_within_two_ulp_of_libm]),
+    "nearest-cell ties go to the higher index": (
+        "if (best < 0 || d < bestd) { best = i; bestd = d; }",
+        "if (best < 0 || d <= bestd) { best = i; bestd = d; }",
+        [ig.test_lattice_point_in_a_hole_snaps_to_the_nearest_burnt_cell]),
+    "lattice rows not centred in their strips": (
+        "const long long R = r0 + ((2LL * a + 1) * (r1 - r0 + 1)) / (2LL * LH);",
+        "const long long R = r0 + ((2LL * a) * (r1 - r0 + 1)) / (2LL * LH);",
+        [ig.test_lattice_on_a_rectangular_scar]),
     "wind term with the wrong sign": (
         "    case 0: return c;\n", "    case 0: return -c;\n",
         [ft.test_relative_wind_equals_cosine_of_bearing_difference]),
