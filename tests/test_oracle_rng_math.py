@@ -32,7 +32,8 @@ def test_philox_round_structure_matches_numpy_4x64(oracle_mod):
         assert np.array_equal(got, want)
 
 
-_CURAND_HDR = "/usr/local/cuda/include/curand_philox4x32_x.h"
+_CURAND_HDR = os.path.join(os.environ.get("CUDA_HOME", "/usr/local/cuda"),
+                           "include", "curand_philox4x32_x.h")
 
 
 def _curand_host_blocks(tmp_path):
