@@ -1,15 +1,23 @@
 """Throughput of batched fire-spread simulations on GB300.
 
-One step = one GA generation of the 512 x 512 calibration workload: 256
-parameter vectors drawn from the Gauss(0, 5) initial distribution (Table 1)
-x 16 replicate seeds = 4096 independent simulations from the fixed centre
-ignition, each run to extinction and scored against the reference burnt map
-(Eq. 2 counts fused in the simulation kernel, fitness ratios by a second
-kernel).  Inputs are resident on the device before timing; every step uses
-fresh seeds; L2 is flushed (256 MB write) between timed steps.
+Default step (the largest single-GPU configuration): the uneven batch of
+nine synthetic fires on grids from 200 x 300 to 2000 x 1500 cells (10.9 M
+cells in total), 100,000 simulations with parameters drawn from the
+Uniform[-30, 30] initial distribution of Table 1, all in one persistent
+launch replayed as a CUDA graph, each run to extinction and scored against
+its fire's reference burnt map (Eq. 2 counts fused in the simulation
+kernel, fitness ratios by a second kernel).  Inputs are resident on the
+device before timing; every step uses fresh seeds; L2 is flushed (256 MB
+write) before every timed step.
 
-Prints one JSON line (see the keys below).  ``--impl reference`` times the
-CPU oracle on the same workload instead.
+``--workload ga512``: one GA generation of the 512 x 512 calibration
+workload (256 Gauss(0, 5) parameter vectors x 16 replicates).
+``--workload recover``: parameter recovery of the plain GA (populations 256
+and 1024) and the surrogate-screened GA against the reference parameters.
+``--impl reference``: the CPU oracle on the same workload and sample as the
+``cpu_baseline`` leg of the default line.
+
+Prints one JSON line.
 """
 from __future__ import annotations
 
@@ -35,16 +43,25 @@ METRIC = "CA sims/s"
 UNIT = "sims/s"
 POP, REPS = 256, 16
 SIMS = POP * REPS
-# Algorithmic operations of one trial: one Philox4x32-10 output word (10
-# rounds of 8 integer operations per 4-word block: 20) plus Eq. 1 for one
-# direction and its comparison with the draw (the five-term sum as 4 FMAs,
-# exponential 2, 1 + e 1, reciprocal 1, draw to float 2, compare 1: 11).
-OPS_PER_TRIAL = 31
+# Algorithmic operations of one trial (one decision of a burning neighbour
+# against its target): a quarter of a Philox4x32-10 block, about 25 integer
+# operations per 32-bit word (10 rounds of two 32x32->64 multiplies, the
+# xors and the key schedule, over four words), plus about 15 single-precision
+# operations for Eq. 1 in one direction, the logistic and the comparison
+# with the draw.
+OPS_PER_TRIAL = 40
 ALU_LANES_PER_SM = 128
-WORKLOAD = ("ga_generation_512: 512x512 map, 256 Gauss(0,5) parameter "
-            "vectors x 16 replicates = 4096 simulations/step, centre "
-            "ignition, constant 45 deg wind, target from the reference "
-            "parameters")
+UNEVEN = ("uneven_fires: nine fires on 200x300 ... 2000x1500 grids (10.9 M "
+          "cells), 100,000 simulations in one persistent launch (11,112 on "
+          "the first fire, 11,111 on each other), Uniform[-30,30] parameters, "
+          "centre ignitions, targets from the reference parameters")
+GA512 = ("ga_generation_512: 512x512 map, 256 Gauss(0,5) parameter "
+         "vectors x 16 replicates = 4096 simulations/step, centre "
+         "ignition, constant 45 deg wind, target from the reference "
+         "parameters")
+L2_NOTE = "flushed before every timed step (256 MB write)"
+# Stratified oracle samples (the same in cpu_baseline and --impl reference)
+UNEVEN_PER_FIRE = 16
 
 
 def _peaks():
@@ -178,82 +195,194 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
+# ---------------------------------------------------------------------------
+# The CPU oracle legs: cpu_baseline of the native line and --impl reference.
+# Both time the same stratified sample of the workload with the oracle as it
+# stands (single-threaded, one simulation per task) on every host core, with
+# the targets simulated by the oracle itself, and extrapolate per fire.
+
 _WORKER = {}
 
 
-def _oracle_init(land_args, target):
-    """Spawned worker: build the oracle's covariates and target once."""
+def _lands(kind):
+    if kind == "uneven":
+        return workloads.uneven_lands()
+    return [synth.preset_landscape("ga_generation_512")]
+
+
+def _oracle_init(kind, packed, barrier):
+    """Spawned worker: the oracle's covariates of every map of the workload
+    and, for timing jobs, the targets (bit-packed)."""
     import oracle
 
-    _WORKER["F"] = oracle.Features(synth.landscape(*land_args))
-    _WORKER["target"] = target
+    lands = _lands(kind)
+    _WORKER["F"] = [oracle.Features(L) for L in lands]
+    _WORKER["ign"] = [synth.centre_ignition(L.veg) for L in lands]
+    _WORKER["burnable"] = [int((L.veg != 0).sum()) for L in lands]
+    _WORKER["T"] = (None if packed is None else
+                    [np.unpackbits(p, count=L.veg.size).reshape(L.veg.shape)
+                     .astype(bool) for p, L in zip(packed, lands)])
+    _WORKER["barrier"] = barrier
+
+
+def _oracle_ready(_):
+    """Returns once every worker of the pool has been initialised."""
+    _WORKER["barrier"].wait(timeout=600)
+    return 0
+
+
+def _oracle_target_job(j):
+    """The reference fire of map j (reference parameters, the first target
+    seed whose fire burns enough), simulated by the oracle."""
+    F, ign = _WORKER["F"][j], _WORKER["ign"][j]
+    seed, burnt = workloads.pick_target(
+        lambda s: F.simulate(synth.TRUTH_BETA, ign, s)[1] >= 0,
+        _WORKER["burnable"][j])
+    return seed, np.packbits(burnt.ravel())
 
 
 def _oracle_job(args):
-    """One oracle simulation in a worker process; returns its step count."""
-    beta, ign, seed = args
-    res, _ = _WORKER["F"].simulate(beta, ign, int(seed),
-                                   target=_WORKER["target"], want_steps=False)
-    return res["steps"]
+    """One oracle simulation: (map index, single-core seconds, steps)."""
+    j, beta, ign, seed = args
+    t0 = time.perf_counter()
+    res, _ = _WORKER["F"][j].simulate(beta, ign, int(seed),
+                                      target=_WORKER["T"][j], want_steps=False)
+    return j, time.perf_counter() - t0, res["steps"]
 
 
-def oracle_throughput(wl, target, nsims: int, cores: int):
-    """Oracle simulations/s on the first nsims simulations of the workload,
-    one simulation per task, `cores` single-threaded worker processes."""
-    import multiprocessing as mp
+class OracleLeg:
+    """A spawn pool of single-threaded oracle workers, one per host core,
+    holding every map of the workload and the targets the oracle simulated
+    for them."""
 
-    p = synth.PRESETS["ga_generation_512"]
-    land_args = (p["H"], p["W"], p["map_seed"], p["wind_seed"])
-    jobs = [(wl.params[i], wl.ignition, int(wl.seeds[i]))
-            for i in range(nsims)]
-    ctx = mp.get_context("spawn")
-    with ctx.Pool(cores, initializer=_oracle_init,
-                  initargs=(land_args, target)) as pool:
-        pool.map(_oracle_job, [(np.full(5, -1000.0), wl.ignition, 1)] * cores,
-                 chunksize=1)  # wait until every worker is initialised
+    def __init__(self, kind: str, cores: int):
+        import multiprocessing as mp
+
+        self.kind, self.cores = kind, cores
+        nmaps = len(_lands(kind))
+        mpc = mp.get_context("spawn")
+        with mpc.Pool(min(cores, nmaps), initializer=_oracle_init,
+                      initargs=(kind, None, None)) as pool:
+            got = pool.map(_oracle_target_job, range(nmaps), chunksize=1)
+        self.target_seeds = [int(g[0]) for g in got]
+        barrier = mpc.Barrier(cores)
+        self.pool = mpc.Pool(cores, initializer=_oracle_init,
+                             initargs=(kind, [g[1] for g in got], barrier))
+        self.pool.map(_oracle_ready, range(cores), chunksize=1)
+
+    def run(self, jobs):
         t0 = time.perf_counter()
-        steps = pool.map(_oracle_job, jobs, chunksize=1)
-        dt = time.perf_counter() - t0
-    return nsims / dt, dt, sum(steps)
+        out = self.pool.map(_oracle_job, jobs, chunksize=1)
+        return out, time.perf_counter() - t0
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
 
 
-def oracle_target(wl):
-    import oracle
+def _oracle_workload(kind):
+    """(workload, sample indices, simulations per map in one step, sample
+    description) of the oracle legs: seeds of the first generation/step."""
+    if kind == "uneven":
+        wl = workloads.uneven_fires()
+        idx = workloads.stratified_sample(wl.map_of_sim, UNEVEN_PER_FIRE)
+        counts = np.bincount(wl.map_of_sim, minlength=len(wl.lands))
+        desc = (f"{UNEVEN_PER_FIRE} simulations per fire ({idx.size}), evenly "
+                "spaced over each fire's block of the 100,000-simulation "
+                "batch, seeds of the first step; extrapolated per fire: "
+                "batch time = sum over fires of (simulations of the fire x "
+                "mean single-core seconds of its sampled simulations) / cores")
+        mos = wl.map_of_sim
+    else:
+        wl = workloads.ga_generation_512(POP, REPS)
+        idx = np.arange(0, SIMS, REPS, dtype=np.int64)
+        counts = np.array([SIMS])
+        desc = ("replicate 0 of each of the 256 parameter vectors of the "
+                "first generation (256 simulations); extrapolated: "
+                "generation time = 4096 x mean single-core seconds / cores")
+        mos = np.zeros(wl.n, np.int32)
+    jobs = [(int(mos[i]), wl.params[i], tuple(int(v) for v in wl.ignitions[i]),
+             int(wl.seeds[i])) for i in idx]
+    return wl, jobs, counts, desc
 
-    F = oracle.Features(wl.land)
-    return workloads.pick_target(
-        lambda s: F.simulate(synth.TRUTH_BETA, wl.ignition, s)[1] >= 0,
-        int(F.burnable.sum()))
+
+def _extrapolate(results, counts, cores):
+    """Seconds of one whole step on `cores` workers: per map, the mean
+    single-core seconds of its sampled simulations times its simulations in
+    the step, summed, over the cores (perfectly balanced work)."""
+    by = {}
+    for j, sec, _ in results:
+        by.setdefault(j, []).append(sec)
+    return sum(counts[j] * float(np.mean(v)) for j, v in by.items()) / cores
+
+
+def cpu_baseline(kind, cores):
+    """The native line's cpu_baseline: the stratified sample once."""
+    leg = OracleLeg(kind, cores)
+    try:
+        wl, jobs, counts, desc = _oracle_workload(kind)
+        res, wall = leg.run(jobs)
+    finally:
+        leg.close()
+    est = _extrapolate(res, counts, cores)
+    return {"value": int(counts.sum()) / est, "unit": UNIT, "cores": cores,
+            "kind": "oracle", "sample": desc,
+            "sample_wall_s": round(wall, 2),
+            "target_seeds": leg.target_seeds}
+
+
+def _config(kind, world):
+    """The workload as both arms name it (no launch details: those are the
+    native arm's own, under "launch")."""
+    if kind == "uneven":
+        cells = int(sum(H * W for H, W in synth.uneven_fire_shapes()))
+        return {"workload": UNEVEN, "sims_per_step": 100_000,
+                "cells_total": cells, "graph": True, "l2": L2_NOTE,
+                "parallelism": f"replicas x{world}"}
+    return {"workload": GA512, "H": 512, "W": 512, "sims_per_step": SIMS,
+            "l2": L2_NOTE, "order": "longest-first by predicted spread "
+            "(FIRE_LONGEST_FIRST)", "parallelism": f"replicas x{world}"}
 
 
 def run_reference(args):
+    """The oracle arm: W untimed warm-up rounds, then K timed steps that
+    cycle through the stratified sample (every sampled simulation at least
+    once when K divides it; the value extrapolates from all of them)."""
     rank, world, _ = parallel.env_rank()
     if rank != 0:
         return 0
+    kind = "ga512" if args.workload == "ga512" else "uneven"
     cores = os.cpu_count() or 1
-    wl = workloads.ga_generation_512(POP, REPS)
-    _, target = oracle_target(wl)
-    per_step = min(SIMS, 4 * cores)
-    times = []
-    for k in range(args.warmup + args.steps):
-        sub = workloads.ga_generation_512(POP, REPS,
-                                          first_seed=1 + k * SIMS)
-        v, dt, _ = oracle_throughput(sub, target, per_step, cores)
-        if k >= args.warmup:
-            times.append(dt)
-    total = sum(times)
-    value = per_step * args.steps / total
+    leg = OracleLeg(kind, cores)
+    try:
+        wl, jobs, counts, desc = _oracle_workload(kind)
+        trivial = (0, np.full(5, -1000.0), jobs[0][2], 1)
+        for _ in range(args.warmup):
+            leg.run([trivial] * cores)
+        per = -(-len(jobs) // args.steps)
+        timed, walls = [], []
+        for k in range(args.steps):
+            step = [jobs[(k * per + i) % len(jobs)] for i in range(per)]
+            res, wall = leg.run(step)
+            timed += res
+            walls.append(wall)
+    finally:
+        leg.close()
+    est = _extrapolate(timed, counts, cores)
+    value = int(counts.sum()) / est
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+        "ms_per_step": 1e3 * est, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u32",
-        "data": "synthetic", "config": {"workload": WORKLOAD, "H": 512,
-                                        "W": 512, "sims_per_step": per_step},
+        "data": "synthetic", "config": _config(kind, world),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores,
                          "kind": "oracle",
-                         "sample": f"first {per_step} simulations of each "
-                                   "4096-simulation generation"},
+                         "sample": desc + f"; the {len(jobs)} sampled "
+                                   f"simulations cycled over the {args.steps}"
+                                   f" timed steps ({per} per step)",
+                         "sample_wall_s": round(sum(walls), 2),
+                         "target_seeds": leg.target_seeds},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -261,7 +390,10 @@ def run_reference(args):
     return 0
 
 
-def run_native(args):
+# ---------------------------------------------------------------------------
+# Native arm, shared pieces
+
+def _setup_gpu():
     import torch
 
     rank, world, local = parallel.env_rank()
@@ -270,11 +402,9 @@ def run_native(args):
 
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     if not torch.cuda.is_available():
-        print(json.dumps({"metric": METRIC, "error": "no CUDA device"}))
-        return 1
+        return None
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-
     import __graft_entry__
 
     __graft_entry__.build()
@@ -283,34 +413,233 @@ def run_native(args):
     stream = torch.cuda.Stream(dev)
     torch.cuda.set_stream(stream)
     ctx = fire.Context(local, stream)
-    first = parallel.rank_seed_offset(rank, SIMS * (args.warmup + args.steps + 2))
-    wl = workloads.ga_generation_512(POP, REPS, first_seed=first)
-    m = ctx.landscape_upload(wl.land)
-    H, W = wl.shape
-    # target: reference parameters, first seed from TARGET_SEED with a
-    # non-trivial fire (simulated on this GPU)
-    burnable = int((wl.land.veg != 0).sum())
+    return torch, fire, ctx, dev, stream, rank, world, local
 
-    def sim_target(seed):
+
+def _gpu_target(fire, m, ign, burnable):
+    """The map's reference fire simulated on this GPU (the first target seed
+    whose fire burns enough)."""
+    def sim(seed):
         _, bs = m.simulate_batch(np.asarray([synth.TRUTH_BETA]),
-                                 np.asarray([wl.ignition], np.int32),
+                                 np.asarray([ign], np.int32),
                                  np.asarray([seed], np.uint64),
                                  want_steps=True)
         return bs[0] >= 0
 
-    tseed, target = workloads.pick_target(sim_target, burnable)
+    return workloads.pick_target(sim, burnable)
+
+
+def _alu_roof(torch, dev, trials_per_launch, launch_s):
+    peaks, kind = _peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    props = torch.cuda.get_device_properties(dev)
+    peak = props.multi_processor_count * ALU_LANES_PER_SM * sm_max * 1e6
+    achieved = trials_per_launch * OPS_PER_TRIAL / launch_s
+    return peaks, kind, {
+        "bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,
+        "unit": "Tops/s", "frac": achieved / peak, "kernel": "k_simulate",
+        "peak_source": f"{props.multi_processor_count} SMs x "
+                       f"{ALU_LANES_PER_SM} lanes x {sm_max:.0f} MHz "
+                       f"({kind} max SM clock)",
+        "ops_per_trial": OPS_PER_TRIAL, "trials_per_launch": trials_per_launch,
+        "kernel_ms": 1e3 * launch_s}
+
+
+def _pinned(torch, a):
+    return torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+
+
+# ---------------------------------------------------------------------------
+# Native arm, default step: the nine-fire uneven batch
+
+def run_uneven(args):
+    """One fire_simulate_multi call per step (CUDA-graph replay of the
+    ordering kernels and the persistent simulation launch) plus the fitness
+    kernel, all on device-resident inputs."""
+    g = _setup_gpu()
+    if g is None:
+        print(json.dumps({"metric": METRIC, "error": "no CUDA device"}))
+        return 1
+    torch, fire, ctx, dev, stream, rank, world, local = g
+    nsteps = args.warmup + args.steps
+    n = 100_000
+    wl = workloads.uneven_fires(n, first_seed=1 + rank * n * (nsteps + 1))
+    maps = [ctx.landscape_upload(L) for L in wl.lands]
+    tseeds = []
+    for j, (m, L) in enumerate(zip(maps, wl.lands)):
+        ign = tuple(int(v) for v in wl.ignitions[np.argmax(wl.map_of_sim == j)])
+        ts, tg = _gpu_target(fire, m, ign, int((L.veg != 0).sum()))
+        m.target_upload(tg)
+        tseeds.append(int(ts))
+    # launch shape: the autotuner times its candidates on a stratified tenth
+    # of the batch (outside the timed region) and the library keeps the best
+    sub = np.arange(0, n, 10)
+    tuned = fire.fire_autotune(ctx, maps, wl.map_of_sim[sub], wl.params[sub],
+                               wl.ignitions[sub], wl.seeds[sub])
+    t_mi = torch.tensor(wl.map_of_sim, device=dev)
+    t_p = torch.tensor(wl.params, dtype=torch.float64, device=dev)
+    t_g = torch.tensor(wl.ignitions, device=dev)
+    t_s = torch.empty(n, dtype=torch.int64, device=dev)
+    seeds_host = [wl.seeds + np.uint64(k * n) for k in range(nsteps)]
+    seeds_all = [torch.tensor(s.view(np.int64), device=dev) for s in seeds_host]
+    out = torch.zeros((n, 6), dtype=torch.int32, device=dev)
+    fit = torch.zeros(n, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    torch.cuda.synchronize()
+
+    def step(k):
+        t_s.copy_(seeds_all[k])
+        fire.fire_simulate_multi(ctx, maps, t_mi, t_p, t_g, t_s, device=True,
+                                 out=out, graph=True)
+        fire.fire_fitness(ctx, out, fire.FITNESS_JACCARD, device=True, out=fit)
+
+    for k in range(args.warmup):
+        flush.zero_()
+        step(k)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    sim_ms, step_ms = [], []
+    steps_sum = trials_sum = cells = 0
+    sizes = np.array([L.veg.size for L in wl.lands], np.int64)[wl.map_of_sim]
+    for j in range(args.steps):
+        k = args.warmup + j
+        flush.zero_()
+        t_s.copy_(seeds_all[k])
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        fire.fire_simulate_multi(ctx, maps, t_mi, t_p, t_g, t_s, device=True,
+                                 out=out, graph=True)
+        e1.record(stream)
+        fire.fire_fitness(ctx, out, fire.FITNESS_JACCARD, device=True, out=fit)
+        e2.record(stream)
+        torch.cuda.synchronize()
+        sim_ms.append(e0.elapsed_time(e1))
+        step_ms.append(e0.elapsed_time(e2))
+        r = fire.results_view(out)
+        assert int((r["status"] & (fire.STATUS_BAD_IGNITION |
+                                   fire.STATUS_TIMEOUT)).max()) == 0
+        st = r["steps"].astype(np.int64)
+        steps_sum += int(st.sum())
+        cells += int((st * sizes).sum())
+        trials_sum += int(r["trials"].astype(np.int64).sum())
+    ck = clocks.stop()
+    total_s = parallel.max_over_ranks(sum(step_ms) / 1e3, world, dev)
+    value = n * args.steps * world / total_s
+    cells_all = parallel.sum_over_ranks(cells, world, dev)
+    trials_all = parallel.sum_over_ranks(trials_sum, world, dev)
+
+    # end to end through the C ABI with host buffers (pinned): the same seeds
+    # and the same L2 flush as the device-timed steps; each call copies the
+    # step's inputs in and its results out, the fitness call copies the
+    # results in and the fitness out
+    pin_mi = _pinned(torch, wl.map_of_sim)
+    pin_p = _pinned(torch, wl.params)
+    pin_g = _pinned(torch, wl.ignitions)
+    pin_s = [_pinned(torch, s) for s in seeds_host]
+    fire.fire_simulate_multi(ctx, maps, pin_mi, pin_p, pin_g, pin_s[0])
+    e2e_steps = min(args.steps, 5)
+    e2e_s = 0.0
+    for j in range(e2e_steps):
+        k = args.warmup + j
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = fire.fire_simulate_multi(ctx, maps, pin_mi, pin_p, pin_g, pin_s[k])
+        f = fire.fire_fitness(ctx, res, fire.FITNESS_JACCARD)
+        e2e_s += time.perf_counter() - t0
+        assert f.shape == (n,)
+    e2e_s = parallel.max_over_ranks(e2e_s, world, dev)
+    e2e_value = n * e2e_steps * world / e2e_s
+    dev_same = parallel.max_over_ranks(sum(step_ms[:e2e_steps]) / 1e3, world,
+                                       dev)
+    h2d = n * (40 + 8 + 8 + 4) + n * 24
+    d2h = n * 24 + n * 8
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline("uneven", os.cpu_count() or 1)
+        cpu["targets_match_gpu"] = cpu["target_seeds"] == tseeds
+
+    if rank == 0:
+        launch_s = sum(sim_ms) / len(sim_ms) / 1e3
+        peaks, pk, roof = _alu_roof(torch, dev, trials_sum / args.steps,
+                                    launch_s)
+        uprof = _committed_profile("k_simulate_uneven_traffic.json")
+        roof["traffic"] = None if uprof is None else uprof["dram_bytes_per_launch"]
+        roof["timed"] = ("the graph (three ordering kernels, counter reset, "
+                         "k_simulate), CUDA events on the launching stream")
+        roof["memory"] = _memory_roofs(launch_s, peaks, pk,
+                                       "k_simulate_uneven_traffic.json")
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": total_s * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u32", "data": "synthetic",
+            "config": _config("uneven", world),
+            "launch": {k: tuned[k] for k in ("warps_per_block", "blocks_per_sm",
+                                             "queue_entries", "state_mode")},
+            "target_seeds": tseeds,
+            "cell_updates_per_s": cells_all / total_s,
+            "cell_updates_vs_dense_sweep": _dense_sweep_roof(
+                cells_all / total_s, peaks, pk),
+            "trials_per_s": trials_all / total_s,
+            "mean_steps_per_sim": steps_sum / (n * args.steps),
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": UNIT,
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "steps": e2e_steps,
+                    "device_value_same_steps": n * e2e_steps * world / dev_same,
+                    "timed": "fire_simulate_multi and fire_fitness on pinned "
+                             "host buffers, wall clock per call, with the "
+                             "seeds and L2 flush of the first device-timed "
+                             "steps"},
+            # per step: k_order_count, k_order_scan, k_order_scatter,
+            # k_simulate (graph) and k_fitness
+            "gpu_launches": 5 * args.steps,
+            "clocks": ck,
+        }
+        print(json.dumps(line))
+    for m in maps:
+        m.free()
+    ctx.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# Native arm, --workload ga512: one GA generation of the 512 x 512 map
+
+def run_ga512(args):
+    """fire_simulate_batch in longest-first order plus the fitness kernel on
+    device-resident inputs, at the autotuned launch shape."""
+    g = _setup_gpu()
+    if g is None:
+        print(json.dumps({"metric": METRIC, "error": "no CUDA device"}))
+        return 1
+    torch, fire, ctx, dev, stream, rank, world, local = g
+    nsteps = args.warmup + args.steps
+    first = parallel.rank_seed_offset(rank, SIMS * (nsteps + 2))
+    wl = workloads.ga_generation_512(POP, REPS, first_seed=first)
+    m = ctx.landscape_upload(wl.land)
+    H, W = wl.shape
+    tseed, target = _gpu_target(fire, m, wl.ignition,
+                                int((wl.land.veg != 0).sum()))
     m.target_upload(target)
-    # launch shape: the autotuner times its candidate shapes on this batch in
-    # the step's longest-first order (outside the timed region) and the
-    # library uses the fastest
+    # the autotuner times its candidate shapes on this batch in the step's
+    # longest-first order (outside the timed region); the library keeps the
+    # fastest
     tuned = fire.fire_autotune(ctx, [m], None, wl.params, wl.ignitions,
                                wl.seeds, longest_first=True)
-
-    nsteps = args.warmup + args.steps
     p_dev = torch.tensor(wl.params, dtype=torch.float64, device=dev)
     g_dev = torch.tensor(wl.ignitions, dtype=torch.int32, device=dev)
-    seeds_all = [wl.seeds + np.uint64(k * SIMS) for k in range(nsteps)]
-    s_dev = [torch.tensor(s.view(np.int64), device=dev) for s in seeds_all]
+    seeds_host = [wl.seeds + np.uint64(k * SIMS) for k in range(nsteps)]
+    s_dev = [torch.tensor(s.view(np.int64), device=dev) for s in seeds_host]
     outs = [torch.zeros((SIMS, 6), dtype=torch.int32, device=dev)
             for _ in range(nsteps)]
     fit = [torch.zeros(SIMS, dtype=torch.float64, device=dev)
@@ -331,10 +660,8 @@ def run_native(args):
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-
-    ev = [(torch.cuda.Event(enable_timing=True),
-           torch.cuda.Event(enable_timing=True),
-           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    ev = [tuple(torch.cuda.Event(enable_timing=True) for _ in range(3))
+          for _ in range(args.steps)]
     clocks = Clocks(local)
     for j in range(args.steps):
         k = args.warmup + j
@@ -353,98 +680,79 @@ def run_native(args):
         torch.distributed.barrier()
     sim_ms = [ev[j][0].elapsed_time(ev[j][1]) for j in range(args.steps)]
     step_ms = [ev[j][0].elapsed_time(ev[j][2]) for j in range(args.steps)]
-    total_s = sum(step_ms) / 1e3
-    total_s = parallel.max_over_ranks(total_s, world, dev)
-
-    # statistics of the timed steps
+    total_s = parallel.max_over_ranks(sum(step_ms) / 1e3, world, dev)
     res = [fire.results_view(outs[args.warmup + j]) for j in range(args.steps)]
     steps_sum = sum(int(r["steps"].astype(np.int64).sum()) for r in res)
     trials_sum = sum(int(r["trials"].astype(np.int64).sum()) for r in res)
-    # all ranks' counts (each rank simulates its own seeds)
     steps_all = parallel.sum_over_ranks(steps_sum, world, dev)
     trials_all = parallel.sum_over_ranks(trials_sum, world, dev)
     assert all(int((r["status"] & (fire.STATUS_BAD_IGNITION
                                     | fire.STATUS_TIMEOUT)).max()) == 0
                for r in res)
-    sims_total = SIMS * args.steps * world
-    value = sims_total / total_s
+    value = SIMS * args.steps * world / total_s
 
-    # roofline of the simulation kernel (ALU bound): algorithmic operations
-    # per launch over its mean event-timed duration
-    peaks, peaks_kind = _peaks()
-    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    props = torch.cuda.get_device_properties(dev)
-    peak_ops = props.multi_processor_count * ALU_LANES_PER_SM * sm_max * 1e6
-    mean_sim_s = sum(sim_ms) / len(sim_ms) / 1e3
-    ops_per_launch = trials_sum / args.steps * OPS_PER_TRIAL
-    achieved = ops_per_launch / mean_sim_s
-    traffic = _committed_traffic()
-
-    # end to end through the C ABI with host buffers (pinned)
-    pin_p = torch.from_numpy(wl.params.copy()).pin_memory().numpy()
-    pin_g = torch.from_numpy(wl.ignitions.copy()).pin_memory().numpy()
-    e2e_steps = max(3, min(args.steps, 10))
-    e2e_seeds = [torch.from_numpy((wl.seeds + np.uint64((nsteps + j) * SIMS))
-                                  .view(np.int64)).pin_memory().numpy()
-                 .view(np.uint64) for j in range(e2e_steps)]
-    m.simulate_batch(pin_p, pin_g, e2e_seeds[0],    # warm the staging buffers
-                     longest_first=True)
-    t0 = time.perf_counter()
+    # end to end through the C ABI with host buffers (pinned): the same seeds
+    # and L2 flush as the device-timed steps
+    pin_p = _pinned(torch, wl.params)
+    pin_g = _pinned(torch, wl.ignitions)
+    pin_s = [_pinned(torch, s) for s in seeds_host]
+    m.simulate_batch(pin_p, pin_g, pin_s[0], longest_first=True)
+    e2e_steps = min(args.steps, 10)
+    e2e_s = 0.0
     for j in range(e2e_steps):
-        r, _ = m.simulate_batch(pin_p, pin_g, e2e_seeds[j], longest_first=True)
+        k = args.warmup + j
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r, _ = m.simulate_batch(pin_p, pin_g, pin_s[k], longest_first=True)
         f = fire.fire_fitness(ctx, r, fire.FITNESS_JACCARD)
-    e2e_s = time.perf_counter() - t0
+        e2e_s += time.perf_counter() - t0
+        assert f.shape == (SIMS,)
     e2e_s = parallel.max_over_ranks(e2e_s, world, dev)
     e2e_value = SIMS * e2e_steps * world / e2e_s
+    dev_same = parallel.max_over_ranks(sum(step_ms[:e2e_steps]) / 1e3, world,
+                                       dev)
     h2d = SIMS * (40 + 8 + 8) + SIMS * 24
     d2h = SIMS * 24 + SIMS * 8
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cores = os.cpu_count() or 1
-        tw = workloads.ga_generation_512(POP, REPS, first_seed=first)
-        nsample = min(SIMS, 32 * cores)
-        v, dt, _ = oracle_throughput(tw, target, nsample, cores)
-        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": f"first {nsample} simulations of one 4096-simulation "
-                         f"generation ({dt:.1f} s wall)"}
+        cpu = cpu_baseline("ga512", os.cpu_count() or 1)
+        cpu["targets_match_gpu"] = cpu["target_seeds"] == [int(tseed)]
 
     if rank == 0:
+        launch_s = sum(sim_ms) / len(sim_ms) / 1e3
+        peaks, pk, roof = _alu_roof(torch, dev, trials_sum / args.steps,
+                                    launch_s)
+        roof["traffic"] = _committed_traffic()
+        roof["timed"] = ("k_spread_key, k_rank_desc and k_simulate, CUDA "
+                         "events on the launching stream")
+        roof["memory"] = _memory_roofs(launch_s, peaks, pk)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * total_s / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "u32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "H": H, "W": W,
-                       "sims_per_step": SIMS, "target_seed": tseed,
-                       "target_cells": int(target.sum()),
-                       "l2": "flushed between timed steps (256 MB write)",
-                       "parallelism": f"replicas x{world}",
-                       "order": "longest-first by predicted spread "
-                                "(FIRE_LONGEST_FIRST)",
-                       "launch": {k: tuned[k] for k in (
-                           "warps_per_block", "blocks_per_sm",
-                           "queue_entries", "state_mode")}},
+            "config": _config("ga512", world),
+            "launch": {k: tuned[k] for k in ("warps_per_block", "blocks_per_sm",
+                                             "queue_entries", "state_mode")},
+            "target_seed": int(tseed), "target_cells": int(target.sum()),
             "cell_updates_per_s": steps_all * H * W / total_s,
             "cell_updates_vs_dense_sweep": _dense_sweep_roof(
-                steps_all * H * W / total_s, peaks, peaks_kind),
+                steps_all * H * W / total_s, peaks, pk),
             "trials_per_s": trials_all / total_s,
             "mean_steps_per_sim": steps_all / (SIMS * args.steps * world),
-            "roofline": {"bound": "alu", "achieved": achieved / 1e12,
-                         "peak": peak_ops / 1e12, "unit": "Tops/s",
-                         "frac": achieved / peak_ops, "traffic": traffic,
-                         "kernel": "k_simulate",
-                         "peak_source": f"{props.multi_processor_count} SMs x "
-                                        f"{ALU_LANES_PER_SM} lanes x "
-                                        f"{sm_max:.0f} MHz ({peaks_kind} max "
-                                        "SM clock)",
-                         "ops_per_trial": OPS_PER_TRIAL,
-                         "kernel_ms": 1e3 * mean_sim_s,
-                         "memory": _memory_roofs(mean_sim_s, peaks, peaks_kind)},
+            "roofline": roof,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT,
-                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "steps": e2e_steps,
+                    "device_value_same_steps": SIMS * e2e_steps * world / dev_same,
+                    "timed": "fire_simulate_batch and fire_fitness on pinned "
+                             "host buffers, wall clock per call, with the "
+                             "seeds and L2 flush of the first device-timed "
+                             "steps"},
             # per step: k_spread_key and k_rank_desc (longest-first order),
             # k_simulate, k_fitness
             "gpu_launches": 4 * args.steps,
@@ -452,154 +760,6 @@ def run_native(args):
         }
         print(json.dumps(line))
     m.free()
-    ctx.close()
-    if world > 1:
-        torch.distributed.destroy_process_group()
-    return 0
-
-
-UNEVEN = ("uneven_fires: nine fires on 200x300 ... 2000x1500 grids (10.9 M "
-          "cells), 100,000 simulations in one persistent launch (11,112 on "
-          "the first fire, 11,111 on each other), Uniform[-30,30] parameters, "
-          "centre ignitions, targets from the reference parameters")
-
-
-def run_uneven(args):
-    """Nine-fire uneven batch: one fire_simulate_multi call per step (CUDA
-    graph replay) plus the fitness kernel."""
-    import torch
-
-    rank, world, local = parallel.env_rank()
-    if world > 1:
-        import torch.distributed as dist
-
-        dist.init_process_group("nccl")
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    import __graft_entry__
-
-    __graft_entry__.build()
-    from paper_1701_03549_gb300 import fire
-
-    stream = torch.cuda.Stream(dev)
-    torch.cuda.set_stream(stream)
-    ctx = fire.Context(local, stream)
-    nsteps = args.warmup + args.steps
-    wl = workloads.uneven_fires(first_seed=1 + rank * 100_000 * (nsteps + 1))
-    n = wl.n
-    maps = [ctx.landscape_upload(L) for L in wl.lands]
-    for j, (m, L) in enumerate(zip(maps, wl.lands)):
-        ign = np.asarray([wl.ignitions[np.argmax(wl.map_of_sim == j)]],
-                         np.int32)
-        burnable = int((L.veg != 0).sum())
-
-        def sim_target(seed, m=m, ign=ign):
-            _, bs = m.simulate_batch(np.asarray([synth.TRUTH_BETA]), ign,
-                                     np.asarray([seed], np.uint64),
-                                     want_steps=True)
-            return bs[0] >= 0
-
-        _, tg = workloads.pick_target(sim_target, burnable)
-        m.target_upload(tg)
-    # autotune on a stratified tenth of the batch
-    sub = np.arange(0, n, 10)
-    tuned = fire.fire_autotune(ctx, maps, wl.map_of_sim[sub], wl.params[sub],
-                               wl.ignitions[sub], wl.seeds[sub])
-    t_mi = torch.tensor(wl.map_of_sim, device=dev)
-    t_p = torch.tensor(wl.params, dtype=torch.float64, device=dev)
-    t_g = torch.tensor(wl.ignitions, device=dev)
-    t_s = torch.tensor(wl.seeds.view(np.int64), device=dev)
-    seeds_all = [torch.tensor((wl.seeds + np.uint64(k * n)).view(np.int64),
-                              device=dev) for k in range(nsteps)]
-    out = torch.zeros((n, 6), dtype=torch.int32, device=dev)
-    fit = torch.zeros(n, dtype=torch.float64, device=dev)
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    torch.cuda.synchronize()
-
-    def step(k):
-        t_s.copy_(seeds_all[k])
-        fire.fire_simulate_multi(ctx, maps, t_mi, t_p, t_g, t_s, device=True,
-                                 out=out, graph=True)
-        fire.fire_fitness(ctx, out, fire.FITNESS_JACCARD, device=True, out=fit)
-
-    for k in range(args.warmup):
-        flush.zero_()
-        step(k)
-    torch.cuda.synchronize()
-    if world > 1:
-        torch.distributed.barrier()
-    clocks = Clocks(local)
-    total_ms = 0.0
-    steps_sum = trials_sum = cells = 0
-    sizes = np.array([L.veg.size for L in wl.lands], np.int64)[wl.map_of_sim]
-    for j in range(args.steps):
-        k = args.warmup + j
-        flush.zero_()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        t_s.copy_(seeds_all[k])
-        e0.record(stream)
-        fire.fire_simulate_multi(ctx, maps, t_mi, t_p, t_g, t_s, device=True,
-                                 out=out, graph=True)
-        fire.fire_fitness(ctx, out, fire.FITNESS_JACCARD, device=True, out=fit)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        total_ms += e0.elapsed_time(e1)
-        r = fire.results_view(out)
-        steps_sum += int(r["steps"].astype(np.int64).sum())
-        cells += int((r["steps"].astype(np.int64) * sizes).sum())
-        trials_sum += int(r["trials"].astype(np.int64).sum())
-    ck = clocks.stop()
-    total_s = parallel.max_over_ranks(total_ms / 1e3, world, dev)
-    value = n * args.steps * world / total_s
-    cells_all = parallel.sum_over_ranks(cells, world, dev)
-    trials_all = parallel.sum_over_ranks(trials_sum, world, dev)
-    if rank == 0:
-        peaks, peaks_kind = _peaks()
-        sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-        props = torch.cuda.get_device_properties(dev)
-        peak_ops = props.multi_processor_count * ALU_LANES_PER_SM * sm_max * 1e6
-        achieved = trials_sum * OPS_PER_TRIAL / (total_ms / 1e3)
-        uprof = _committed_profile("k_simulate_uneven_traffic.json")
-        line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": total_s * 1e3 / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "u32", "data": "synthetic",
-            "config": {"workload": UNEVEN, "sims_per_step": n,
-                       "cells_total": int(sum(L.veg.size for L in wl.lands)),
-                       "graph": True, "l2": "flushed between timed steps "
-                       "(256 MB write)",
-                       "launch": {k: tuned[k] for k in (
-                           "warps_per_block", "blocks_per_sm",
-                           "queue_entries", "state_mode")}},
-            "cell_updates_per_s": cells_all / total_s,
-            "cell_updates_vs_dense_sweep": _dense_sweep_roof(
-                cells_all / total_s, peaks, peaks_kind),
-            "trials_per_s": trials_all / total_s,
-            "mean_steps_per_sim": steps_sum / (n * args.steps),
-            "roofline": {"bound": "alu", "achieved": achieved / 1e12,
-                         "peak": peak_ops / 1e12, "unit": "Tops/s",
-                         "frac": achieved / peak_ops,
-                         "traffic": (None if uprof is None
-                                     else uprof["dram_bytes_per_launch"]),
-                         "kernel": "k_simulate",
-                         "peak_source": f"{props.multi_processor_count} SMs x "
-                                        f"{ALU_LANES_PER_SM} lanes x "
-                                        f"{sm_max:.0f} MHz ({peaks_kind})",
-                         "ops_per_trial": OPS_PER_TRIAL,
-                         "kernel_ms": total_ms / args.steps,
-                         "memory": _memory_roofs(
-                             total_ms / args.steps / 1e3, peaks, peaks_kind,
-                             "k_simulate_uneven_traffic.json")},
-            "cpu_baseline": None, "e2e": None,
-            "gpu_launches": 5 * args.steps,
-            "clocks": ck,
-        }
-        print(json.dumps(line))
-    for m in maps:
-        m.free()
     ctx.close()
     if world > 1:
         torch.distributed.destroy_process_group()
@@ -888,12 +1048,13 @@ def main():
                     default="native")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload",
-                    choices=("ga512", "uneven", "surrogate", "surrogate_step"),
-                    default="ga512",
-                    help="ga512: 512x512 GA generation (default line); "
-                         "uneven: nine fires 200x300..2000x1500, 100k "
-                         "simulations in one launch; surrogate: the "
-                         "surrogate-screened GA against the plain GA")
+                    choices=("uneven", "ga512", "surrogate", "surrogate_step"),
+                    default="uneven",
+                    help="uneven (default): nine fires 200x300..2000x1500, "
+                         "100k simulations in one launch; ga512: one "
+                         "512x512 GA generation; surrogate: the "
+                         "surrogate-screened GA against the plain GA; "
+                         "surrogate_step: the surrogate network alone")
     ap.add_argument("--generations", type=int, default=50)
     ap.add_argument("--train-steps", type=int, default=1500)
     ap.add_argument("--train-groups", type=int, default=6250)
@@ -901,14 +1062,19 @@ def main():
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
+        if args.workload not in ("uneven", "ga512"):
+            print(json.dumps({"impl": "reference", "unavailable":
+                              "the oracle arm times the automaton workloads "
+                              "(uneven, ga512) only"}))
+            return 0
         return run_reference(args)
-    if args.workload == "uneven":
-        return run_uneven(args)
+    if args.workload == "ga512":
+        return run_ga512(args)
     if args.workload == "surrogate":
         return run_surrogate(args)
     if args.workload == "surrogate_step":
         return run_surrogate_step(args)
-    return run_native(args)
+    return run_uneven(args)
 
 
 if __name__ == "__main__":

@@ -145,7 +145,10 @@ FIRE_API void fire_destroy(fire_ctx *ctx);
 /* Text of the last error on this context ("" if none).  Owned by ctx. */
 FIRE_API const char *fire_last_error(const fire_ctx *ctx);
 
-/* Block until all work issued on the context's stream has finished. */
+/* Block until all work issued on the context's stream has finished.
+ * Returns FIRE_ETIMEOUT (once) when a bounded device wait of earlier work ran
+ * out: the context's error word, or the error word of the no-alloc scratch on
+ * the context's device (fire_simulate_batch_noalloc). */
 FIRE_API int fire_sync(fire_ctx *ctx);
 
 /* Launch shape used by later simulation calls: warps per block (1..16),
@@ -199,7 +202,8 @@ FIRE_API int fire_target_upload(fire_ctx *ctx, fire_map *map, const uint8_t *bur
  *   max_steps     0 for no cap, else stop a fire after that many steps and
  *                 set FIRE_STATUS_STEP_CAP.
  * Host ignitions that are outside the grid or non-burnable make the call
- * return FIRE_EIGNITION before any work is issued. */
+ * return FIRE_EIGNITION before any work is issued; a map uploaded through a
+ * context on another device is refused with FIRE_EINVAL. */
 FIRE_API int fire_simulate_batch(fire_ctx *ctx, const fire_map *map, int n,
                         const fire_params *params, const fire_cell *ignitions,
                         const uint64_t *seeds, uint32_t max_steps,
@@ -221,8 +225,16 @@ FIRE_API int fire_simulate_batch(fire_ctx *ctx, const fire_map *map, int n,
  * device looks up the array's address once; make that first call before any
  * stream capture begins on the device.  All calls on a device share the
  * array and each clears its counter area before launching, so calls whose
- * work overlaps on the GPU race: serialise them.  Asynchronous unless
- * FIRE_SYNC is set (then a timed-out device wait returns FIRE_ETIMEOUT). */
+ * work overlaps on the GPU race: serialise them.  Flags: FIRE_DEVICE_PTRS
+ * (implied), FIRE_WANT_STEPS, FIRE_SYNC and FIRE_CELL_UNIFORM; any other flag
+ * (FIRE_LONGEST_FIRST, FIRE_GRAPH: both need library-owned buffers) is
+ * refused with FIRE_EINVAL, as is a map uploaded on another device than the
+ * context's, before any work is issued.  Asynchronous unless FIRE_SYNC is
+ * set (then a timed-out device wait returns FIRE_ETIMEOUT).  After an
+ * asynchronous call, a timed-out wait shows as FIRE_STATUS_TIMEOUT in the
+ * affected out[i].status and is returned as FIRE_ETIMEOUT by the next
+ * fire_sync on the context (which reads and clears the array's error word),
+ * provided no later no-alloc call on the device has cleared it first. */
 FIRE_API int fire_simulate_batch_noalloc(fire_ctx *ctx, const fire_map *map,
                                          int n, const fire_params *params,
                                          const fire_cell *ignitions,

@@ -220,6 +220,14 @@ int fire_sync(fire_ctx *ctx)
         cudaMemset(ctx->counter + 1, 0, 4);
         return set_err(ctx, FIRE_ETIMEOUT, "a bounded device wait ran out");
     }
+    // asynchronous fire_simulate_batch_noalloc calls keep their error word
+    // in the no-alloc scratch of this device
+    bool na = false;
+    if (noalloc_take_error(ctx->device, &na) != FIRE_OK)
+        return set_err(ctx, FIRE_ECUDA, "read the no-alloc error word");
+    if (na)
+        return set_err(ctx, FIRE_ETIMEOUT,
+                       "a bounded device wait ran out (no-alloc call)");
     return FIRE_OK;
 }
 
@@ -468,6 +476,9 @@ int fire_simulate_batch(fire_ctx *ctx, const fire_map *m, int n,
 {
     if (!ctx) return FIRE_EINVAL;
     if (!valid_map(m)) return set_err(ctx, FIRE_EINVAL, "invalid map");
+    if (m->ctx->device != ctx->device)
+        return set_err(ctx, FIRE_EINVAL, "the map was uploaded on device %d, the "
+                       "context runs on device %d", m->ctx->device, ctx->device);
     if (n < 0) return set_err(ctx, FIRE_EINVAL, "n = %d", n);
     if (n == 0) return FIRE_OK;
     if (!params || !ignitions || !seeds || !out)

@@ -237,6 +237,7 @@ int grow_device(fire_ctx *ctx, void **buf, size_t *cap, size_t need,
                 const char *what);
 size_t round16(size_t x);
 bool valid_map(const fire_map *m);
+int noalloc_take_error(int device, bool *set);
 int plan_launch(fire_ctx *ctx, int ntiles, long long n, LaunchPlan *p);
 cudaError_t launch_conv_tma(int mode, const uint16_t *in, const uint16_t *w,
                             const float *bias, const uint16_t *hprev, uint16_t *out,

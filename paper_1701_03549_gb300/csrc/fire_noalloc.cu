@@ -37,6 +37,10 @@ namespace {
 constexpr size_t kNoAllocScratchBytes = size_t(2) << 20;  // 2 MiB per GPU
 constexpr size_t kCounterBytes = 256;                     // counter + error word
 constexpr int kMaxDevices = 64;
+// Flags this entry point honours; any other flag (FIRE_LONGEST_FIRST and
+// FIRE_GRAPH need buffers the library would allocate) is refused.
+constexpr uint32_t kNoAllocFlags =
+    FIRE_DEVICE_PTRS | FIRE_WANT_STEPS | FIRE_SYNC | FIRE_CELL_UNIFORM;
 
 // The scratch itself.  In host code this name is only a host-side stand-in:
 // kernels receive the device address found by cudaGetSymbolAddress.
@@ -75,6 +79,36 @@ int scratch_address(fire_ctx *ctx, int dev, void **out)
 
 }  // namespace
 
+namespace fire {
+
+// Reads and clears the error word of the no-alloc scratch on `device` (the
+// current device), so that fire_sync reports a bounded wait that ran out in
+// an asynchronous no-alloc call.  Returns FIRE_OK with *set = 0 when the
+// scratch was never set up on that device.
+int noalloc_take_error(int device, bool *set)
+{
+    *set = false;
+    void *p = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_setup_mu);
+        if (device < 0 || device >= kMaxDevices || !g_scratch_addr[device])
+            return FIRE_OK;
+        p = g_scratch_addr[device];
+    }
+    uint32_t *errw = static_cast<uint32_t *>(p) + 1;
+    uint32_t v = 0;
+    cudaError_t e = cudaMemcpy(&v, errw, sizeof v, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return FIRE_ECUDA;
+    if (v) {
+        *set = true;
+        e = cudaMemset(errw, 0, sizeof v);
+        if (e != cudaSuccess) return FIRE_ECUDA;
+    }
+    return FIRE_OK;
+}
+
+}  // namespace fire
+
 extern "C" int fire_simulate_batch_noalloc(fire_ctx *ctx, const fire_map *m,
                                            int n, const fire_params *params,
                                            const fire_cell *ignitions,
@@ -84,7 +118,16 @@ extern "C" int fire_simulate_batch_noalloc(fire_ctx *ctx, const fire_map *m,
                                            int32_t *burn_step)
 {
     if (!ctx) return FIRE_EINVAL;
-    if (!m || !m->feat) return na_err(ctx, FIRE_EINVAL, "invalid map");
+    // every check below runs before the first CUDA call
+    if (!valid_map(m)) return na_err(ctx, FIRE_EINVAL, "invalid map");
+    if (m->ctx->device != ctx->device)
+        return na_err(ctx, FIRE_EINVAL,
+                      "the map was uploaded on another device than the context's");
+    if (flags & ~kNoAllocFlags)
+        return na_err(ctx, FIRE_EINVAL,
+                      "flag not supported by the no-alloc entry point (it takes "
+                      "FIRE_DEVICE_PTRS, FIRE_WANT_STEPS, FIRE_SYNC and "
+                      "FIRE_CELL_UNIFORM only)");
     if (n < 0) return na_err(ctx, FIRE_EINVAL, "negative simulation count");
     if (n == 0) return FIRE_OK;
     if (!params || !ignitions || !seeds || !out)

@@ -90,6 +90,13 @@ class MultiWorkload:
         return self.params.shape[0]
 
 
+def uneven_lands():
+    """Maps of the nine-fire uneven batch: fire i on a (200 + 225 i) x
+    (300 + 150 i) grid from map seed 100 + i, constant 45 degree wind."""
+    return [synth.landscape(H, W, seed=100 + i)
+            for i, (H, W) in enumerate(synth.uneven_fire_shapes())]
+
+
 def uneven_fires(n_total: int = 100_000, param_seed: int = 0,
                  first_seed: int = 1) -> MultiWorkload:
     """Nine fires on grids 200x300 ... 2000x1500 (fire i: 200 + 225 i rows,
@@ -97,9 +104,7 @@ def uneven_fires(n_total: int = 100_000, param_seed: int = 0,
     its centre ignition; n_total simulations spread as evenly as possible
     over the fires (the first fires take the remainder), parameters drawn
     from the Uniform[-30, 30] initial distribution of Table 1."""
-    shapes = synth.uneven_fire_shapes()
-    lands = [synth.landscape(H, W, seed=100 + i)
-             for i, (H, W) in enumerate(shapes)]
+    lands = uneven_lands()
     k = len(lands)
     counts = [n_total // k + (1 if i < n_total % k else 0) for i in range(k)]
     map_of_sim = np.repeat(np.arange(k, dtype=np.int32), counts)
@@ -108,3 +113,20 @@ def uneven_fires(n_total: int = 100_000, param_seed: int = 0,
     return MultiWorkload("uneven_fires", lands, map_of_sim, params,
                          ign[map_of_sim], synth.replicate_seeds(n_total,
                                                                first_seed))
+
+
+def stratified_sample(groups: np.ndarray, per_group: int) -> np.ndarray:
+    """Indices of a stratified sample of a batch: for every group label g
+    (0, 1, ...), `per_group` members evenly spaced over the batch positions
+    of that group (all of them when the group is smaller), in the order
+    round 0 of every group, round 1 of every group, ... so that a prefix of
+    the sample covers every group."""
+    groups = np.asarray(groups)
+    rounds = []
+    for g in range(int(groups.max()) + 1):
+        pos = np.flatnonzero(groups == g)
+        k = min(per_group, pos.size)
+        rounds.append(pos[(np.arange(k) * pos.size) // max(k, 1)])
+    width = max(r.size for r in rounds)
+    out = [r[j] for j in range(width) for r in rounds if j < r.size]
+    return np.asarray(out, np.int64)

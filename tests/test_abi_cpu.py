@@ -101,3 +101,24 @@ def test_tile_row_division_by_magic_multiply():
         m = np.uint64(2 ** 32 - 1) // TW
         q = ((k + np.uint64(1)) * m) >> np.uint64(32)
         assert np.array_equal(q, k // TW), lo
+
+
+def test_simulation_guards_refuse_before_any_cuda_call(libpath, tmp_path):
+    """A map uploaded on another device than the context's, and flags the
+    no-alloc entry point does not honour, are refused with FIRE_EINVAL before
+    any CUDA call: contexts and maps are built in host memory by a small
+    program compiled against the library (tests/abi_guards_host.cu), so the
+    checks run here without a GPU."""
+    from paper_1701_03549_gb300 import build
+
+    src = os.path.join(ROOT, "tests", "abi_guards_host.cu")
+    so = str(tmp_path / "libabi_guards.so")
+    libdir = os.path.dirname(libpath)
+    cmd = [build._nvcc(), *build.ARCH, "-std=c++17", "-O1", "-Xcompiler",
+           "-fPIC", "-shared", "-I", build.INCLUDE, "-I", build.CSRC, src,
+           "-o", so, "-L" + libdir, "-lfire", "-Xlinker", "-rpath=" + libdir]
+    subprocess.run(cmd, check=True, capture_output=True)
+    lib = ctypes.CDLL(so)
+    msg = ctypes.create_string_buffer(512)
+    rc = lib.abi_guard_cases(msg, 512)
+    assert rc == 0, msg.value.decode()

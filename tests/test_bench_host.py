@@ -4,6 +4,8 @@ record (a record whose source hash differs from the kernel sources gives no
 traffic), and the dense-sweep reference rate."""
 import json
 
+import numpy as np
+
 import pytest
 
 import bench
@@ -77,7 +79,47 @@ def test_dense_sweep_reference_rate():
 
 
 def test_trial_op_count():
-    # one Philox4x32-10 word: 10 rounds x 8 ops over 4 words; Eq. 1 and the
-    # comparison: 4 FMAs, exp 2, 1 + e 1, reciprocal 1, draw to float 2,
-    # compare 1
-    assert bench.OPS_PER_TRIAL == 10 * 8 // 4 + (4 + 2 + 1 + 1 + 2 + 1)
+    # a quarter of one Philox4x32-10 block: 10 rounds of (two 32x32->64
+    # multiplies as 4 operations, two 3-way xors as 4, two key additions)
+    # over 4 words = 25 integer operations; Eq. 1 in one direction, the
+    # logistic and the comparison with the draw: about 15 single-precision
+    # operations
+    assert bench.OPS_PER_TRIAL == 10 * (4 + 4 + 2) // 4 + 15
+
+
+def test_oracle_extrapolation_is_per_fire():
+    """Batch time = sum over fires of (simulations of the fire x mean
+    single-core seconds of its sampled simulations) / cores."""
+    res = [(0, 1.0, 5), (0, 3.0, 9), (1, 10.0, 40)]
+    est = bench._extrapolate(res, {0: 100, 1: 10}, 4)
+    assert est == pytest.approx((100 * 2.0 + 10 * 10.0) / 4)
+
+
+def test_both_arms_name_the_same_config():
+    """The native line and the oracle arm print the same config object (the
+    launch shape sits outside it), so the two lines compare like for like."""
+    for kind in ("uneven", "ga512"):
+        a, b = bench._config(kind, 1), bench._config(kind, 1)
+        assert a == b and "launch" not in a
+        assert a["l2"] == bench.L2_NOTE
+    assert bench._config("uneven", 1)["sims_per_step"] == 100_000
+    assert bench._config("uneven", 1)["cells_total"] == sum(
+        H * W for H, W in bench.synth.uneven_fire_shapes())
+
+
+def test_stratified_sample_of_the_uneven_batch():
+    """16 simulations per fire, evenly spaced within each fire's block of
+    the batch, ordered so that every prefix of 9 covers the nine fires."""
+    from paper_1701_03549_gb300 import workloads
+
+    counts = [11112] + [11111] * 8
+    mos = np.repeat(np.arange(9), counts)
+    idx = workloads.stratified_sample(mos, 16)
+    assert idx.size == 144 and len(set(idx.tolist())) == 144
+    assert np.array_equal(np.bincount(mos[idx], minlength=9), [16] * 9)
+    for k in range(16):
+        assert sorted(mos[idx[9 * k:9 * k + 9]].tolist()) == list(range(9))
+    starts = np.concatenate([[0], np.cumsum(counts)[:-1]])
+    for j in range(9):
+        pos = np.sort(idx[mos[idx] == j]) - starts[j]
+        assert pos[0] == 0 and np.all(np.diff(pos) >= counts[j] // 16)

@@ -1,9 +1,7 @@
-"""Parity at the benchmark's full sizes and launch configurations, and at the
-largest grid the library accepts, on sampled outputs the oracle computes one
-by one:
+"""Parity at full sizes and at the largest grid the library accepts, on sampled
+outputs the oracle computes one by one (the benchmark's own launches are
+checked in test_gpu_bench_launch.py):
 
-* the nine-fire uneven batch (100,000 simulations on grids up to 2000 x 1500)
-  in one graph-replayed fire_simulate_multi launch at the autotuned shape;
 * the 1024 x 1024 ignition search (32 x 32 candidates x 64 replicates =
   65,536 simulations): candidate cells against the nearest-cell definition,
   the fitness map against the replicate means of the batch's own results,
@@ -22,31 +20,6 @@ import pytest
 pytestmark = pytest.mark.gpu
 
 _W = {}
-
-
-def _init_uneven():
-    import oracle
-
-    from paper_1701_03549_gb300 import workloads
-
-    wl = workloads.uneven_fires()
-    _W["wl"] = wl
-    _W["F"] = [oracle.Features(L) for L in wl.lands]
-
-
-def _run_uneven(args):
-    i, target_seed = args
-    wl = _W["wl"]
-    j = int(wl.map_of_sim[i])
-    tgt = _uneven_target(wl.lands[j], target_seed + j)
-    r, _ = _W["F"][j].simulate(wl.params[i], tuple(wl.ignitions[i]),
-                               int(wl.seeds[i]), target=tgt, want_steps=False)
-    return i, r
-
-
-def _uneven_target(land, seed):
-    rng = np.random.default_rng(seed)
-    return rng.random(land.veg.shape) < 0.2
 
 
 def _init_ign(H, W, map_seed, wind_seed):
@@ -118,64 +91,6 @@ def env():
     __graft_entry__.build()
     oracle.build()
     return torch
-
-
-def test_uneven_batch_full_size_sample(env):
-    torch = env
-    from paper_1701_03549_gb300 import fire, workloads
-
-    target_seed = 500
-    pool = _pool(_init_uneven)   # before the first GPU call
-    try:
-        wl = workloads.uneven_fires()
-        ctx = fire.Context(0)
-        maps = [ctx.landscape_upload(L) for L in wl.lands]
-        for j, (m, L) in enumerate(zip(maps, wl.lands)):
-            m.target_upload(_uneven_target(L, target_seed + j))
-        sub = np.arange(0, wl.n, 10)
-        fire.fire_autotune(ctx, maps, wl.map_of_sim[sub], wl.params[sub],
-                           wl.ignitions[sub], wl.seeds[sub])
-        dev = torch.device("cuda")
-        t_mi = torch.tensor(wl.map_of_sim, device=dev)
-        t_p = torch.tensor(wl.params, dtype=torch.float64, device=dev)
-        t_g = torch.tensor(wl.ignitions, device=dev)
-        t_s = torch.tensor(wl.seeds.view(np.int64), device=dev)
-        out = torch.zeros((wl.n, 6), dtype=torch.int32, device=dev)
-        outs = []
-        for _ in range(2):   # capture, then replay of the same graph
-            out.zero_()
-            fire.fire_simulate_multi(ctx, maps, t_mi, t_p, t_g, t_s,
-                                     device=True, out=out, graph=True,
-                                     sync=True)
-            outs.append(fire.results_view(out).copy())
-        assert np.array_equal(outs[0], outs[1])
-        res = outs[0]
-        ctx.close()
-        # samples, in index order per map: the first fire that dies within
-        # 20 steps, the first two longer ones the oracle finishes within a
-        # bounded time (steps x cells), and on every third map one larger
-        sizes = np.array([L.veg.size for L in wl.lands], np.int64)
-        steps = res["steps"].astype(np.int64)
-        cost = steps * sizes[wl.map_of_sim]
-        picks = []
-        for j in range(len(wl.lands)):
-            on = wl.map_of_sim == j
-            picks += list(np.flatnonzero(on & (steps < 20))[:1])
-            picks += list(np.flatnonzero(on & (steps >= 20) &
-                                         (cost <= 2_000_000_000))[:2])
-            big = np.flatnonzero(on & (cost > 2_000_000_000) &
-                                 (cost <= 4_000_000_000))
-            if j % 3 == 0 and len(big):
-                picks.append(big[0])
-        assert len(picks) >= 18
-        checked = pool.map(_run_uneven, [(int(i), target_seed) for i in picks],
-                           chunksize=1)
-    finally:
-        pool.close()
-        pool.join()
-    for i, o in checked:
-        for k in ("burnt", "inter", "target", "steps", "status", "trials"):
-            assert int(res[k][i]) == o[k], (i, k, int(res[k][i]), o[k])
 
 
 def test_ignition_search_full_size_sample(env):

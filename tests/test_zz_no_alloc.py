@@ -97,3 +97,32 @@ def test_noalloc_rejects_state_beyond_its_scratch(env):
     assert e.value.code == fire.FIRE_EINVAL
     assert "no-alloc" in str(e.value)
     m.free()
+
+
+def test_noalloc_takes_no_device_memory(env):
+    """The promise itself: on a context that has never simulated, a call
+    whose per-block state lives in the scratch array (1024 x 1024 grid) leaves
+    the device's free memory unchanged.  The first call (address lookup,
+    module loading) runs before the measurement; every tensor the calls use is
+    allocated before it too."""
+    torch, fire, _ = env
+    ctx = fire.Context(0)
+    land = synth.landscape(1024, 1024, seed=3, wind_seed=3)
+    m = ctx.landscape_upload(land)
+    ign = synth.centre_ignition(land.veg)
+    params = np.array([synth.TRUTH_BETA, [0.5, 0, 0, 0, 0]])
+    p, g, s = _device_args(torch, params,
+                           np.tile(np.asarray(ign, np.int32), (2, 1)),
+                           np.array([21, 22], np.uint64))
+    out = torch.zeros((2, 6), dtype=torch.int32, device=p.device)
+    m.simulate_batch_noalloc(p, g, s, out, sync=True)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info(0)
+    for _ in range(3):
+        m.simulate_batch_noalloc(p, g, s, out, sync=True)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info(0)
+    assert free1 == free0, (free0, free1)
+    assert int(fire.results_view(out)["burnt"][0]) > 1
+    m.free()
+    ctx.close()
