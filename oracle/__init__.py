@@ -120,6 +120,10 @@ def lib():
                                           C.c_int, C.c_uint64, C.c_int,
                                           C.c_double, C.c_void_p, C.c_void_p,
                                           C.c_void_p]
+        L.orc_snap_ignition.restype = C.c_int
+        L.orc_snap_ignition.argtypes = [C.POINTER(_Map), C.c_void_p,
+                                        C.c_double, C.c_double, C.c_void_p,
+                                        C.c_void_p]
         _lib = L
     return _lib
 
@@ -299,6 +303,19 @@ class Features:
         if rc:
             raise ValueError("target has no burnable burnt cell")
         return fm, cells, xy
+
+    def snap_ignition(self, target, x: float, y: float):
+        """Ignition cell (row, col) of the genes x (column) and y (row): the
+        burnable target cell nearest to the clamped, rounded point (see
+        fire_oracle.c)."""
+        tg = np.ascontiguousarray(target, np.uint8)
+        r = np.zeros(1, np.int32)
+        c = np.zeros(1, np.int32)
+        rc = lib().orc_snap_ignition(C.byref(self._m), _p(tg), float(x),
+                                     float(y), _p(r), _p(c))
+        if rc:
+            raise ValueError("target has no burnable burnt cell")
+        return int(r[0]), int(c[0])
 
     def burn_frequency(self, beta, ignition, seed0: int, nseeds: int,
                        mode: int = 0, burn_time=None):

@@ -802,3 +802,38 @@ int orc_ignition_search(const orc_map *m, const uint8_t *target,
     xy[3] = k > 1 ? sqrt(vy / (double)(k - 1)) : 0.0;
     return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Ignition point as two more genes (Sec. 3, Table 3; Appendix B: with the
+ * ignition unknown the search runs over seven parameters, x and y added).
+ * The paper starts those fires from points of the reference fire's burnt
+ * area.  Reading: gene x is the column and y the row; each is clamped to the
+ * grid ([0, W - 1] and [0, H - 1], a NaN counting as 0), rounded half up to
+ * an integer, and the fire starts from the burnable cell of the target burnt
+ * area nearest to that point (squared distance, ties to the lower row-major
+ * index) - the same nearest-cell rule as the lattice candidates of
+ * orc_ignition_search.  Returns -1 when the target has no burnable cell.   */
+static double orc_clamp_gene(double v, double hi)
+{
+    if (!(v >= 0.0)) return 0.0;   /* NaN and negatives */
+    return v > hi ? hi : v;
+}
+
+int orc_snap_ignition(const orc_map *m, const uint8_t *target, double x,
+                      double y, int32_t *row, int32_t *col)
+{
+    const int H = m->H, W = m->W;
+    const long long C = (long long)floor(orc_clamp_gene(x, (double)(W - 1)) + 0.5);
+    const long long R = (long long)floor(orc_clamp_gene(y, (double)(H - 1)) + 0.5);
+    long long best = -1, bestd = 0;
+    for (long i = 0; i < (long)H * W; ++i) {
+        if (!target[i] || !m->burnable[i]) continue;
+        const long long dr = i / W - R, dc = i % W - C;
+        const long long d = dr * dr + dc * dc;
+        if (best < 0 || d < bestd) { best = i; bestd = d; }
+    }
+    if (best < 0) return -1;
+    *row = (int32_t)(best / W);
+    *col = (int32_t)(best % W);
+    return 0;
+}

@@ -2,6 +2,7 @@
 snapping checked on hand-built scars, fitness against the p = 0 closed form,
 and the ensemble statistics against numpy."""
 import numpy as np
+import pytest
 
 from paper_1701_03549_gb300 import synth
 
@@ -86,3 +87,75 @@ def test_ensemble_statistics(oracle_mod):
     b = int(np.argmin(fm3.ravel()))
     assert xy3.tolist() == [cells3.reshape(-1, 2)[b, 1], 0.0,
                             cells3.reshape(-1, 2)[b, 0], 0.0]
+
+
+# ---------------------------------------------------------------------------
+# The ignition point as two more genes (Sec. 3, Table 3): gene x (column) and
+# y (row) clamped to the grid, rounded half up, moved to the nearest burnable
+# cell of the target burnt area (ties to the lower row-major index).
+
+def _snap_scene():
+    """9 x 11 burnable map; target cells (2, 2), (2, 6), (6, 4), (5, 9) and a
+    burnt but non-burnable cell (4, 4)."""
+    land = synth.uniform_landscape(9, 11)
+    land.veg[4, 4] = 0
+    t = np.zeros((9, 11), bool)
+    for rc in ((2, 2), (2, 6), (6, 4), (5, 9), (4, 4)):
+        t[rc] = True
+    return land, t
+
+
+# (x, y) -> (row, col), worked out by hand on the scene above
+SNAP_CASES = [
+    ((4.0, 2.0), (2, 2)),    # (2,2) and (2,6) both at d^2 = 4: lower index
+    ((4.0, 4.0), (6, 4)),    # (4,4) is at 0 but non-burnable; (6,4) at 4
+    ((4.5, 2.0), (2, 6)),    # half up: column 5, d^2 1 against 9
+    ((50.0, 0.0), (2, 6)),   # clamped to column 10: (2,6) 20, (5,9) 26
+    ((9.0, 5.0), (5, 9)),    # exactly on a target cell
+    ((-7.0, 100.0), (6, 4)), # clamped to (8, 0): (6,4) 20, (2,2) 40
+]
+
+
+def test_snap_ignition_worked_cases(oracle_mod):
+    land, t = _snap_scene()
+    F = oracle_mod.Features(land)
+    for xy, want in SNAP_CASES:
+        assert F.snap_ignition(t, *xy) == want, xy
+
+
+def test_snap_ignition_nan_and_empty_target(oracle_mod):
+    land, t = _snap_scene()
+    F = oracle_mod.Features(land)
+    assert F.snap_ignition(t, float("nan"), float("nan")) == (2, 2)
+    with pytest.raises(ValueError):
+        F.snap_ignition(np.zeros_like(t), 3.0, 3.0)
+    only_blocked = np.zeros_like(t)
+    only_blocked[4, 4] = True
+    with pytest.raises(ValueError):
+        F.snap_ignition(only_blocked, 3.0, 3.0)
+
+
+def test_snap_ignition_is_the_nearest_by_brute_force(oracle_mod):
+    """Random tiny maps and points: the cell is burnable and burnt, and no
+    burnable burnt cell is nearer to the rounded point, nor equally near with
+    a lower row-major index."""
+    rng = np.random.default_rng(8)
+    for case in range(40):
+        H, W = rng.integers(2, 8, 2)
+        land = synth.noise_landscape(int(H), int(W), 100 + case)
+        t = rng.random((H, W)) < 0.3
+        ok = t & (land.veg != 0)
+        if not ok.any():
+            continue
+        F = oracle_mod.Features(land)
+        for _ in range(6):
+            x, y = rng.uniform(-2, W + 1), rng.uniform(-2, H + 1)
+            r, c = F.snap_ignition(t, x, y)
+            assert ok[r, c]
+            C = np.floor(min(max(x, 0.0), W - 1) + 0.5)
+            R = np.floor(min(max(y, 0.0), H - 1) + 0.5)
+            d = (r - R) ** 2 + (c - C) ** 2
+            rows, cols = np.nonzero(ok)
+            dd = (rows - R) ** 2 + (cols - C) ** 2
+            assert d == dd.min()
+            assert r * W + c == (rows * W + cols)[dd == d].min()

@@ -140,6 +140,33 @@ MUTANTS = {
         "            ca[k] = k <= cut ? pa[k] : pb[k];\n"
         "            cb[k] = k <= cut ? pb[k] : pa[k];",
         [ga.test_crossover_children_are_prefix_suffix_swaps]),
+    "ignition gene rounded half down": (
+        "const long long C = (long long)floor(orc_clamp_gene(x, (double)(W - 1)) + 0.5);",
+        "const long long C = (long long)ceil(orc_clamp_gene(x, (double)(W - 1)) - 0.5);",
+        [ig.test_snap_ignition_worked_cases]),
+    "ignition gene not clamped to the grid": (
+        "    if (!(v >= 0.0)) return 0.0;   /* NaN and negatives */\n"
+        "    return v > hi ? hi : v;",
+        "    return v;",
+        [ig.test_snap_ignition_worked_cases]),
+    "snapped ignition may be non-burnable": (
+        "        if (!target[i] || !m->burnable[i]) continue;\n"
+        "        const long long dr = i / W - R, dc = i % W - C;\n"
+        "        const long long d = dr * dr + dc * dc;\n"
+        "        if (best < 0 || d < bestd) { best = i; bestd = d; }\n"
+        "    }\n    if (best < 0) return -1;\n    *row",
+        "        if (!target[i]) continue;\n"
+        "        const long long dr = i / W - R, dc = i % W - C;\n"
+        "        const long long d = dr * dr + dc * dc;\n"
+        "        if (best < 0 || d < bestd) { best = i; bestd = d; }\n"
+        "    }\n    if (best < 0) return -1;\n    *row",
+        [ig.test_snap_ignition_worked_cases]),
+    "snapped ignition ties go to the higher index": (
+        "        if (best < 0 || d < bestd) { best = i; bestd = d; }\n"
+        "    }\n    if (best < 0) return -1;\n    *row",
+        "        if (best < 0 || d <= bestd) { best = i; bestd = d; }\n"
+        "    }\n    if (best < 0) return -1;\n    *row",
+        [ig.test_snap_ignition_worked_cases]),
 }
 
 
