@@ -1039,6 +1039,155 @@ def run_surrogate_step(args):
     return 0
 
 
+RECOVER = ("recover_1024: 1024x1024 map (spatially varying wind), target "
+           "from the reference parameters (Table 2) at the centre ignition; "
+           "plain GA with populations 256 and 1024 x 16 replicates, the "
+           "surrogate-screened GA (1024 candidates, 256 simulated x 16) and "
+           "the variable-ignition GA (seven genes, population 1024 x 16), 50 "
+           "generations each; brute-force Monte Carlo for the time per "
+           "simulation")
+
+
+def _param_errors(hist, truth, frac=0.1):
+    """Per generation: the ensemble mean (best `frac` of that generation's
+    population) and each parameter's relative error against the truth."""
+    ens = []
+    for P, F in zip(hist.params, hist.fitness):
+        order = np.argsort(F, kind="stable")
+        ens.append(P[order[:max(1, int(len(F) * frac))]].mean(axis=0))
+    ens = np.asarray(ens)
+    k = len(truth)
+    return ens, np.abs(ens[:, :k] - truth) / np.abs(truth)
+
+
+def _time_to_recover(errs, seconds, tol=0.05):
+    """GA seconds (cumulative, through the generation) until every
+    parameter's relative error is within tol, and per parameter until it
+    first is; None where never."""
+    t = np.cumsum(seconds)
+    allok = np.nonzero((errs <= tol).all(axis=1))[0]
+    per = []
+    for j in range(errs.shape[1]):
+        hit = np.nonzero(errs[:, j] <= tol)[0]
+        per.append(None if hit.size == 0 else round(float(t[hit[0]]), 3))
+    return (None if allok.size == 0 else round(float(t[allok[0]]), 3)), per
+
+
+def _ga_report(hist, truth, sims_per_gen):
+    ens, errs = _param_errors(hist, truth)
+    rec, per = _time_to_recover(errs, hist.seconds)
+    return {"seconds": round(float(sum(hist.seconds)), 3),
+            "sims_per_generation": sims_per_gen,
+            "recovered_all_s": rec, "recovered_each_s": per,
+            "rel_error_by_gen": [[round(float(x), 4) for x in e] for e in errs],
+            "final_estimate": [round(float(x), 3) for x in ens[-1]],
+            "final_rel_error": [round(float(x), 4) for x in errs[-1]]}
+
+
+def run_recover(args):
+    """Parameter recovery against the reference parameters (Table 2 layout
+    per generation; Table 3 layout for the variable-ignition GA) and the GA
+    against Monte Carlo time per simulation (App. C, Fig. 11)."""
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_1701_03549_gb300 import calibrate, fire, surrogate
+
+    rank, world, local = parallel.env_rank()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    ctx = fire.Context(local, stream)
+    truth = np.asarray(synth.TRUTH_BETA, np.float64)
+    land = synth.preset_landscape("ignition_search_1024")
+    land2 = synth.preset_landscape("ga_generation_512")
+    m = ctx.landscape_upload(land)
+    m2 = ctx.landscape_upload(land2)
+    ign = synth.centre_ignition(land.veg)
+    tseed, tgt = _gpu_target(fire, m, ign, int((land.veg != 0).sum()))
+    m.target_upload(tgt)
+    gens = args.generations
+    clocks = Clocks(local)
+    plain = calibrate.run_ga(ctx, m, ign, pop=1024, reps=16, generations=gens,
+                             ga_seed=5, sim_seed=1 << 30)
+    plain256 = calibrate.run_ga(ctx, m, ign, pop=256, reps=16,
+                                generations=gens, ga_seed=5, sim_seed=1 << 32)
+    ga7 = calibrate.run_ga_ignition(ctx, m, tgt, land.veg != 0, pop=1024,
+                                    reps=16, generations=gens, ga_seed=5,
+                                    sim_seed=1 << 35)
+    # brute-force Monte Carlo (App. C): uniform parameters, one replicate
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    n_mc = 1024 * 16
+    calibrate.run_mc(ctx, m, ign, n=n_mc, reps=1, seed=11, sim_seed=1 << 36)
+    t_mc = time.perf_counter() - t0
+    # the surrogate-screened GA (trained on automaton runs of both maps)
+    sur = surrogate.Surrogate(ctx, S=256, max_batch=8, seed=1)
+    t0 = time.perf_counter()
+    data = [surrogate.make_dataset(ctx, m2, land2, sur, args.train_groups, 16,
+                                   21),
+            surrogate.make_dataset(ctx, m, land, sur, args.train_groups, 16,
+                                   22)]
+    sur.train(data, steps=args.train_steps, lr=2e-3, lr_final=1e-4, seed=3)
+    t_train = time.perf_counter() - t0
+    scr = surrogate.run_screened_ga(ctx, m, land, sur, ign, pop=256, pool=1024,
+                                    reps=16, generations=gens, ga_seed=5,
+                                    sim_seed=1 << 31)
+    ck = clocks.stop()
+    rp = _ga_report(plain, truth, 1024 * 16)
+    r256 = _ga_report(plain256, truth, 256 * 16)
+    rscr = _ga_report(scr, truth, 256 * 16)
+    rscr["surrogate_training_s"] = round(t_train, 3)
+    # variable ignition: Table 3 layout over the best tenth of every
+    # individual the GA evaluated
+    P7, F7 = ga7.all()
+    est = calibrate.ensemble(P7, F7, keep=max(1, len(F7) // 10))
+    ref7 = list(truth) + [float(ign[1]), float(ign[0])]
+    names = ["b0", "b1", "b2", "b3", "b4", "x", "y"]
+    table3 = {nm: {"reference": r, "mean": round(float(mu), 3),
+                   "sd": round(float(sd), 3)}
+              for nm, r, mu, sd in zip(names, ref7, est["mean"], est["sd"])}
+    ens7, err7 = _param_errors(ga7, truth)
+    ga_sim_s = sum(plain.seconds) / (gens * 1024 * 16)
+    line = {
+        "metric": "time-to-recover 5 params (each within 5% of the reference "
+                  "value), plain GA population 1024",
+        "value": rp["recovered_all_s"], "unit": "s", "n_gpus": world,
+        "steps": gens, "warmup": 0,
+        "ms_per_step": 1e3 * rp["seconds"] / gens, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "u32 (automaton) / bf16 (surrogate)", "data": "synthetic",
+        "config": {"workload": RECOVER, "target_seed": int(tseed),
+                   "reference": list(truth),
+                   "estimate": "mean of the best 10% of a generation"},
+        "plain_ga_1024": rp, "plain_ga_256": r256, "screened_ga": rscr,
+        "variable_ignition_ga": {
+            "seconds": round(float(sum(ga7.seconds)), 3),
+            "table3": table3, "ensemble_size": est["size"],
+            "final_rel_error_beta": [round(float(x), 4) for x in err7[-1]],
+            "final_xy": [round(float(x), 2) for x in ens7[-1][5:]],
+            "reference_xy": ref7[5:]},
+        "ga_vs_mc": {"ga_s_per_sim": ga_sim_s, "mc_s_per_sim": t_mc / n_mc,
+                     "ratio": ga_sim_s / (t_mc / n_mc),
+                     "note": "wall time per simulation of whole GA "
+                             "generations against one Monte Carlo batch of "
+                             f"{n_mc} uniform draws (App. C, Fig. 11: the "
+                             "paper's GA simulations took about half)"},
+        "cpu_baseline": None, "e2e": None, "gpu_launches": None,
+        "clocks": ck,
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    sur.net.free()
+    m.free()
+    m2.free()
+    ctx.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1048,11 +1197,13 @@ def main():
                     default="native")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload",
-                    choices=("uneven", "ga512", "surrogate", "surrogate_step"),
+                    choices=("uneven", "ga512", "recover", "surrogate",
+                             "surrogate_step"),
                     default="uneven",
                     help="uneven (default): nine fires 200x300..2000x1500, "
                          "100k simulations in one launch; ga512: one "
-                         "512x512 GA generation; surrogate: the "
+                         "512x512 GA generation; recover: parameter "
+                         "recovery of the GAs; surrogate: the "
                          "surrogate-screened GA against the plain GA; "
                          "surrogate_step: the surrogate network alone")
     ap.add_argument("--generations", type=int, default=50)
@@ -1070,6 +1221,8 @@ def main():
         return run_reference(args)
     if args.workload == "ga512":
         return run_ga512(args)
+    if args.workload == "recover":
+        return run_recover(args)
     if args.workload == "surrogate":
         return run_surrogate(args)
     if args.workload == "surrogate_step":

@@ -164,6 +164,16 @@ FIRE_API int fire_sync(fire_ctx *ctx);
 FIRE_API int fire_set_launch(fire_ctx *ctx, int warps_per_block, int blocks_per_sm,
                              int queue_entries, int state_mode);
 
+/* Test hook for the out-of-memory path: the growth of a context-owned
+ * device buffer (argument staging, simulation state and frontier lists,
+ * ordering scratch) that comes `after` growths from now fails as if
+ * cudaMalloc had failed: the buffer is released, the call returns
+ * FIRE_ENOMEM with a message naming the hook, and the context stays usable
+ * (the next call grows the buffer again).  after = -1 turns the hook off;
+ * it fires once.  Growths that find a large enough buffer do not count. */
+FIRE_API int fire_debug_fail_alloc(fire_ctx *ctx, int after);
+
+
 /* Upload the raster maps of one landscape (Sec. 2.1, Fig. 1) and precompute
  * the per-cell covariates of Eq. 1 on the device:
  *   veg[H*W]     uint8 vegetation code: 0 non-burnable, 1 forest, 2.. other
@@ -312,6 +322,25 @@ FIRE_API int ga_step(fire_ctx *ctx, int pop, int genes, const double *genes_in,
                      const double *fitness, int generation, int total_gens,
                      uint64_t ga_seed, const double *lo, const double *hi,
                      uint32_t flags, double *genes_out);
+
+/* Ignition cells of individuals that carry the ignition point as two genes
+ * (Sec. 3, Table 3 and Appendix B: with the ignition unknown the genetic
+ * algorithm searches seven parameters, the five of Eq. 1 plus x and y).  For
+ * individual i of genes_in[n*genes] (row-major), gene gx is x (the column)
+ * and gene gy is y (the row); each is clamped to the grid ([0, W - 1],
+ * [0, H - 1]; a NaN counts as 0) and rounded half up, and the fire starts
+ * from the burnable cell of the map's target burnt area nearest to that
+ * point (squared distance, ties to the lower row-major index), so every
+ * simulated fire starts inside the reference scar as the paper's do.  The
+ * cell is written to ignitions[i*reps + r] for r < reps (the layout
+ * fire_simulate_batch takes with each individual's reps replicates
+ * consecutive).  Host or device pointers (FIRE_DEVICE_PTRS); FIRE_EINVAL
+ * for bad sizes or indices, a map of another device, or a target without a
+ * burnable cell.  Synchronous. */
+FIRE_API int fire_snap_ignitions(fire_ctx *ctx, const fire_map *map, int n,
+                                 int genes, int gx, int gy,
+                                 const double *genes_in, int reps,
+                                 uint32_t flags, fire_cell *ignitions);
 
 /* Ignition-point search: the ignition treated as unknown and sought inside
  * the map's target scar (the paper's variable-ignition experiment).  A

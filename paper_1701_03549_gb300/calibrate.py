@@ -12,6 +12,8 @@ between torch and the library.
 """
 from __future__ import annotations
 
+import json
+import os
 import time
 from dataclasses import dataclass, field
 
@@ -28,6 +30,37 @@ class History:
 
     def all(self):
         return np.concatenate(self.params), np.concatenate(self.fitness)
+
+
+def _meta(kind_of_run, **kw):
+    return json.dumps(dict(run=kind_of_run, **{k: (float(v) if isinstance(
+        v, float) else v) for k, v in kw.items()}), sort_keys=True)
+
+
+def save_checkpoint(path: str, generation: int, genes: np.ndarray,
+                    hist: History, meta: str) -> None:
+    """State of a GA run after `generation` generations: the population of
+    the next generation, every finished generation's population, fitness and
+    wall time, and the run's settings (the keyed draws of the GA step and of
+    the simulations depend only on them and the generation index, so a
+    resumed run continues bit for bit).  Written to a temporary file and
+    renamed, so an interrupted write leaves the previous checkpoint."""
+    tmp = path + ".tmp.npz"
+    np.savez(tmp, generation=np.int64(generation), genes=np.asarray(genes),
+             params=np.asarray(hist.params), fitness=np.asarray(hist.fitness),
+             seconds=np.asarray(hist.seconds, np.float64), meta=np.str_(meta))
+    os.replace(tmp, path)
+
+
+def load_checkpoint(path: str, meta: str):
+    """(generation, genes, History) of a checkpoint written by a run with the
+    same settings; ValueError for one of another run."""
+    with np.load(path) as z:
+        if str(z["meta"]) != meta:
+            raise ValueError(f"checkpoint {path} belongs to another run")
+        hist = History(list(z["params"]), list(z["fitness"]),
+                       [float(x) for x in z["seconds"]])
+        return int(z["generation"]), np.array(z["genes"]), hist
 
 
 def sim_seeds(base: int, generation: int, pop: int, reps: int) -> np.ndarray:
@@ -101,26 +134,37 @@ def evaluate_sharded(ctx, m, params_dev, ignition, seeds, reps, kind, torch,
 
 def run_ga(ctx, m, ignition, pop=256, reps=16, generations=50,
            prior="gauss", lo=-30.0, hi=30.0, ga_seed=1, sim_seed=1,
-           kind=fire.FITNESS_JACCARD, init=None, rank=0, world=1):
+           kind=fire.FITNESS_JACCARD, init=None, rank=0, world=1,
+           checkpoint=None, stop_after=None):
     """The Appendix B genetic algorithm on map `m` (which holds the target).
     Returns the History of every generation's population and fitness.  With
     world > 1 (one process per GPU, default process group initialised) each
     generation's simulations are split over the ranks (evaluate_sharded);
-    the GA step is replicated, so every rank holds the same population."""
+    the GA step is replicated, so every rank holds the same population.
+    checkpoint: a path; the run saves its state there after every
+    generation and, when the file exists, resumes from it (bit-identical to
+    an uninterrupted run).  stop_after: return after that many generations
+    of this call (the history so far)."""
     import torch
 
     dev = torch.device("cuda", ctx.device)
     G = 5
+    meta = _meta("ga5", pop=pop, reps=reps, generations=generations,
+                 prior=prior, lo=lo, hi=hi, ga_seed=ga_seed,
+                 sim_seed=sim_seed, kind=int(kind), ignition=list(map(
+                     int, ignition)), custom_init=init is not None)
     if init is None:
         init = (synth.gauss_population(pop, ga_seed) if prior == "gauss"
                 else synth.uniform_population(pop, ga_seed, lo=lo, hi=hi))
     init = np.clip(np.asarray(init, np.float64), lo, hi)
+    start, hist = 0, History()
+    if checkpoint and os.path.exists(checkpoint):
+        start, init, hist = load_checkpoint(checkpoint, meta)
     genes = torch.tensor(init, dtype=torch.float64, device=dev)
     nxt = torch.empty_like(genes)
     tlo = torch.full((G,), float(lo), dtype=torch.float64, device=dev)
     thi = torch.full((G,), float(hi), dtype=torch.float64, device=dev)
-    hist = History()
-    for g in range(generations):
+    for g in range(start, generations):
         t0 = time.perf_counter()
         seeds = sim_seeds(sim_seed, g, pop, reps)
         if world > 1:
@@ -137,6 +181,98 @@ def run_ga(ctx, m, ignition, pop=256, reps=16, generations=50,
             ctx.sync()
             genes, nxt = nxt, genes
         hist.seconds.append(time.perf_counter() - t0)
+        if checkpoint and rank == 0:
+            save_checkpoint(checkpoint, g + 1, genes.cpu().numpy(), hist, meta)
+        if stop_after is not None and g + 1 - start >= stop_after:
+            break
+    return hist
+
+
+def evaluate_at(ctx, m, params_dev, ign_dev, seeds, reps, kind, torch):
+    """Mean fitness over `reps` replicates of each parameter vector, each
+    replicate starting from its own ignition (ign_dev: (P reps, 2) int32
+    device tensor, replicates of an individual consecutive)."""
+    dev = params_dev.device
+    P = params_dev.shape[0]
+    n = P * reps
+    p_sims = params_dev.repeat_interleave(reps, dim=0).contiguous()
+    s = torch.tensor(np.asarray(seeds, np.uint64).view(np.int64), device=dev)
+    out = torch.zeros((n, 6), dtype=torch.int32, device=dev)
+    fit = torch.zeros(n, dtype=torch.float64, device=dev)
+    mean = torch.zeros(P, dtype=torch.float64, device=dev)
+    torch.cuda.synchronize(dev)
+    m.simulate_batch(p_sims, ign_dev, s, device=True, out=out,
+                     longest_first=True)
+    fire.fire_fitness(ctx, out, kind, device=True, out=fit)
+    fire.fire_group_mean(ctx, fit, reps, device=True, out=mean)
+    ctx.sync()
+    return mean
+
+
+def initial_population_7(target, burnable, pop, seed, prior="gauss",
+                         lo=-30.0, hi=30.0):
+    """Seven-gene individuals (beta_0..beta_4, x, y): the parameters from the
+    Table 1 prior, the ignition point from the reference fire's burnt area
+    (Sec. 3: fires start from random points of the reference scar)."""
+    beta = (synth.gauss_population(pop, seed) if prior == "gauss"
+            else synth.uniform_population(pop, seed, lo=lo, hi=hi))
+    xy = synth.burnt_area_points(np.asarray(target) & np.asarray(burnable),
+                                 pop, seed)
+    return np.concatenate([np.clip(beta, lo, hi), xy], axis=1)
+
+
+def run_ga_ignition(ctx, m, target, burnable, pop=256, reps=16,
+                    generations=50, prior="gauss", lo=-30.0, hi=30.0,
+                    ga_seed=1, sim_seed=1, kind=fire.FITNESS_JACCARD,
+                    init=None, checkpoint=None, stop_after=None):
+    """The Appendix B genetic algorithm with the ignition point unknown
+    (Sec. 3, Table 3): seven genes, the five parameters of Eq. 1 and the
+    ignition's x (column) and y (row), bounded by the grid.  Each
+    generation maps every individual's (x, y) to the nearest burnable cell
+    of the target scar (fire_snap_ignitions), simulates it `reps` times
+    from there, scores the replicate-mean fitness and breeds the next
+    generation (ga_step, G = 7).  History.params holds (P, 7) arrays.
+    checkpoint and stop_after as in run_ga."""
+    import torch
+
+    dev = torch.device("cuda", ctx.device)
+    H, W = m.H, m.W
+    meta = _meta("ga7", pop=pop, reps=reps, generations=generations,
+                 prior=prior, lo=lo, hi=hi, ga_seed=ga_seed,
+                 sim_seed=sim_seed, kind=int(kind), shape=[H, W],
+                 custom_init=init is not None)
+    if init is None:
+        init = initial_population_7(target, burnable, pop, ga_seed, prior,
+                                    lo, hi)
+    start, hist = 0, History()
+    if checkpoint and os.path.exists(checkpoint):
+        start, init, hist = load_checkpoint(checkpoint, meta)
+    genes = torch.tensor(np.asarray(init, np.float64), device=dev)
+    nxt = torch.empty_like(genes)
+    tlo = torch.tensor([lo] * 5 + [0.0, 0.0], dtype=torch.float64, device=dev)
+    thi = torch.tensor([hi] * 5 + [W - 1.0, H - 1.0], dtype=torch.float64,
+                       device=dev)
+    ign = torch.empty((pop * reps, 2), dtype=torch.int32, device=dev)
+    for g in range(start, generations):
+        t0 = time.perf_counter()
+        torch.cuda.synchronize(dev)
+        fire.fire_snap_ignitions(ctx, m, genes, 5, 6, reps, device=True,
+                                 out=ign)
+        f = evaluate_at(ctx, m, genes[:, :5].contiguous(), ign,
+                        sim_seeds(sim_seed, g, pop, reps), reps, kind, torch)
+        hist.params.append(genes.cpu().numpy())
+        hist.fitness.append(f.cpu().numpy())
+        if g + 1 < generations:
+            torch.cuda.synchronize(dev)
+            fire.ga_step(ctx, genes, f, g, generations, ga_seed, tlo, thi,
+                         device=True, out=nxt)
+            ctx.sync()
+            genes, nxt = nxt, genes
+        hist.seconds.append(time.perf_counter() - t0)
+        if checkpoint:
+            save_checkpoint(checkpoint, g + 1, genes.cpu().numpy(), hist, meta)
+        if stop_after is not None and g + 1 - start >= stop_after:
+            break
     return hist
 
 

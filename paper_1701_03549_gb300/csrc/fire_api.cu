@@ -51,6 +51,9 @@ int grow_device(fire_ctx *ctx, void **buf, size_t *cap, size_t need,
     *buf = nullptr;
     *cap = 0;
     size_t n = need + need / 4 + 256;
+    if (ctx->fail_alloc_after >= 0 && ctx->fail_alloc_after-- == 0)
+        return set_err(ctx, FIRE_ENOMEM, "cudaMalloc(%zu) for %s: failure "
+                       "forced by fire_debug_fail_alloc", n, what);
     cudaError_t e = cudaMalloc(buf, n);
     if (e != cudaSuccess) {
         *buf = nullptr;
@@ -209,6 +212,7 @@ const char *fire_last_error(const fire_ctx *ctx)
 
 int fire_sync(fire_ctx *ctx)
 {
+    FIRE_NVTX("fire_sync");
     if (!ctx) return FIRE_EINVAL;
     int rc = ensure_device(ctx);
     if (rc) return rc;
@@ -228,6 +232,13 @@ int fire_sync(fire_ctx *ctx)
     if (na)
         return set_err(ctx, FIRE_ETIMEOUT,
                        "a bounded device wait ran out (no-alloc call)");
+    return FIRE_OK;
+}
+
+int fire_debug_fail_alloc(fire_ctx *ctx, int after)
+{
+    if (!ctx || after < -1) return FIRE_EINVAL;
+    ctx->fail_alloc_after = after;
     return FIRE_OK;
 }
 
@@ -254,6 +265,7 @@ int fire_maps_upload(fire_ctx *ctx, int H, int W, float cell_m,
                      const float *aspect, const float *wind, uint32_t flags,
                      fire_map **out)
 {
+    FIRE_NVTX("fire_maps_upload");
     if (!ctx || !out) return FIRE_EINVAL;
     *out = nullptr;
     if (H <= 0 || W <= 0)
@@ -377,6 +389,7 @@ int fire_map_shape(const fire_map *m, int *H, int *W)
 int fire_target_upload(fire_ctx *ctx, fire_map *m, const uint8_t *burnt,
                        uint32_t flags)
 {
+    FIRE_NVTX("fire_target_upload");
     if (!ctx || !valid_map(m) || !burnt) return set_err(ctx, FIRE_EINVAL,
                                                          "bad target arguments");
     int rc = ensure_device(ctx);
@@ -474,6 +487,7 @@ int fire_simulate_batch(fire_ctx *ctx, const fire_map *m, int n,
                         const uint64_t *seeds, uint32_t max_steps,
                         uint32_t flags, fire_result *out, int32_t *burn_step)
 {
+    FIRE_NVTX("fire_simulate_batch");
     if (!ctx) return FIRE_EINVAL;
     if (!valid_map(m)) return set_err(ctx, FIRE_EINVAL, "invalid map");
     if (m->ctx->device != ctx->device)
@@ -571,6 +585,7 @@ int fire_simulate_batch(fire_ctx *ctx, const fire_map *m, int n,
 int fire_fitness(fire_ctx *ctx, const fire_result *results, int n, int kind,
                  uint32_t flags, double *out)
 {
+    FIRE_NVTX("fire_fitness");
     if (!ctx) return FIRE_EINVAL;
     if (n < 0 || (kind != 0 && kind != 1))
         return set_err(ctx, FIRE_EINVAL, "bad fitness arguments");
@@ -626,6 +641,7 @@ int with_beta(fire_ctx *ctx, const fire_params *params, uint32_t flags,
 int fire_thresholds(fire_ctx *ctx, const fire_map *m, const fire_params *params,
                     uint32_t flags, int64_t *out)
 {
+    FIRE_NVTX("fire_thresholds");
     if (!ctx) return FIRE_EINVAL;
     if (!valid_map(m) || !params || !out)
         return set_err(ctx, FIRE_EINVAL, "bad thresholds arguments");
@@ -654,6 +670,7 @@ int fire_thresholds(fire_ctx *ctx, const fire_map *m, const fire_params *params,
 int fire_probabilities(fire_ctx *ctx, const fire_map *m, const fire_params *params,
                        uint32_t flags, float *p32, double *p64)
 {
+    FIRE_NVTX("fire_probabilities");
     if (!ctx) return FIRE_EINVAL;
     if (!valid_map(m) || !params || (!p32 && !p64))
         return set_err(ctx, FIRE_EINVAL, "bad probabilities arguments");
@@ -687,6 +704,7 @@ int fire_map_features(fire_ctx *ctx, const fire_map *m, uint32_t flags,
                       float *psi, float *sig, float *cos_wind, float *sin_wind,
                       uint16_t *cell_flags)
 {
+    FIRE_NVTX("fire_map_features");
     if (!ctx) return FIRE_EINVAL;
     if (!valid_map(m)) return set_err(ctx, FIRE_EINVAL, "invalid map");
     int rc = ensure_device(ctx);
@@ -720,6 +738,7 @@ int fire_map_features(fire_ctx *ctx, const fire_map *m, uint32_t flags,
 int fire_screen_selftest(fire_ctx *ctx, uint64_t n, uint64_t seed,
                          uint64_t counts[3], double max_err_ratio[1])
 {
+    FIRE_NVTX("fire_screen_selftest");
     if (!ctx) return FIRE_EINVAL;
     if (!counts || !max_err_ratio) return set_err(ctx, FIRE_EINVAL, "NULL output");
     int rc = ensure_device(ctx);
@@ -744,6 +763,7 @@ int fire_screen_selftest(fire_ctx *ctx, uint64_t n, uint64_t seed,
 int fire_philox_blocks(fire_ctx *ctx, uint64_t n, const uint32_t ctr[4],
                        const uint32_t key[2], uint32_t flags, uint32_t *out)
 {
+    FIRE_NVTX("fire_philox_blocks");
     if (!ctx) return FIRE_EINVAL;
     if (!ctr || !key || !out) return set_err(ctx, FIRE_EINVAL, "NULL argument");
     if (n == 0) return FIRE_OK;

@@ -14,6 +14,7 @@ extern "C" int fire_simulate_burnout(fire_ctx *ctx, const fire_map *m, int n,
                                      uint32_t flags, fire_result *out,
                                      int32_t *burn_step)
 {
+    FIRE_NVTX("fire_simulate_burnout");
     if (!ctx) return FIRE_EINVAL;
     if (!valid_map(m)) return set_err(ctx, FIRE_EINVAL, "invalid map");
     if (n < 0) return set_err(ctx, FIRE_EINVAL, "n = %d", n);

@@ -154,6 +154,7 @@ int ga_step(fire_ctx *ctx, int pop, int genes, const double *genes_in,
             uint64_t ga_seed, const double *lo, const double *hi,
             uint32_t flags, double *genes_out)
 {
+    FIRE_NVTX("ga_step");
     if (!ctx) return FIRE_EINVAL;
     if (pop <= 0 || genes <= 0 || total_gens <= 0 || generation < 0 ||
         !genes_in || !fitness || !lo || !hi || !genes_out)
@@ -224,6 +225,7 @@ int ga_step(fire_ctx *ctx, int pop, int genes, const double *genes_in,
 int fire_group_mean(fire_ctx *ctx, const double *values, int groups,
                     int per_group, uint32_t flags, double *out)
 {
+    FIRE_NVTX("fire_group_mean");
     if (!ctx) return FIRE_EINVAL;
     if (groups < 0 || per_group <= 0)
         return set_err(ctx, FIRE_EINVAL, "bad group-mean arguments");

@@ -37,17 +37,12 @@ __global__ void k_target_bbox(MapDev m, int *bbox)
     }
 }
 
-// One block per lattice point: nearest burnable burnt cell.
-__global__ void k_snap(MapDev m, const int *__restrict__ bbox, int LH, int LW,
-                       int32_t *__restrict__ cells, int *__restrict__ fail)
+// Row-major index of the burnable burnt cell nearest to (R, C): least
+// (squared distance, index), one block cooperating (all threads call it);
+// 0xffffffff when the target has no burnable cell.  The distance can exceed
+// 32 bits on wide maps, so the pair is compared field by field.
+__device__ uint32_t block_nearest(const MapDev &m, long long R, long long C)
 {
-    const int cidx = blockIdx.x;
-    const int a = cidx / LW, b = cidx - a * LW;
-    const int r0 = bbox[0], r1 = bbox[1], c0 = bbox[2], c1 = bbox[3];
-    const long long R = r0 + ((2LL * a + 1) * (r1 - r0 + 1)) / (2LL * LH);
-    const long long C = c0 + ((2LL * b + 1) * (c1 - c0 + 1)) / (2LL * LW);
-    // nearest = least (squared distance, row-major index); the distance can
-    // exceed 32 bits on wide maps, so the pair is compared field by field
     unsigned long long bd = ~0ull;
     uint32_t bi = 0xffffffffu;
     const int nw = m.ntiles * 32;
@@ -86,16 +81,55 @@ __global__ void k_snap(MapDev m, const int *__restrict__ bbox, int LH, int LW,
         }
         __syncthreads();
     }
+    const uint32_t best = rd[0] == ~0ull ? 0xffffffffu : ri[0];
+    __syncthreads();   // the arrays may be reused by the next call
+    return best;
+}
+
+// One block (256 threads) per lattice point: nearest burnable burnt cell.
+__global__ void k_snap(MapDev m, const int *__restrict__ bbox, int LH, int LW,
+                       int32_t *__restrict__ cells, int *__restrict__ fail)
+{
+    const int cidx = blockIdx.x;
+    const int a = cidx / LW, b = cidx - a * LW;
+    const int r0 = bbox[0], r1 = bbox[1], c0 = bbox[2], c1 = bbox[3];
+    const long long R = r0 + ((2LL * a + 1) * (r1 - r0 + 1)) / (2LL * LH);
+    const long long C = c0 + ((2LL * b + 1) * (c1 - c0 + 1)) / (2LL * LW);
+    const uint32_t best = block_nearest(m, R, C);
     if (threadIdx.x == 0) {
-        if (rd[0] == ~0ull) {
+        if (best == 0xffffffffu) {
             atomicOr(fail, 1);
             cells[2 * cidx] = cells[2 * cidx + 1] = 0;
         } else {
-            const long long cell = (long long)ri[0];
-            cells[2 * cidx] = (int32_t)(cell / m.W);
-            cells[2 * cidx + 1] = (int32_t)(cell % m.W);
+            cells[2 * cidx] = (int32_t)(best / (uint32_t)m.W);
+            cells[2 * cidx + 1] = (int32_t)(best % (uint32_t)m.W);
         }
     }
+}
+
+// A coordinate gene clamped to [0, hi] (a NaN counts as 0) and rounded half
+// up.
+__device__ __forceinline__ long long gene_coord(double v, int hi)
+{
+    const double c = v >= 0.0 ? (v > (double)hi ? (double)hi : v) : 0.0;
+    return (long long)floor(__dadd_rn(c, 0.5));
+}
+
+// One block (256 threads) per individual: the ignition cell of its x
+// (column) and y (row) genes, written to its reps simulations.
+__global__ void k_snap_genes(MapDev m, int G, int gx, int gy,
+                             const double *__restrict__ genes, int reps,
+                             fire_cell *__restrict__ ign, int *__restrict__ fail)
+{
+    const long long j = blockIdx.x;
+    const long long C = gene_coord(genes[j * G + gx], m.W - 1);
+    const long long R = gene_coord(genes[j * G + gy], m.H - 1);
+    const uint32_t best = block_nearest(m, R, C);
+    fire_cell cell;
+    cell.row = best == 0xffffffffu ? 0 : (int32_t)(best / (uint32_t)m.W);
+    cell.col = best == 0xffffffffu ? 0 : (int32_t)(best % (uint32_t)m.W);
+    if (best == 0xffffffffu && threadIdx.x == 0) atomicOr(fail, 1);
+    for (int r = threadIdx.x; r < reps; r += blockDim.x) ign[j * reps + r] = cell;
 }
 
 __global__ void k_ign_batch(int L, int reps, const int32_t *__restrict__ cells,
@@ -166,6 +200,7 @@ extern "C" int ignition_search(fire_ctx *ctx, const fire_map *map,
                                uint32_t flags, double *fitness_map,
                                int32_t *cells, double xy_mean_sd[4])
 {
+    FIRE_NVTX("ignition_search");
     if (!ctx) return FIRE_EINVAL;
     if (!valid_map(map) || !params || lat_h <= 0 || lat_w <= 0 || reps <= 0 ||
         (kind != 0 && kind != 1) || !fitness_map || !xy_mean_sd)
@@ -235,4 +270,52 @@ extern "C" int ignition_search(fire_ctx *ctx, const fire_map *map,
         CUDA_TRY(ctx, cudaMemcpyAsync(cells, dcells, (size_t)L * 8, dk, st), "cells");
     CUDA_TRY(ctx, cudaMemcpyAsync(xy_mean_sd, dxy, 32, dk, st), "estimate");
     return fire_sync(ctx);
+}
+
+extern "C" int fire_snap_ignitions(fire_ctx *ctx, const fire_map *map, int n,
+                                   int genes, int gx, int gy,
+                                   const double *genes_in, int reps,
+                                   uint32_t flags, fire_cell *ignitions)
+{
+    FIRE_NVTX("fire_snap_ignitions");
+    if (!ctx) return FIRE_EINVAL;
+    if (!valid_map(map) || n < 0 || genes < 1 || gx < 0 || gx >= genes ||
+        gy < 0 || gy >= genes || reps < 1)
+        return set_err(ctx, FIRE_EINVAL, "bad fire_snap_ignitions arguments");
+    if (map->ctx->device != ctx->device)
+        return set_err(ctx, FIRE_EINVAL, "the map was uploaded on another device");
+    if (n == 0) return FIRE_OK;
+    if (!genes_in || !ignitions) return set_err(ctx, FIRE_EINVAL, "NULL argument");
+    if ((long long)n * reps > 0x7fffffffll)
+        return set_err(ctx, FIRE_EINVAL, "individuals x replicates too large");
+    int rc = ensure_device(ctx);
+    if (rc) return rc;
+    const bool dev = flags & FIRE_DEVICE_PTRS;
+    const size_t bg = round16((size_t)n * genes * 8);
+    const size_t bi = round16((size_t)n * reps * sizeof(fire_cell));
+    rc = grow_device(ctx, &ctx->staging, &ctx->staging_bytes,
+                     16 + (dev ? 0 : bg + bi), "ignition genes");
+    if (rc) return rc;
+    char *base = (char *)ctx->staging;
+    int *dfail = (int *)base;
+    const double *dgenes = genes_in;
+    fire_cell *dign = ignitions;
+    cudaStream_t st = ctx->stream;
+    if (!dev) {
+        dgenes = (const double *)(base + 16);
+        dign = (fire_cell *)(base + 16 + bg);
+        CUDA_TRY(ctx, cudaMemcpyAsync((void *)dgenes, genes_in, (size_t)n * genes * 8,
+                                      cudaMemcpyHostToDevice, st), "genes H2D");
+    }
+    CUDA_TRY(ctx, cudaMemsetAsync(dfail, 0, 4, st), "fail init");
+    k_snap_genes<<<n, 256, 0, st>>>(map->dev, genes, gx, gy, dgenes, reps, dign, dfail);
+    CUDA_TRY(ctx, cudaGetLastError(), "snap kernel");
+    if (!dev)
+        CUDA_TRY(ctx, cudaMemcpyAsync(ignitions, dign, (size_t)n * reps * sizeof(fire_cell),
+                                      cudaMemcpyDeviceToHost, st), "ignitions D2H");
+    int hfail = 0;
+    CUDA_TRY(ctx, cudaMemcpyAsync(&hfail, dfail, 4, cudaMemcpyDeviceToHost, st), "fail D2H");
+    CUDA_TRY(ctx, cudaStreamSynchronize(st), "snap sync");
+    if (hfail) return set_err(ctx, FIRE_EINVAL, "the target has no burnable burnt cell");
+    return FIRE_OK;
 }

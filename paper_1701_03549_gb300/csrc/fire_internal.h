@@ -8,6 +8,7 @@
 #include <vector>
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "fire.h"
 #include "fire_device.cuh"
@@ -212,6 +213,7 @@ struct fire_ctx {
     std::vector<TuneEntry> tuned;    // autotuned launch shapes
     std::vector<GraphEntry> graphs;  // captured calls
     unsigned epoch = 0;              // bumped when a device buffer moves
+    int fail_alloc_after = -1;       // test hook: fail that growth (-1: off)
 };
 
 struct fire_map {
@@ -254,6 +256,17 @@ int launch_batch(fire_ctx *ctx, const fire_map *m, int n,
                  const uint64_t *dseeds, uint32_t max_steps, uint32_t flags,
                  fire_result *dout, int32_t *dsteps, uint32_t *dbits);
 }  // namespace fire
+
+// NVTX range named after the C-ABI entry point, open for the call's
+// duration (profilers such as Nsight show the library's calls on the host
+// timeline; without a tool attached each range costs a no-op call).
+struct NvtxScope {
+    explicit NvtxScope(const char *name) { nvtxRangePushA(name); }
+    ~NvtxScope() { nvtxRangePop(); }
+    NvtxScope(const NvtxScope &) = delete;
+    NvtxScope &operator=(const NvtxScope &) = delete;
+};
+#define FIRE_NVTX(name) NvtxScope fire_nvtx_scope_(name)
 
 #define CUDA_TRY(ctx, expr, what)                                   \
     do {                                                            \

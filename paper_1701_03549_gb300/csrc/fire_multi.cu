@@ -66,6 +66,7 @@ int fire_simulate_multi(fire_ctx *ctx, int nmaps, const fire_map *const *maps,
                         const uint64_t *seeds, uint32_t max_steps,
                         uint32_t flags, fire_result *out)
 {
+    FIRE_NVTX("fire_simulate_multi");
     if (!ctx) return FIRE_EINVAL;
     if (nmaps <= 0 || !maps) return set_err(ctx, FIRE_EINVAL, "no maps");
     if (n < 0) return set_err(ctx, FIRE_EINVAL, "n = %d", n);
@@ -238,6 +239,7 @@ int fire_autotune(fire_ctx *ctx, int nmaps, const fire_map *const *maps,
                   const fire_cell *ignitions, const uint64_t *seeds,
                   uint32_t flags, fire_launch *best)
 {
+    FIRE_NVTX("fire_autotune");
     if (!ctx) return FIRE_EINVAL;
     if (!best || n <= 0 || nmaps <= 0 || !maps)
         return set_err(ctx, FIRE_EINVAL, "bad autotune arguments");

@@ -700,6 +700,7 @@ int fire_net_get(fire_ctx *ctx, const fire_net *net, int which, uint32_t flags,
 int fire_net_forward(fire_ctx *ctx, fire_net *net, int n, const uint16_t *x,
                      uint32_t flags, float *prob)
 {
+    FIRE_NVTX("fire_net_forward");
     if (!ctx) return FIRE_EINVAL;
     if (!net || n < 0 || !(flags & FIRE_DEVICE_PTRS) || (n && (!x || !prob)) ||
         ((uintptr_t)x & 15))
@@ -725,6 +726,7 @@ int fire_net_forward(fire_ctx *ctx, fire_net *net, int n, const uint16_t *x,
 int fire_net_backward(fire_ctx *ctx, fire_net *net, int n, const uint16_t *x,
                       const float *target, uint32_t flags, double *loss)
 {
+    FIRE_NVTX("fire_net_backward");
     if (!ctx) return FIRE_EINVAL;
     if (!net || n < 1 || n > net->max_batch || !x || !target ||
         !(flags & FIRE_DEVICE_PTRS) || ((uintptr_t)x & 15))
@@ -788,6 +790,7 @@ int fire_net_backward(fire_ctx *ctx, fire_net *net, int n, const uint16_t *x,
 
 int fire_net_adam(fire_ctx *ctx, fire_net *net, float lr, uint32_t flags)
 {
+    FIRE_NVTX("fire_net_adam");
     if (!ctx) return FIRE_EINVAL;
     if (!net || !(lr >= 0.0f)) return net_err(ctx, "fire_net_adam: bad arguments");
     int rc = ensure_device(ctx);
@@ -826,6 +829,7 @@ int fire_net_planes(fire_ctx *ctx, int H, int W, int S, const uint8_t *veg,
                     const float *slope, const float *aspect, const float *wind,
                     uint32_t flags, float *planes)
 {
+    FIRE_NVTX("fire_net_planes");
     if (!ctx) return FIRE_EINVAL;
     if (S < 1 || H < S || W < S || H % S || W % S || !veg || !slope || !aspect ||
         !wind || !planes || !(flags & FIRE_DEVICE_PTRS))
@@ -843,6 +847,7 @@ int fire_net_inputs(fire_ctx *ctx, int S, int H, int W, int n, const float *plan
                     const fire_params *params, const fire_cell *ign, uint32_t flags,
                     uint16_t *x)
 {
+    FIRE_NVTX("fire_net_inputs");
     if (!ctx) return FIRE_EINVAL;
     if (S < 1 || H < S || W < S || H % S || W % S || n < 0 ||
         (n && (!planes || !params || !ign || !x)) || !(flags & FIRE_DEVICE_PTRS) ||
@@ -864,6 +869,7 @@ int fire_net_labels(fire_ctx *ctx, const fire_map *map, int S, int groups, int r
                     uint32_t max_steps, uint32_t flags, float *labels,
                     fire_result *results)
 {
+    FIRE_NVTX("fire_net_labels");
     if (!ctx) return FIRE_EINVAL;
     if (!valid_map(map) || S < 1 || groups < 0 || reps < 1 ||
         map->dev.H % S || map->dev.W % S || !(flags & FIRE_DEVICE_PTRS) ||
@@ -935,6 +941,7 @@ int fire_net_screen(fire_ctx *ctx, int S, int n, const float *prob,
                     const float *target_frac, double cells_per_coarse, int kind,
                     int keep, uint32_t flags, double *pred, int32_t *keep_idx)
 {
+    FIRE_NVTX("fire_net_screen");
     if (!ctx) return FIRE_EINVAL;
     if (S < 1 || n < 0 || keep < 0 || keep > n || (kind != 0 && kind != 1) ||
         !(cells_per_coarse > 0) || !(flags & FIRE_DEVICE_PTRS) ||

@@ -72,6 +72,7 @@ extern "C" int fire_tc_gemm(fire_ctx *ctx, int M, int N, int K,
                             const uint16_t *A, const uint16_t *B, int ksplit,
                             uint32_t flags, float *C)
 {
+    FIRE_NVTX("fire_tc_gemm");
     if (!ctx) return FIRE_EINVAL;
     const bool amn = flags & FIRE_TC_A_MN, bmn = flags & FIRE_TC_B_MN;
     if (!(flags & FIRE_DEVICE_PTRS) || !A || !B || !C || M <= 0 || N <= 0 ||

@@ -59,12 +59,14 @@ RESULT_DTYPE = np.dtype([(f, "<u4") for f in RESULT_FIELDS])
 
 EXPORTED = (
     "fire_create", "fire_destroy", "fire_last_error", "fire_sync",
-    "fire_set_launch", "fire_maps_upload", "fire_map_free", "fire_map_shape",
+    "fire_set_launch", "fire_debug_fail_alloc",
+    "fire_maps_upload", "fire_map_free", "fire_map_shape",
     "fire_target_upload", "fire_simulate_batch", "fire_fitness",
     "fire_thresholds", "fire_probabilities", "fire_map_features",
     "fire_screen_selftest", "fire_philox_blocks",
     "fire_simulate_batch_noalloc", "fire_simulate_multi", "fire_autotune",
-    "ga_step", "fire_group_mean", "ignition_search", "fire_tc_gemm",
+    "ga_step", "fire_group_mean", "ignition_search", "fire_snap_ignitions",
+    "fire_tc_gemm",
     "fire_net_param_count", "fire_net_create", "fire_net_free",
     "fire_net_set_params", "fire_net_get", "fire_net_forward",
     "fire_net_backward", "fire_net_adam", "fire_net_buffer",
@@ -100,6 +102,7 @@ def load(path: str = LIB_PATH):
         "fire_last_error": (C.c_char_p, [vp]),
         "fire_sync": (i32, [vp]),
         "fire_set_launch": (i32, [vp, i32, i32, i32, i32]),
+        "fire_debug_fail_alloc": (i32, [vp, i32]),
         "fire_maps_upload": (i32, [vp, i32, i32, C.c_float, vp, vp, vp, vp, vp,
                                    u32, C.POINTER(vp)]),
         "fire_map_free": (None, [vp]),
@@ -121,6 +124,8 @@ def load(path: str = LIB_PATH):
         "ga_step": (i32, [vp, i32, i32, vp, vp, i32, i32, u64, vp, vp, u32,
                           vp]),
         "fire_group_mean": (i32, [vp, vp, i32, i32, u32, vp]),
+        "fire_snap_ignitions": (i32, [vp, vp, i32, i32, i32, i32, vp, i32,
+                                      u32, vp]),
         "ignition_search": (i32, [vp, vp, vp, i32, i32, i32, u64, i32,
                                   C.c_double, u32, vp, vp, vp]),
         "fire_tc_gemm": (i32, [vp, i32, i32, i32, vp, vp, i32, u32, vp]),
@@ -281,6 +286,11 @@ class Context:
 
     def sync(self):
         return self.check(self.lib.fire_sync(self.h))
+
+    def debug_fail_alloc(self, after: int = 0):
+        """fire_debug_fail_alloc: make the buffer growth `after` growths from
+        now fail with FIRE_ENOMEM (-1: off)."""
+        return self.check(self.lib.fire_debug_fail_alloc(self.h, int(after)))
 
     def set_launch(self, warps_per_block: int = 0, blocks_per_sm: int = 0,
                    queue_entries: int = 0, state_mode: int = 0):
@@ -606,6 +616,33 @@ def ignition_search(ctx: Context, m: Map, beta, lat_h, lat_w, reps, seed,
                                       int(kind), float(cutoff), 0, _ptr(fm),
                                       _ptr(cells), _ptr(xy)))
     return fm, cells, xy
+
+
+def fire_snap_ignitions(ctx: Context, m: Map, genes, gx: int, gy: int,
+                        reps: int = 1, device=False, out=None):
+    """Ignition cells of a population whose genes gx (x = column) and gy
+    (y = row) hold the ignition point: the burnable target cell nearest to
+    each clamped, rounded point, repeated `reps` times per individual.
+    Host mode: numpy genes (n, G); returns (n * reps, 2) int32 (row, col).
+    Device mode: torch CUDA float64 genes (n, G) and a preallocated int32
+    `out` (n * reps, 2); returns `out`."""
+    lib = ctx.lib
+    if device:
+        n = int(genes.shape[0])
+        G = int(genes.shape[1]) if genes.dim() == 2 else 0
+        ctx.check(lib.fire_snap_ignitions(
+            ctx.h, m.h, n, G, int(gx), int(gy),
+            _dev(ctx, genes, "genes", _F64, n * G), int(reps),
+            FIRE_DEVICE_PTRS, _dev(ctx, out, "out", _I32, 2 * n * int(reps))))
+        return out
+    g = _host(genes, np.float64)
+    if g.ndim != 2:
+        raise FireError(FIRE_EINVAL, "genes: expected (n, G)")
+    n, G = g.shape
+    o = np.zeros((n * int(reps), 2), np.int32)
+    ctx.check(lib.fire_snap_ignitions(ctx.h, m.h, n, G, int(gx), int(gy),
+                                      _ptr(g), int(reps), 0, _ptr(o)))
+    return o
 
 
 def fire_group_mean(ctx: Context, values, per_group, device=False, out=None):

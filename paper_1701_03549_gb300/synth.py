@@ -216,6 +216,19 @@ def uniform_population(n: int, seed: int, genes: int = 5,
     return rng.uniform(lo, hi, size=(n, genes)).astype(np.float64)
 
 
+def burnt_area_points(area: np.ndarray, n: int, seed: int) -> np.ndarray:
+    """n points (x = column, y = row) drawn uniformly from the cells set in
+    `area` (the initial ignition genes of the variable-ignition GA: the
+    paper starts those fires from random points of the reference fire's
+    burnt area), as float64 (n, 2)."""
+    rows, cols = np.nonzero(np.asarray(area))
+    if rows.size == 0:
+        raise ValueError("empty area")
+    rng = np.random.default_rng([seed, 0x16A1])
+    k = rng.integers(0, rows.size, n)
+    return np.stack([cols[k], rows[k]], axis=1).astype(np.float64)
+
+
 def replicate_seeds(n: int, first: int = 1) -> np.ndarray:
     return np.arange(first, first + n, dtype=np.uint64)
 

@@ -122,3 +122,51 @@ def test_simulation_guards_refuse_before_any_cuda_call(libpath, tmp_path):
     msg = ctypes.create_string_buffer(512)
     rc = lib.abi_guard_cases(msg, 512)
     assert rc == 0, msg.value.decode()
+
+
+def _guards_lib(libpath, tmp_path):
+    from paper_1701_03549_gb300 import build
+
+    src = os.path.join(ROOT, "tests", "abi_guards_host.cu")
+    so = str(tmp_path / "libabi_guards.so")
+    libdir = os.path.dirname(libpath)
+    subprocess.run([build._nvcc(), *build.ARCH, "-std=c++17", "-O1",
+                    "-Xcompiler", "-fPIC", "-shared", "-I", build.INCLUDE,
+                    "-I", build.CSRC, src, "-o", so, "-L" + libdir, "-lfire",
+                    "-Xlinker", "-rpath=" + libdir],
+                   check=True, capture_output=True)
+    return so
+
+
+def test_entry_points_open_nvtx_ranges(libpath, tmp_path):
+    """Each C-ABI compute call opens an NVTX range named after itself and
+    closes it on every return path: a minimal NVTX tool
+    (tests/nvtx_capture.c, loaded through NVTX_INJECTION64_PATH) records the
+    ranges of calls the argument guards refuse, in a child process without a
+    GPU."""
+    import sys
+
+    from paper_1701_03549_gb300 import build
+
+    guards = _guards_lib(libpath, tmp_path)
+    tool = str(tmp_path / "libnvtx_capture.so")
+    cuda_inc = os.path.join(os.path.dirname(os.path.dirname(build._nvcc())),
+                            "include")
+    subprocess.run(["gcc", "-O1", "-fPIC", "-shared", "-I", cuda_inc,
+                    os.path.join(ROOT, "tests", "nvtx_capture.c"), "-o", tool],
+                   check=True)
+    child = (
+        "import ctypes\n"
+        f"tool = ctypes.CDLL({tool!r})\n"
+        f"g = ctypes.CDLL({guards!r})\n"
+        "msg = ctypes.create_string_buffer(512)\n"
+        "assert g.abi_guard_cases(msg, 512) == 0, msg.value\n"
+        "tool.nvtx_capture_names.restype = ctypes.c_char_p\n"
+        "print(tool.nvtx_capture_names().decode().replace(chr(10), ' '))\n"
+        "print(tool.nvtx_capture_depth())\n")
+    env = dict(os.environ, NVTX_INJECTION64_PATH=tool)
+    out = subprocess.run([sys.executable, "-c", child], env=env,
+                         capture_output=True, text=True, check=True).stdout
+    names, depth = out.strip().split("\n")
+    assert "fire_simulate_batch" in names.split(), names
+    assert int(depth) == 0

@@ -123,3 +123,22 @@ def test_stratified_sample_of_the_uneven_batch():
     for j in range(9):
         pos = np.sort(idx[mos[idx] == j]) - starts[j]
         assert pos[0] == 0 and np.all(np.diff(pos) >= counts[j] // 16)
+
+
+def test_recovery_errors_and_times():
+    """The recovery report: ensemble = mean of the best tenth of a
+    generation; a parameter is recovered once its relative error is within
+    5 %; the time is the GA's cumulative seconds through that generation."""
+    from paper_1701_03549_gb300 import calibrate
+
+    truth = np.array([-5.0, -10.0, 5.0, 18.1, -5.0])
+    P = np.tile(truth, (20, 1))
+    P[:2] *= 1.2                           # the two best are 20 % off
+    h = calibrate.History([P, np.tile(truth, (20, 1))],
+                          [np.arange(20.0), np.arange(20.0)], [1.5, 2.0])
+    ens, errs = bench._param_errors(h, truth)
+    assert np.allclose(errs[0], 0.2) and np.allclose(errs[1], 0.0)
+    rec, per = bench._time_to_recover(errs, h.seconds)
+    assert rec == 3.5 and per == [3.5] * 5
+    rec, per = bench._time_to_recover(errs[:1], h.seconds[:1])
+    assert rec is None and per == [None] * 5

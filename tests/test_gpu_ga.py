@@ -157,3 +157,119 @@ def test_sharded_evaluation_on_one_rank_equals_evaluate(env):
                                    fire.FITNESS_JACCARD, torch, 0, 1)
     assert torch.equal(a, b)
     m.free()
+
+
+def test_snap_ignitions_match_the_oracle(env):
+    """Ignition cells of coordinate genes against the oracle's nearest-cell
+    rule on a map with non-burnable cells inside the scar: points inside,
+    outside (clamped), exactly half-way between cells, NaN, and both
+    host and device buffers; reps copies per individual."""
+    torch, fire, oracle, ctx = env
+    land = synth.landscape(70, 90, seed=12, wind_seed=12)
+    F = oracle.Features(land)
+    ign = synth.centre_ignition(land.veg)
+    _, tb = F.simulate(synth.TRUTH_BETA, ign, synth.TARGET_SEED)
+    target = tb >= 0
+    target[5:9, 5:9] = True               # a second patch, partly blocked
+    m = ctx.landscape_upload(land)
+    m.target_upload(target)
+    rng = np.random.default_rng(4)
+    n, G, reps = 300, 7, 3
+    genes = rng.normal(0, 5, (n, G))
+    genes[:, 5] = rng.uniform(-20, 110, n)
+    genes[:, 6] = rng.uniform(-20, 90, n)
+    genes[:40, 5] = np.floor(genes[:40, 5]) + 0.5
+    genes[40:60, 6] = np.floor(genes[40:60, 6]) + 0.5
+    genes[60, 5:] = np.nan
+    got = fire.fire_snap_ignitions(ctx, m, genes, 5, 6, reps)
+    want = np.array([F.snap_ignition(target, genes[i, 5], genes[i, 6])
+                     for i in range(n)], np.int32)
+    assert np.array_equal(got, np.repeat(want, reps, axis=0))
+    gd = torch.tensor(genes, device="cuda")
+    out = torch.full((n * reps, 2), -1, dtype=torch.int32, device="cuda")
+    torch.cuda.synchronize()
+    fire.fire_snap_ignitions(ctx, m, gd, 5, 6, reps, device=True, out=out)
+    assert np.array_equal(out.cpu().numpy(), got)
+    m.free()
+
+
+def test_seven_gene_ga_run_matches_oracle_driven_run(env):
+    """The variable-ignition GA (Sec. 3, Table 3: x and y as genes 6 and 7):
+    four generations of population 16 x 2 replicates, every generation's
+    population and fitness equal to the same run with the oracle's snapping,
+    simulation, fitness, averaging and seven-gene GA step."""
+    torch, fire, oracle, ctx = env
+    from paper_1701_03549_gb300 import calibrate
+
+    land = synth.landscape(48, 56, seed=33, wind_seed=33)
+    ign = synth.centre_ignition(land.veg)
+    F = oracle.Features(land)
+    _, target = workloads.pick_target(
+        lambda s: F.simulate(synth.TRUTH_BETA, ign, s)[1] >= 0,
+        int(F.burnable.sum()))
+    burnable = land.veg != 0
+    m = ctx.landscape_upload(land)
+    m.target_upload(target)
+    P, R, NG = 16, 2, 4
+    hist = calibrate.run_ga_ignition(ctx, m, target, burnable, pop=P, reps=R,
+                                     generations=NG, ga_seed=13, sim_seed=7)
+    genes = calibrate.initial_population_7(target, burnable, P, 13)
+    H, W = land.veg.shape
+    lo = np.array([-30.0] * 5 + [0.0, 0.0])
+    hi = np.array([30.0] * 5 + [W - 1.0, H - 1.0])
+    for g in range(NG):
+        seeds = calibrate.sim_seeds(7, g, P, R)
+        fit = []
+        for i in range(P * R):
+            cell = F.snap_ignition(target, genes[i // R, 5], genes[i // R, 6])
+            o, _ = F.simulate(genes[i // R, :5], cell, int(seeds[i]),
+                              target=target, want_steps=False)
+            fit.append(oracle.fitness(o["burnt"], o["inter"], o["target"], 1))
+        f = oracle.group_mean(np.asarray(fit), R)
+        assert np.array_equal(hist.params[g], genes), g
+        assert np.array_equal(hist.fitness[g], f), g
+        genes = oracle.ga_step(genes, f, g, NG, 13, lo, hi)
+    # the ignition genes stay on the grid
+    last = hist.params[-1]
+    assert np.all((last[:, 5] >= 0) & (last[:, 5] <= W - 1))
+    assert np.all((last[:, 6] >= 0) & (last[:, 6] <= H - 1))
+    m.free()
+
+
+@pytest.mark.parametrize("genes7", [False, True])
+def test_checkpoint_resume_is_bit_identical(env, tmp_path, genes7):
+    """A GA run stopped after two of five generations and resumed from its
+    checkpoint ends with exactly the populations and fitness of the run that
+    was never interrupted (five and seven genes)."""
+    torch, fire, oracle, ctx = env
+    from paper_1701_03549_gb300 import calibrate
+
+    land = synth.landscape(64, 64, seed=41, wind_seed=41)
+    ign = synth.centre_ignition(land.veg)
+    m = ctx.landscape_upload(land)
+    _, bs = m.simulate_batch(np.asarray([synth.TRUTH_BETA]),
+                             np.asarray([ign], np.int32),
+                             np.asarray([synth.TARGET_SEED], np.uint64),
+                             want_steps=True)
+    target = bs[0] >= 0
+    m.target_upload(target)
+    burnable = land.veg != 0
+    path = str(tmp_path / "ga.npz")
+
+    def run(**kw):
+        if genes7:
+            return calibrate.run_ga_ignition(ctx, m, target, burnable, pop=12,
+                                             reps=2, generations=5, ga_seed=2,
+                                             sim_seed=3, **kw)
+        return calibrate.run_ga(ctx, m, ign, pop=12, reps=2, generations=5,
+                                ga_seed=2, sim_seed=3, **kw)
+
+    full = run()
+    part = run(checkpoint=path, stop_after=2)
+    assert len(part.params) == 2
+    resumed = run(checkpoint=path)
+    assert len(resumed.params) == 5
+    for g in range(5):
+        assert np.array_equal(resumed.params[g], full.params[g]), g
+        assert np.array_equal(resumed.fitness[g], full.fitness[g]), g
+    m.free()

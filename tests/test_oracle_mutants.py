@@ -77,8 +77,8 @@ MUTANTS = {
         "double r = x - k * ORC_LN2_HEAD;",
         [rm.test_spec_exp_within_two_ulp_of_libm]),
     "nearest-cell ties go to the higher index": (
-        "if (best < 0 || d < bestd) { best = i; bestd = d; }",
-        "if (best < 0 || d <= bestd) { best = i; bestd = d; }",
+        "                if (best < 0 || d < bestd) { best = i; bestd = d; }",
+        "                if (best < 0 || d <= bestd) { best = i; bestd = d; }",
         [ig.test_lattice_point_in_a_hole_snaps_to_the_nearest_burnt_cell]),
     "lattice rows not centred in their strips": (
         "const long long R = r0 + ((2LL * a + 1) * (r1 - r0 + 1)) / (2LL * LH);",
