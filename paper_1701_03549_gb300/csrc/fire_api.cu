@@ -294,6 +294,7 @@ int fire_maps_upload(fire_ctx *ctx, int H, int W, float cell_m,
     cudaError_t e = cudaSuccess;
     if ((e = cudaMalloc(&m->feat, HW * sizeof(float4))) != cudaSuccess ||
         (e = cudaMalloc(&m->wdiag, HW * sizeof(float2))) != cudaSuccess ||
+        (e = cudaMalloc(&m->ps, HW * sizeof(float2))) != cudaSuccess ||
         (e = cudaMalloc(&m->cfl, HW * sizeof(uint16_t))) != cudaSuccess ||
         (e = cudaMalloc(&m->blk, words * 4)) != cudaSuccess ||
         (e = cudaMalloc(&m->tgt, words * 4)) != cudaSuccess ||
@@ -304,6 +305,7 @@ int fire_maps_upload(fire_ctx *ctx, int H, int W, float cell_m,
     }
     m->dev.feat = m->feat;
     m->dev.wdiag = m->wdiag;
+    m->dev.ps = m->ps;
     m->dev.cfl = m->cfl;
     m->dev.blk = m->blk;
     m->dev.tgt = m->tgt;
@@ -340,8 +342,30 @@ int fire_maps_upload(fire_ctx *ctx, int H, int W, float cell_m,
         daspect = f[2];
         dwind = f[3];
     }
+    // the map's tgt_count word doubles as the wind-uniformity flag until the
+    // target is cleared below
     e = launch_features(H, W, dveg, delev, dslope, daspect, dwind, m->feat,
-                        m->wdiag, m->cfl, ctx->stream);
+                        m->wdiag, m->ps, m->cfl, m->tgt_count, ctx->stream);
+    uint32_t wind_varies = 1;
+    float4 f0;
+    float2 w0;
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&wind_varies, m->tgt_count, 4, cudaMemcpyDeviceToHost,
+                            ctx->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&f0, m->feat, sizeof f0, cudaMemcpyDeviceToHost,
+                            ctx->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&w0, m->wdiag, sizeof w0, cudaMemcpyDeviceToHost,
+                            ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e == cudaSuccess && !wind_varies) {
+        m->dev.uniform_wind = 1;
+        m->dev.cw = f0.z;
+        m->dev.sw = f0.w;
+        m->dev.om1 = w0.x;
+        m->dev.om3 = w0.y;
+    }
     if (e == cudaSuccess) e = launch_blocked(m->dev, dveg, m->blk, ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(m->tgt, 0, words * 4, ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(m->tgt_count, 0, 16, ctx->stream);
@@ -371,6 +395,7 @@ void fire_map_free(fire_map *m)
     if (m->ctx) cudaSetDevice(m->ctx->device);
     if (m->feat) cudaFree(m->feat);
     if (m->wdiag) cudaFree(m->wdiag);
+    if (m->ps) cudaFree(m->ps);
     if (m->cfl) cudaFree(m->cfl);
     if (m->blk) cudaFree(m->blk);
     if (m->tgt) cudaFree(m->tgt);

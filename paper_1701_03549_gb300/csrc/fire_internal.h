@@ -24,6 +24,12 @@ struct MapDev {
     int H, W, TH, TW, ntiles;
     const float4 *feat;         // (psi, sig, cos wind, sin wind) per cell
     const float2 *wdiag;        // cos(wind - 45 deg), cos(wind - 135 deg) per cell
+    const float2 *ps;           // (psi, sig) per cell
+    // A wind raster of one value everywhere (bit for bit) has the same four
+    // wind terms in every cell: the simulation then reads them from here and
+    // only (psi, sig) per cell (10 bytes with the flags instead of 26).
+    int uniform_wind;
+    float cw, sw, om1, om3;
     const uint16_t *cfl;        // bit d<8 uphill from source d, 8 forest, 9 burnable
     const uint32_t *blk;        // non-burnable bitmap, ntiles * 32 words
     const uint32_t *tgt;        // target bitmap, ntiles * 32 words
@@ -129,7 +135,8 @@ __host__ __device__ inline SimLayout sim_layout(int ntiles, int qcap,
 cudaError_t launch_features(int H, int W, const uint8_t *veg, const float *elev,
                             const float *slope, const float *aspect,
                             const float *wind, float4 *feat, float2 *wdiag,
-                            uint16_t *cfl, cudaStream_t st);
+                            float2 *ps, uint16_t *cfl, uint32_t *wind_varies,
+                            cudaStream_t st);
 cudaError_t launch_blocked(const MapDev &m, const uint8_t *veg, uint32_t *blk,
                            cudaStream_t st);
 cudaError_t launch_target(const MapDev &m, const uint8_t *burnt, uint32_t *tgt,
@@ -222,6 +229,7 @@ struct fire_map {
     float cell_m = 0.f;
     float4 *feat = nullptr;
     float2 *wdiag = nullptr;
+    float2 *ps = nullptr;
     uint16_t *cfl = nullptr;
     uint32_t *blk = nullptr;
     uint32_t *tgt = nullptr;

@@ -54,9 +54,12 @@ __global__ void k_features(int H, int W, const uint8_t *__restrict__ veg,
                            const float *__restrict__ wind,
                            float4 *__restrict__ feat,
                            float2 *__restrict__ wdiag,
-                           uint16_t *__restrict__ cfl)
+                           float2 *__restrict__ ps,
+                           uint16_t *__restrict__ cfl,
+                           uint32_t *__restrict__ wind_varies)
 {
     const long long n = (long long)H * W;
+    const uint32_t wind0 = __float_as_uint(wind[0]);
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
         const int r = (int)(i / W), c = (int)(i - (long long)r * W);
@@ -81,6 +84,8 @@ __global__ void k_features(int H, int W, const uint8_t *__restrict__ veg,
         if (v == 1) f |= kFlagForest;
         if (v != 0) f |= kFlagBurnable;
         feat[i] = make_float4(psi, sig, cw, sw);
+        ps[i] = make_float2(psi, sig);
+        if (__float_as_uint(wind[i]) != wind0) *wind_varies = 1u;
         wdiag[i] = make_float2(__double2float_rn(spec::omega(cw, sw, 1)),
                                __double2float_rn(spec::omega(cw, sw, 3)));
         cfl[i] = f;
@@ -268,8 +273,16 @@ __device__ __forceinline__ bool trial_cell(const SimCtx &s, uint32_t cell,
 {
     const MapDev &m = *s.map;
     const SimShared &sh = *s.sh;
-    const float4 f = __ldg(&m.feat[cell]);
-    const float2 wd = __ldg(&m.wdiag[cell]);
+    float4 f;   // (psi, sig, cos wind, sin wind)
+    float2 wd;  // diagonal wind terms
+    if (m.uniform_wind) {
+        const float2 p = __ldg(&m.ps[cell]);
+        f = make_float4(p.x, p.y, m.cw, m.sw);
+        wd = make_float2(m.om1, m.om3);
+    } else {
+        f = __ldg(&m.feat[cell]);
+        wd = __ldg(&m.wdiag[cell]);
+    }
     const uint32_t fl = __ldg(&m.cfl[cell]);
     const bool forest = (fl & kFlagForest) != 0;
     const uint32_t up = fl & 0xffu;
@@ -1244,11 +1257,15 @@ static int grid_for(long long n, int block)
 cudaError_t launch_features(int H, int W, const uint8_t *veg, const float *elev,
                             const float *slope, const float *aspect,
                             const float *wind, float4 *feat, float2 *wdiag,
-                            uint16_t *cfl, cudaStream_t st)
+                            float2 *ps, uint16_t *cfl, uint32_t *wind_varies,
+                            cudaStream_t st)
 {
     const long long n = (long long)H * W;
+    cudaError_t e = cudaMemsetAsync(wind_varies, 0, sizeof(uint32_t), st);
+    if (e != cudaSuccess) return e;
     k_features<<<grid_for(n, 256), 256, 0, st>>>(H, W, veg, elev, slope, aspect,
-                                                 wind, feat, wdiag, cfl);
+                                                 wind, feat, wdiag, ps, cfl,
+                                                 wind_varies);
     return cudaGetLastError();
 }
 

@@ -8,7 +8,8 @@
   device's storage points, from the same inputs and weights (tolerances from
   the BF16 rounding: a stored value may differ by one BF16 step where the
   FP32 and float64 sums straddle a rounding boundary);
-* the gradient against the exact float64 gradient (mixed-precision error);
+* the gradient against the exact float64 gradient (mixed-precision error),
+  per tensor in norm and element by element;
 * Adam's first step against its closed form; training lowers the loss;
 * screening (expected-size fitness and ranking) on seeded inputs.
 """
@@ -181,6 +182,24 @@ def test_forward_backward_match_the_oracle(ctx):
     for name, e_emul, e_gpu, _ in report:
         assert e_gpu <= 2.0 * e_emul + 2e-3, (name, e_emul, e_gpu)
     assert rel(g, g_exact) <= 5e-2
+    # Element by element: the device and the emulation round the same values
+    # to BF16 at the same points and differ only in FP32 against float64
+    # sums, so each is a rounding perturbation of the exact gradient of the
+    # same kind.  With E = the emulation's largest deviation from the exact
+    # gradient over the tensor, the triangle inequality bounds every element
+    # of |g_dev - g_emul| by E + (the device's own largest deviation, of the
+    # same size): 2 E, held here to 3 E for the spread of that maximum, plus
+    # a floor of 2^-20 max |g| for tensors the rounding barely moves.
+    worst = []
+    for name in E:
+        d = np.abs(G[name] - R[name])
+        bound = (3.0 * np.abs(R[name] - E[name]).max() +
+                 2.0 ** -20 * np.abs(R[name]).max())
+        i = int(np.argmax(d))
+        worst.append((name, i, float(d.flat[i]), float(bound)))
+        assert d.max() <= bound, (name, i, float(d.flat[i]), float(bound))
+    print("worst element per tensor (name, flat index, |dev - emul|, bound):",
+          [(n, i, f"{v:.3g}", f"{b:.3g}") for n, i, v, b in worst])
     # one Adam step from zero moments moves each weight by lr g/(|g| + eps)
     lr = 1e-3
     net.adam(lr, sync=True)
