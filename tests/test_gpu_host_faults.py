@@ -23,7 +23,10 @@ def test_forced_allocation_failure_leaves_the_context_usable(after):
     ref_ctx = fire.Context(0)
     ref_m = ref_ctx.landscape_upload(wl.land)
     want, _ = ref_m.simulate_batch(wl.params, wl.ignitions, wl.seeds)
-    ctx = fire.Context(0)       # fresh: its first call grows two buffers
+    # fresh, with the state in global memory: its first host-pointer call
+    # grows two buffers (argument staging, then the state buffers)
+    ctx = fire.Context(0)
+    ctx.set_launch(4, 0, 0, fire.STATE_GLOBAL)
     m = ctx.landscape_upload(wl.land)
     ctx.debug_fail_alloc(after)
     with pytest.raises(fire.FireError) as e:
