@@ -464,6 +464,12 @@ def run_uneven(args):
     nsteps = args.warmup + args.steps
     n = 100_000
     wl = workloads.uneven_fires(n, first_seed=1 + rank * n * (nsteps + 1))
+    if args.sample > 1:   # a reduced batch (profiling): every K-th simulation
+        keep = np.arange(0, n, args.sample)
+        wl = workloads.MultiWorkload(wl.name, wl.lands, wl.map_of_sim[keep],
+                                     wl.params[keep], wl.ignitions[keep],
+                                     wl.seeds[keep])
+        n = wl.n
     maps = [ctx.landscape_upload(L) for L in wl.lands]
     tseeds = []
     for j, (m, L) in enumerate(zip(maps, wl.lands)):
@@ -559,7 +565,7 @@ def run_uneven(args):
     d2h = n * 24 + n * 8
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.sample == 1:
         cpu = cpu_baseline("uneven", os.cpu_count() or 1)
         cpu["targets_match_gpu"] = cpu["target_seeds"] == tseeds
 
@@ -579,7 +585,9 @@ def run_uneven(args):
             "ms_per_step": total_s * 1e3 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "u32", "data": "synthetic",
-            "config": _config("uneven", world),
+            "config": dict(_config("uneven", world), **(
+                {"sample_every": args.sample, "sims_per_step": n}
+                if args.sample > 1 else {})),
             "launch": {k: tuned[k] for k in ("warps_per_block", "blocks_per_sm",
                                              "queue_entries", "state_mode")},
             "target_seeds": tseeds,
@@ -626,6 +634,11 @@ def run_ga512(args):
     nsteps = args.warmup + args.steps
     first = parallel.rank_seed_offset(rank, SIMS * (nsteps + 2))
     wl = workloads.ga_generation_512(POP, REPS, first_seed=first)
+    if args.sample > 1:   # a reduced batch (profiling): every K-th simulation
+        keep = np.arange(0, SIMS, args.sample)
+        wl = workloads.Workload(wl.name, wl.land, wl.ignition, wl.params[keep],
+                                wl.ignitions[keep], wl.seeds[keep])
+    nsim = wl.n
     m = ctx.landscape_upload(wl.land)
     H, W = wl.shape
     tseed, target = _gpu_target(fire, m, wl.ignition,
@@ -638,11 +651,11 @@ def run_ga512(args):
                                wl.seeds, longest_first=True)
     p_dev = torch.tensor(wl.params, dtype=torch.float64, device=dev)
     g_dev = torch.tensor(wl.ignitions, dtype=torch.int32, device=dev)
-    seeds_host = [wl.seeds + np.uint64(k * SIMS) for k in range(nsteps)]
+    seeds_host = [wl.seeds + np.uint64(k * nsim) for k in range(nsteps)]
     s_dev = [torch.tensor(s.view(np.int64), device=dev) for s in seeds_host]
-    outs = [torch.zeros((SIMS, 6), dtype=torch.int32, device=dev)
+    outs = [torch.zeros((nsim, 6), dtype=torch.int32, device=dev)
             for _ in range(nsteps)]
-    fit = [torch.zeros(SIMS, dtype=torch.float64, device=dev)
+    fit = [torch.zeros(nsim, dtype=torch.float64, device=dev)
            for _ in range(nsteps)]
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     torch.cuda.synchronize()
@@ -689,7 +702,7 @@ def run_ga512(args):
     assert all(int((r["status"] & (fire.STATUS_BAD_IGNITION
                                     | fire.STATUS_TIMEOUT)).max()) == 0
                for r in res)
-    value = SIMS * args.steps * world / total_s
+    value = nsim * args.steps * world / total_s
 
     # end to end through the C ABI with host buffers (pinned): the same seeds
     # and L2 flush as the device-timed steps
@@ -707,16 +720,16 @@ def run_ga512(args):
         r, _ = m.simulate_batch(pin_p, pin_g, pin_s[k], longest_first=True)
         f = fire.fire_fitness(ctx, r, fire.FITNESS_JACCARD)
         e2e_s += time.perf_counter() - t0
-        assert f.shape == (SIMS,)
+        assert f.shape == (nsim,)
     e2e_s = parallel.max_over_ranks(e2e_s, world, dev)
-    e2e_value = SIMS * e2e_steps * world / e2e_s
+    e2e_value = nsim * e2e_steps * world / e2e_s
     dev_same = parallel.max_over_ranks(sum(step_ms[:e2e_steps]) / 1e3, world,
                                        dev)
-    h2d = SIMS * (40 + 8 + 8) + SIMS * 24
-    d2h = SIMS * 24 + SIMS * 8
+    h2d = nsim * (40 + 8 + 8) + nsim * 24
+    d2h = nsim * 24 + nsim * 8
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.sample == 1:
         cpu = cpu_baseline("ga512", os.cpu_count() or 1)
         cpu["targets_match_gpu"] = cpu["target_seeds"] == [int(tseed)]
 
@@ -734,7 +747,9 @@ def run_ga512(args):
             "ms_per_step": 1e3 * total_s / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "u32", "data": "synthetic",
-            "config": _config("ga512", world),
+            "config": dict(_config("ga512", world), **(
+                {"sample_every": args.sample, "sims_per_step": nsim}
+                if args.sample > 1 else {})),
             "launch": {k: tuned[k] for k in ("warps_per_block", "blocks_per_sm",
                                              "queue_entries", "state_mode")},
             "target_seed": int(tseed), "target_cells": int(target.sum()),
@@ -742,13 +757,13 @@ def run_ga512(args):
             "cell_updates_vs_dense_sweep": _dense_sweep_roof(
                 steps_all * H * W / total_s, peaks, pk),
             "trials_per_s": trials_all / total_s,
-            "mean_steps_per_sim": steps_all / (SIMS * args.steps * world),
+            "mean_steps_per_sim": steps_all / (nsim * args.steps * world),
             "roofline": roof,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "steps": e2e_steps,
-                    "device_value_same_steps": SIMS * e2e_steps * world / dev_same,
+                    "device_value_same_steps": nsim * e2e_steps * world / dev_same,
                     "timed": "fire_simulate_batch and fire_fitness on pinned "
                              "host buffers, wall clock per call, with the "
                              "seeds and L2 flush of the first device-timed "
@@ -1196,6 +1211,9 @@ def main():
     ap.add_argument("--impl", choices=("native", "reference"),
                     default="native")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sample", type=int, default=1,
+                    help="time every K-th simulation of the workload only (a "
+                         "reduced batch for profiling; not a headline line)")
     ap.add_argument("--workload",
                     choices=("uneven", "ga512", "recover", "surrogate",
                              "surrogate_step"),
