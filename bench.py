@@ -1054,6 +1054,86 @@ def run_surrogate_step(args):
     return 0
 
 
+BURNOUT = ("burnout_512: the 512x512 GA generation (4096 simulations) with "
+           "per-cell burn times: 1 everywhere (the paper's rule) and per fuel "
+           "class (1, 3, 1, 2, 4) for classes 0..4, against fire_simulate_batch "
+           "at the same launch shape and order")
+
+
+def run_burnout(args):
+    """Burn-time variant of the simulation kernel against the plain one on
+    the 512x512 generation (device-resident inputs, L2 flushed before every
+    timed call, CUDA events)."""
+    g = _setup_gpu()
+    if g is None:
+        print(json.dumps({"metric": METRIC, "error": "no CUDA device"}))
+        return 1
+    torch, fire, ctx, dev, stream, rank, world, local = g
+    wl = workloads.ga_generation_512(POP, REPS)
+    m = ctx.landscape_upload(wl.land)
+    tseed, target = _gpu_target(fire, m, wl.ignition,
+                                int((wl.land.veg != 0).sum()))
+    m.target_upload(target)
+    tuned = fire.fire_autotune(ctx, [m], None, wl.params, wl.ignitions,
+                               wl.seeds)
+    p = torch.tensor(wl.params, dtype=torch.float64, device=dev)
+    gi = torch.tensor(wl.ignitions, dtype=torch.int32, device=dev)
+    sd = torch.tensor(wl.seeds.view(np.int64), device=dev)
+    out = torch.zeros((SIMS, 6), dtype=torch.int32, device=dev)
+    ones = torch.ones(wl.land.veg.shape, dtype=torch.uint8, device=dev)
+    fuel = torch.tensor(np.asarray((1, 3, 1, 2, 4), np.uint8)[
+        np.minimum(wl.land.veg, 4)], device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    calls = {
+        "batch": lambda: m.simulate_batch(p, gi, sd, device=True, out=out),
+        "burn_1": lambda: m.simulate_burnout(p, gi, sd, ones, device=True,
+                                             out=out),
+        "burn_per_fuel": lambda: m.simulate_burnout(p, gi, sd, fuel,
+                                                    device=True, out=out),
+    }
+    res = {}
+    clocks = Clocks(local)
+    for name, fn in calls.items():
+        for _ in range(args.warmup):
+            flush.zero_()
+            fn()
+        ms = []
+        for _ in range(args.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        r = fire.results_view(out)
+        res[name] = {"ms": statistics.mean(ms),
+                     "mean_steps": float(r["steps"].astype(np.int64).mean()),
+                     "trials": int(r["trials"].astype(np.int64).sum())}
+    ck = clocks.stop()
+    v = SIMS / (res["burn_per_fuel"]["ms"] / 1e3)
+    line = {
+        "metric": "burn-time CA sims/s", "value": v, "unit": UNIT,
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": res["burn_per_fuel"]["ms"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic",
+        "config": {"workload": BURNOUT, "l2": L2_NOTE,
+                   "launch": {k: tuned[k] for k in (
+                       "warps_per_block", "blocks_per_sm", "queue_entries",
+                       "state_mode")}},
+        "calls": res,
+        "burn_1_over_batch": res["burn_1"]["ms"] / res["batch"]["ms"],
+        "cpu_baseline": None, "e2e": None,
+        "gpu_launches": args.steps * 3, "clocks": ck}
+    if rank == 0:
+        print(json.dumps(line))
+    m.free()
+    ctx.close()
+    return 0
+
+
 RECOVER = ("recover_1024: 1024x1024 map (spatially varying wind), target "
            "from the reference parameters (Table 2) at the centre ignition; "
            "plain GA with populations 256 and 1024 x 16 replicates, the "
@@ -1215,8 +1295,8 @@ def main():
                     help="time every K-th simulation of the workload only (a "
                          "reduced batch for profiling; not a headline line)")
     ap.add_argument("--workload",
-                    choices=("uneven", "ga512", "recover", "surrogate",
-                             "surrogate_step"),
+                    choices=("uneven", "ga512", "recover", "burnout",
+                             "surrogate", "surrogate_step"),
                     default="uneven",
                     help="uneven (default): nine fires 200x300..2000x1500, "
                          "100k simulations in one launch; ga512: one "
@@ -1241,6 +1321,8 @@ def main():
         return run_ga512(args)
     if args.workload == "recover":
         return run_recover(args)
+    if args.workload == "burnout":
+        return run_burnout(args)
     if args.workload == "surrogate":
         return run_surrogate(args)
     if args.workload == "surrogate_step":

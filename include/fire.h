@@ -425,9 +425,12 @@ FIRE_API int fire_philox_blocks(fire_ctx *ctx, uint64_t n, const uint32_t ctr[4]
  *              times are a table lookup by vegetation class on the caller's
  *              side.
  * Other arguments, layouts and errors as fire_simulate_batch;
- * FIRE_CELL_UNIFORM and FIRE_GRAPH are rejected (FIRE_EINVAL).  Runs a
- * simpler kernel than fire_simulate_batch (a byte of state per cell, dense
- * sweeps of the burning box). */
+ * FIRE_CELL_UNIFORM and FIRE_GRAPH are rejected (FIRE_EINVAL).  Runs the
+ * bit-plane simulation kernel of fire_simulate_batch in its burn-time form
+ * (state in global memory: the two state planes, two planes of the cells
+ * still burning from earlier steps and one byte of fuel per cell per block),
+ * at the launch shape set by fire_set_launch or the autotuner for the map's
+ * tile count. */
 FIRE_API int fire_simulate_burnout(fire_ctx *ctx, const fire_map *map, int n,
                                    const fire_params *params,
                                    const fire_cell *ignitions,

@@ -86,7 +86,7 @@ bool valid_map(const fire_map *m) { return m && m->ctx && m->feat; }
 // Launch shape of the simulation kernel for maps of up to `ntiles` tiles:
 // an explicit fire_set_launch override, else the autotuned shape recorded for
 // this tile count, else a heuristic.
-int plan_launch(fire_ctx *ctx, int ntiles, long long n, LaunchPlan *p)
+int plan_launch(fire_ctx *ctx, int ntiles, long long n, LaunchPlan *p, bool burn)
 {
     int warps = 0, bps = 0, queue = 0, state = FIRE_STATE_AUTO;
     const bool override = ctx->warps_per_block || ctx->blocks_per_sm ||
@@ -110,6 +110,8 @@ int plan_launch(fire_ctx *ctx, int ntiles, long long n, LaunchPlan *p)
     nwarps = std::min(nwarps, kSimMaxThreads / 32);
     int qcap = queue > 0 ? queue : 4096;
     SimLayout L = sim_layout(ntiles, qcap, true);
+    // the burn-time variant keeps its state in global memory
+    if (burn) state = FIRE_STATE_GLOBAL;
     bool smem_state = state == FIRE_STATE_SHARED ||
                       (state == FIRE_STATE_AUTO && L.total <= ctx->max_smem_optin);
     if (smem_state && L.total > ctx->max_smem_optin)
@@ -126,7 +128,7 @@ int plan_launch(fire_ctx *ctx, int ntiles, long long n, LaunchPlan *p)
             return set_err(ctx, FIRE_EINVAL, "worklists of %d tiles do not fit in "
                            "shared memory", ntiles);
     }
-    const void *kfn = simulate_kernel_ptr(smem_state);
+    const void *kfn = burn ? simulate_burn_kernel_ptr() : simulate_kernel_ptr(smem_state);
     cudaError_t e = cudaFuncSetAttribute(
         kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
     if (e != cudaSuccess) return cuda_err(ctx, e, "cudaFuncSetAttribute");
@@ -491,6 +493,8 @@ int launch_batch(fire_ctx *ctx, const fire_map *m, int n,
     a.burnt_bits = dbits;
     a.work_counter = ctx->counter;
     a.gstate = ctx->gstate;
+    a.block_words = 0;
+    a.burn_time = nullptr;
     a.error_word = ctx->counter + 1;
     a.max_steps = max_steps;
     a.qcap = plan.qcap;

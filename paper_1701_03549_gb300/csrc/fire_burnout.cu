@@ -1,6 +1,8 @@
 // C ABI of the burn-out-time variant (fire_simulate_burnout, include/fire.h):
-// argument checks, staging of host arguments and the launch of k_burnout.
+// argument checks, staging of host arguments and the launch of the bit-plane
+// simulation kernel in its burn-time form.
 #include <cmath>
+#include <cstring>
 
 #include "fire_internal.h"
 
@@ -93,27 +95,43 @@ extern "C" int fire_simulate_burnout(fire_ctx *ctx, const fire_map *m, int n,
         dout = (fire_result *)(p + bp + bi + bs + bb);
         if (want_steps) dsteps = (int32_t *)(p + bp + bi + bs + bb + bo);
     }
-    const int grid = (int)std::min<long long>((long long)n, (long long)ctx->num_sms * 4);
-    rc = grow_device(ctx, (void **)&ctx->gstate, &ctx->gstate_bytes,
-                     (size_t)grid * HW, "burn-out state");
+    // the bit-plane simulation kernel with burn times: state, two "still
+    // burning" planes and a fuel byte per cell in each block's global buffer
+    LaunchPlan plan;
+    rc = plan_launch(ctx, m->dev.ntiles, n, &plan, true);
     if (rc) {
         if (tmp) cudaFree(tmp);
         return rc;
     }
-    BurnLaunch a;
+    const size_t words = burn_block_words(m->dev.ntiles, (long long)HW);
+    rc = grow_device(ctx, (void **)&ctx->gstate, &ctx->gstate_bytes,
+                     (size_t)plan.grid * words * 4, "burn-time state");
+    if (rc) {
+        if (tmp) cudaFree(tmp);
+        return rc;
+    }
+    SimLaunch a;
+    std::memset(&a, 0, sizeof a);
     a.map = m->dev;
+    a.nmaps = 1;
+    a.ntiles_max = m->dev.ntiles;
     a.n = n;
     a.params = dp;
     a.ign = di;
     a.seeds = ds;
-    a.burn_time = db;
     a.out = dout;
     a.burn_step = dsteps;
-    a.state = (uint8_t *)ctx->gstate;
     a.work_counter = ctx->counter;
+    a.gstate = ctx->gstate;
+    a.block_words = words;
+    a.burn_time = db;
+    a.error_word = ctx->counter + 1;
     a.max_steps = max_steps;
+    a.qcap = plan.qcap;
+    a.cell_uniform = 0;
     cudaError_t e = cudaMemsetAsync(ctx->counter, 0, 4, ctx->stream);
-    if (e == cudaSuccess) e = launch_burnout(a, grid, ctx->stream);
+    if (e == cudaSuccess)
+        e = launch_simulate_burn(a, plan.nwarps, plan.grid, plan.L.total, ctx->stream);
     if (e == cudaSuccess && !dev) {
         e = cudaMemcpyAsync(out, dout, (size_t)n * sizeof(fire_result),
                             cudaMemcpyDeviceToHost, ctx->stream);

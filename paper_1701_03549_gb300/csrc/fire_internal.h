@@ -53,26 +53,16 @@ struct SimLaunch {
                                // burnt words (tile-major, blocked cells
                                // cleared), ntiles * 32 words per simulation
     uint32_t *work_counter;    // zeroed before launch
-    uint32_t *gstate;          // global-state variant: 2 * ntiles * 32 words per block
+    uint32_t *gstate;          // global-state variant: block_words words per block
+    size_t block_words;        // 0: 2 * ntiles_max * 32 (the X, Y planes)
+    const uint8_t *burn_time;  // burn-time variant: steps each cell burns
+                               // (1..250, others clamped); its blocks keep X, Y,
+                               // two "still burning" planes and one fuel byte
+                               // per cell in their global state
     uint32_t *error_word;      // set nonzero when a bounded wait runs out
     uint32_t max_steps;        // 0 = no cap
     int qcap;                  // candidate-queue capacity (entries)
     int cell_uniform;          // 1: one uniform per target cell (Sec. 2.3)
-};
-
-// Launch of the burn-out-time variant (per-cell burn times, byte state).
-struct BurnLaunch {
-    MapDev map;
-    int n;
-    const fire_params *params;
-    const fire_cell *ign;
-    const uint64_t *seeds;
-    const uint8_t *burn_time;  // per cell; >= 1 on burnable cells
-    fire_result *out;
-    int32_t *burn_step;        // nullable
-    uint8_t *state;            // H * W bytes per block
-    uint32_t *work_counter;    // zeroed before launch
-    uint32_t max_steps;        // 0 = no cap
 };
 
 // Largest batch ordered longest-first (the ranking is quadratic in n).
@@ -143,10 +133,18 @@ cudaError_t launch_target(const MapDev &m, const uint8_t *burnt, uint32_t *tgt,
                           uint32_t *tgt_count, cudaStream_t st);
 cudaError_t launch_simulate(const SimLaunch &a, bool smem_state, int nwarps,
                             int grid, size_t smem_bytes, cudaStream_t st);
+// The burn-time variant (global-memory state only).
+cudaError_t launch_simulate_burn(const SimLaunch &a, int nwarps, int grid,
+                                 size_t smem_bytes, cudaStream_t st);
+// Words of one block's global state in the burn-time variant.
+inline size_t burn_block_words(int ntiles, long long HW)
+{
+    return 4 * (size_t)ntiles * 32 + (size_t)((HW + 15) / 16) * 4;
+}
 // Threads per block the simulation kernel is compiled for (upper bound).
 constexpr int kSimMaxThreads = 512;
 const void *simulate_kernel_ptr(bool smem_state);
-cudaError_t launch_burnout(const BurnLaunch &a, int grid, cudaStream_t st);
+const void *simulate_burn_kernel_ptr();
 cudaError_t launch_longest_first(const MapDev &m, int n, const fire_params *params,
                                  float *key, uint32_t *order, cudaStream_t st);
 cudaError_t launch_fitness(const fire_result *r, int n, int kind, double *out,
@@ -248,7 +246,10 @@ int grow_device(fire_ctx *ctx, void **buf, size_t *cap, size_t need,
 size_t round16(size_t x);
 bool valid_map(const fire_map *m);
 int noalloc_take_error(int device, bool *set);
-int plan_launch(fire_ctx *ctx, int ntiles, long long n, LaunchPlan *p);
+// Launch shape of the simulation kernel (burn: the burn-time variant, whose
+// state is always in global memory).
+int plan_launch(fire_ctx *ctx, int ntiles, long long n, LaunchPlan *p,
+                bool burn = false);
 cudaError_t launch_conv_tma(int mode, const uint16_t *in, const uint16_t *w,
                             const float *bias, const uint16_t *hprev, uint16_t *out,
                             int n, int S, int lgS, int d, uint32_t *err,

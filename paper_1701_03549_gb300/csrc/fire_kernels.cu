@@ -191,9 +191,18 @@ struct SimCtx {
     uint16_t *lists;
     uint32_t *queue;
     uint32_t *X, *Y;
+    uint32_t *K0, *K1;   // burn-time variant: cells still burning, by step parity
+    uint8_t *fuel;       // burn-time variant: steps of fuel left per cell
     int ntiles;
     int sim;
 };
+
+// Steps a cell ignited now will burn (burn-time variant), 1..250.
+__device__ __forceinline__ uint8_t burn_steps(const SimLaunch &a, uint32_t cell)
+{
+    const uint32_t b = __ldg(&a.burn_time[cell]);
+    return (uint8_t)(b < 1u ? 1u : (b > 250u ? 250u : b));
+}
 
 __device__ __forceinline__ int tile_row(const SimShared &sh, int k)
 {
@@ -323,12 +332,14 @@ __device__ __forceinline__ bool trial_cell(const SimCtx &s, uint32_t cell,
 // Cell (row r, column i of tile k = (ti, tj)) ignites at step t: write it with
 // the "burning, parity t + 1" code and put its tile, and the neighbour tiles
 // across the edges it lies on, on the worklist of step t + 1.
+template <bool kBurn>
 __device__ __forceinline__ void ignite(const SimCtx &s, int k, int ti, int tj,
                                        int r, int i, uint32_t cell, uint32_t t)
 {
     const MapDev &m = *s.map;
     uint32_t *P = (t & 1u) ? s.X : s.Y;
     atomicOr(&P[k * 32 + r], 1u << i);
+    if (kBurn) s.fuel[cell] = burn_steps(*s.a, cell);
     if (s.a->burn_step)
         s.a->burn_step[(long long)s.sim * m.H * m.W + cell] = (int32_t)(t + 1);
     const uint32_t tn = t + 1;
@@ -361,6 +372,7 @@ __device__ __forceinline__ int nth_set_bit(uint32_t m, uint32_t n)
 // Phase A of step t for active tile k, one warp (lane = tile row): retire the
 // previous step's burning cells, find the targets with a burning source in
 // each direction, count the trials and queue the candidates for phase B.
+template <bool kBurn>
 __device__ __forceinline__ void phase_a(const SimCtx &s, int k, uint32_t t,
                                         int lane, uint32_t &ntrials)
 {
@@ -371,15 +383,25 @@ __device__ __forceinline__ void phase_a(const SimCtx &s, int k, uint32_t t,
     const int ti = tile_row(sh, k), tj = k - ti * TW;
     const uint32_t par = t & 1u;
     uint32_t *X = s.X, *Y = s.Y;
+    // burn-time variant: the sources of step t also include the cells that
+    // ignited before step t - 1 and still burn (plane K[t & 1])
+    const uint32_t *Kt = kBurn ? (par ? s.K1 : s.K0) : nullptr;
 
     if (lane == 0) atomicAnd(&s.marks[k >> 4], ~(1u << (2 * (k & 15) + par)));
 
     const int w = k * 32 + lane;
     const uint32_t x = X[w], y = Y[w];
-    const uint32_t b = burning(x, y, par);
+    uint32_t b = burning(x, y, par);
+    if (kBurn) b |= Kt[w];
     uint32_t bl = 0, br = 0;
-    if (tj > 0) bl = burning(X[w - 32], Y[w - 32], par);
-    if (tj < TW - 1) br = burning(X[w + 32], Y[w + 32], par);
+    if (tj > 0) {
+        bl = burning(X[w - 32], Y[w - 32], par);
+        if (kBurn) bl |= Kt[w - 32];
+    }
+    if (tj < TW - 1) {
+        br = burning(X[w + 32], Y[w + 32], par);
+        if (kBurn) br |= Kt[w + 32];
+    }
     // Edge rows of the tiles above (row 31) and below (row 0), including the
     // diagonal neighbours: lanes 0..5 fetch one word each.
     uint32_t edge = 0;
@@ -390,6 +412,7 @@ __device__ __forceinline__ void phase_a(const SimCtx &s, int k, uint32_t t,
         if (nti >= 0 && nti < TH && ntj >= 0 && ntj < TW) {
             const int we = (nti * TW + ntj) * 32 + (dti < 0 ? 31 : 0);
             edge = burning(X[we], Y[we], par);
+            if (kBurn) edge |= Kt[we];
         }
     }
     uint32_t bu = __shfl_up_sync(kFull, b, 1);
@@ -420,6 +443,41 @@ __device__ __forceinline__ void phase_a(const SimCtx &s, int k, uint32_t t,
     if (stale) {
         X[w] = x | stale;
         Y[w] = y | stale;
+    }
+    if (kBurn) {
+        // each cell burning at step t spends one step of fuel; the ones left
+        // with fuel burn at step t + 1 as well (plane K[(t + 1) & 1], written
+        // for this tile's rows only by this warp; a tile holding such cells
+        // is on the next worklist, and so is a neighbour tile across an edge
+        // they lie on)
+        uint32_t cont = 0, mm = b;
+        const uint32_t rowc = (uint32_t)(ti * 32 + lane) * (uint32_t)m.W +
+                              (uint32_t)(tj * 32);
+        while (mm) {
+            const int i = __ffs(mm) - 1;
+            mm &= mm - 1;
+            const uint8_t left = (uint8_t)(s.fuel[rowc + i] - 1u);
+            s.fuel[rowc + i] = left;
+            if (left) cont |= 1u << i;
+        }
+        (par ? s.K0 : s.K1)[w] = cont;
+        const uint32_t cl = __ballot_sync(kFull, cont & 1u);
+        const uint32_t cr = __ballot_sync(kFull, (cont >> 31) & 1u);
+        const uint32_t top = __shfl_sync(kFull, cont, 0);
+        const uint32_t bot = __shfl_sync(kFull, cont, 31);
+        if (__any_sync(kFull, cont != 0) && lane == 0) {
+            sh.newflag[(t + 1) % 3] = 1;
+            const uint32_t tn = t + 1;
+            if (top && ti > 0) mark_tile(s, k - TW, tn);
+            if (bot && ti < TH - 1) mark_tile(s, k + TW, tn);
+            if (cl && tj > 0) mark_tile(s, k - 1, tn);
+            if (cr && tj < TW - 1) mark_tile(s, k + 1, tn);
+            if ((top & 1u) && ti > 0 && tj > 0) mark_tile(s, k - TW - 1, tn);
+            if ((top >> 31) && ti > 0 && tj < TW - 1) mark_tile(s, k - TW + 1, tn);
+            if ((bot & 1u) && ti < TH - 1 && tj > 0) mark_tile(s, k + TW - 1, tn);
+            if ((bot >> 31) && ti < TH - 1 && tj < TW - 1)
+                mark_tile(s, k + TW + 1, tn);
+        }
     }
     if (__any_sync(kFull, b != 0) && lane == 0) mark_tile(s, k, t + 1);
     __syncwarp();
@@ -490,7 +548,7 @@ __device__ __forceinline__ void phase_a(const SimCtx &s, int k, uint32_t t,
                                   (uint32_t)(tj * 32 + i);
             ntrials += (uint32_t)__popc(dm);
             if (trial_cell(s, cell, dm, t)) {
-                ignite(s, k, ti, tj, r, i, cell, t);
+                ignite<kBurn>(s, k, ti, tj, r, i, cell, t);
                 // every writer of this step stores the same values
                 sh.newflag[(t + 1) % 3] = 1;
                 sh.last_new = t + 1;
@@ -499,7 +557,7 @@ __device__ __forceinline__ void phase_a(const SimCtx &s, int k, uint32_t t,
     }
 }
 
-template <bool kSmemState>
+template <bool kSmemState, bool kBurn>
 __global__ void __launch_bounds__(kSimMaxThreads, 2) k_simulate(SimLaunch a)
 {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -520,9 +578,18 @@ __global__ void __launch_bounds__(kSimMaxThreads, 2) k_simulate(SimLaunch a)
     if (kSmemState) {
         s.X = reinterpret_cast<uint32_t *>(smem + L.planes);
     } else {
-        s.X = a.gstate + (size_t)blockIdx.x * 2 * ntiles_max * 32;
+        const size_t stride =
+            a.block_words ? a.block_words : 2 * (size_t)ntiles_max * 32;
+        s.X = a.gstate + (size_t)blockIdx.x * stride;
     }
     s.Y = s.X + ntiles_max * 32;
+    s.K0 = s.K1 = nullptr;
+    s.fuel = nullptr;
+    if (kBurn) {
+        s.K0 = s.Y + ntiles_max * 32;
+        s.K1 = s.K0 + ntiles_max * 32;
+        s.fuel = reinterpret_cast<uint8_t *>(s.K1 + ntiles_max * 32);
+    }
 
     if (kSmemState && threadIdx.x == 0) {
         mbar_init(&sh.mbar, 1);
@@ -553,7 +620,10 @@ __global__ void __launch_bounds__(kSimMaxThreads, 2) k_simulate(SimLaunch a)
                 sh.map = a.map;
             }
             const long long hw = (long long)sh.map.H * sh.map.W;
-            sh.hard_cap = (uint32_t)min(hw + 2, (long long)0x7fffffff);
+            // a fire runs at most one step per cell (one step per cell and
+            // step of burn time in the burn-time variant) plus the last
+            sh.hard_cap = (uint32_t)min((hw + 2) * (kBurn ? 256 : 1),
+                                        (long long)0x7fffffff);
             sh.nmark = (sh.map.ntiles + 15) / 16;
             sh.tw_magic = 0xffffffffu / (uint32_t)sh.map.TW;
             sh.status = map_ok ? 0u : FIRE_STATUS_BAD_MAP;
@@ -601,6 +671,11 @@ __global__ void __launch_bounds__(kSimMaxThreads, 2) k_simulate(SimLaunch a)
                 dx[i] = v;
                 dy[i] = v;
             }
+            if (kBurn) {
+                uint4 *dk = reinterpret_cast<uint4 *>(s.K0);
+                for (int i = threadIdx.x; i < ntiles_max * 16; i += blockDim.x)
+                    dk[i] = make_uint4(0u, 0u, 0u, 0u);
+            }
         }
         if (a.burn_step) {
             int32_t *bs = a.burn_step + (long long)sim * HW;
@@ -640,6 +715,10 @@ __global__ void __launch_bounds__(kSimMaxThreads, 2) k_simulate(SimLaunch a)
                 const int k0 = (g.row >> 5) * m.TW + (g.col >> 5);
                 const int r0 = g.row & 31, i0 = g.col & 31;
                 s.X[k0 * 32 + r0] |= 1u << i0;   // burning, parity 0
+                if (kBurn) {
+                    const uint32_t c0 = (uint32_t)g.row * (uint32_t)m.W + (uint32_t)g.col;
+                    s.fuel[c0] = burn_steps(a, c0);
+                }
                 if (a.burn_step)
                     a.burn_step[(long long)sim * HW + (long long)g.row * m.W +
                                 g.col] = 0;
@@ -672,6 +751,9 @@ __global__ void __launch_bounds__(kSimMaxThreads, 2) k_simulate(SimLaunch a)
             const uint32_t nA = sh.count[t % 3];
             if (nA == 0) break;
             const bool burning_now = sh.newflag[t % 3] != 0;
+            // burn-time variant: the fire ends when nothing burns (its
+            // worklist can still hold tiles to retire)
+            if (kBurn && !burning_now) break;
             if (burning_now && ((a.max_steps && t >= a.max_steps) || t >= sh.hard_cap)) {
                 capped = true;
                 break;
@@ -682,7 +764,7 @@ __global__ void __launch_bounds__(kSimMaxThreads, 2) k_simulate(SimLaunch a)
             }
             const uint16_t *list = s.lists + (t % 3) * ntiles_max;
             for (uint32_t li = warp; li < nA; li += nwarps)
-                phase_a(s, list[li], t, lane, ntrials);
+                phase_a<kBurn>(s, list[li], t, lane, ntrials);
             __syncthreads();
             const uint32_t par = t & 1u;
             const uint32_t nq = min(sh.qcount[par], sh.qvalid[par]);
@@ -701,7 +783,7 @@ __global__ void __launch_bounds__(kSimMaxThreads, 2) k_simulate(SimLaunch a)
                                       (uint32_t)(tj * 32 + i);
                 ntrials += (uint32_t)__popc(e & 0xffu);
                 if (trial_cell(s, cell, e & 0xffu, t)) {
-                    ignite(s, k, ti, tj, r, i, cell, t);
+                    ignite<kBurn>(s, k, ti, tj, r, i, cell, t);
                     any = true;
                 }
             }
@@ -745,231 +827,13 @@ __global__ void __launch_bounds__(kSimMaxThreads, 2) k_simulate(SimLaunch a)
             r.burnt = sh.burnt;
             r.inter = sh.inter;
             r.target = *m.tgt_count;
-            r.steps = capped ? t : sh.last_new + 1;
+            // steps in which some cell burned (the burn-time variant leaves
+            // the loop at the first step with none)
+            r.steps = (capped || kBurn) ? t : sh.last_new + 1;
             r.status = sh.status | (capped ? FIRE_STATUS_STEP_CAP : 0u);
             r.trials = sh.trials;
             a.out[sim] = r;
         }
-    }
-}
-
-// ---------------------------------------------------------------------------
-// Burn-out times (the paper burns every fuel out one step after it ignites,
-// Sec. 2.1, and names fuel-consumption times as future work).  A cell ignited
-// at step t stays burning for burn_time[cell] steps and tries its unburnt
-// neighbours at each of them, with the trial draws and decisions of
-// k_simulate (counter (cell, step, d/4, 0), screened FP32 with the exact FP64
-// fallback), so burn_time = 1 everywhere reproduces k_simulate's fires.
-//
-// A plainer design than k_simulate: one block per simulation at a time, one
-// byte of state per cell in a per-block global buffer (0 unburnt, 1..250
-// steps of fuel left, 253 igniting in this step, 254 burnt, 255
-// non-burnable), and per step two sweeps over the box of burning cells grown
-// by one cell: (1) trials for every unburnt cell with a burning neighbour,
-// (2) burning cells spend a step of fuel and the step's new cells start
-// burning.
-__device__ __forceinline__ bool burnout_decide(const MapDev &m,
-                                               const ScreenParams &sp,
-                                               const double *beta, uint32_t key0,
-                                               uint32_t key1, uint32_t cell,
-                                               uint32_t dm, uint32_t t)
-{
-    const float4 f = __ldg(&m.feat[cell]);
-    const float2 wd = __ldg(&m.wdiag[cell]);
-    const uint32_t fl = __ldg(&m.cfl[cell]);
-    const bool forest = (fl & kFlagForest) != 0;
-    const uint32_t up = fl & 0xffu;
-    const ScreenCell sc = screen_cell(sp, forest, f.x, f.y, f.z, wd.x, f.w, wd.y);
-    bool ign = false;
-    if (dm & 0x0fu) {
-        const uint4 u = philox4x32_10(cell, t, 0u, 0u, key0, key1);
-        ign = test_dirs(dm & 0x0fu, 0, u, sc, sp.b3, sp.margin, up, beta,
-                        forest, f);
-    }
-    if (!ign && (dm & 0xf0u)) {
-        const uint4 u = philox4x32_10(cell, t, 1u, 0u, key0, key1);
-        ign = test_dirs(dm >> 4, 4, u, sc, sp.b3, sp.margin, up, beta,
-                        forest, f);
-    }
-    return ign;
-}
-
-__device__ __forceinline__ uint32_t target_bit(const MapDev &m, int r, int c)
-{
-    const uint32_t w = __ldg(&m.tgt[((r >> 5) * m.TW + (c >> 5)) * 32 + (r & 31)]);
-    return (w >> (c & 31)) & 1u;
-}
-
-constexpr uint8_t kBoUnburnt = 0, kBoMaxFuel = 250, kBoIgnite = 253,
-                  kBoBurnt = 254, kBoBlocked = 255;
-
-__global__ void __launch_bounds__(256) k_burnout(BurnLaunch a)
-{
-    __shared__ double beta[5];
-    __shared__ ScreenParams sp;
-    __shared__ uint32_t key0, key1;
-    __shared__ int sim, skip, r0, r1, c0, c1, nr0, nr1, nc0, nc1;
-    __shared__ unsigned nburn, burnt, inter, trials, status;
-    const MapDev &m = a.map;
-    const int H = m.H, W = m.W;
-    const long long HW = (long long)H * W;
-    uint8_t *st = a.state + (size_t)blockIdx.x * HW;
-    const unsigned long long hard_cap = (unsigned long long)(HW + 2) * 256ull;
-
-    for (;;) {
-        if (threadIdx.x == 0) {
-            const uint32_t w = atomicAdd(a.work_counter, 1u);
-            sim = w < (uint32_t)a.n ? (int)w : a.n;
-        }
-        __syncthreads();
-        const int s = sim;
-        if (s >= a.n) break;
-        if (threadIdx.x == 0) {
-            const fire_params P = a.params[s];
-            for (int j = 0; j < 5; ++j) beta[j] = P.b[j];
-            sp = screen_params(P.b);
-            const uint64_t seed = a.seeds[s];
-            key0 = (uint32_t)seed;
-            key1 = (uint32_t)(seed >> 32);
-            const fire_cell g = a.ign[s];
-            const bool ok = g.row >= 0 && g.row < H && g.col >= 0 && g.col < W &&
-                            (m.cfl[(long long)g.row * W + g.col] & kFlagBurnable);
-            skip = ok ? 0 : 1;
-            status = ok ? 0u : FIRE_STATUS_BAD_IGNITION;
-            burnt = inter = trials = 0;
-            r0 = r1 = g.row;
-            c0 = c1 = g.col;
-        }
-        for (long long i = threadIdx.x; i < HW; i += blockDim.x) {
-            const bool b = (__ldg(&m.cfl[i]) & kFlagBurnable) != 0;
-            st[i] = b ? kBoUnburnt : kBoBlocked;
-            if (a.burn_step) a.burn_step[(long long)s * HW + i] = b ? -1 : -2;
-        }
-        __syncthreads();
-        uint32_t t = 0;
-        bool capped = false;
-        if (!skip) {
-            if (threadIdx.x == 0) {
-                const long long gi = (long long)r0 * W + c0;
-                const uint8_t b = __ldg(&a.burn_time[gi]);
-                st[gi] = b < 1 ? 1 : (b > kBoMaxFuel ? kBoMaxFuel : b);
-                burnt = 1;
-                inter = target_bit(m, r0, c0);
-                if (r0 == 0 || r0 == H - 1 || c0 == 0 || c0 == W - 1)
-                    status |= FIRE_STATUS_BORDER;
-                if (a.burn_step) a.burn_step[(long long)s * HW + gi] = 0;
-            }
-            __syncthreads();
-            for (;;) {
-                if (a.max_steps && t >= a.max_steps) {
-                    capped = true;
-                    break;
-                }
-                if (t > hard_cap) {
-                    if (threadIdx.x == 0) status |= FIRE_STATUS_TIMEOUT;
-                    break;
-                }
-                const int R0 = max(r0 - 1, 0), R1 = min(r1 + 1, H - 1);
-                const int C0 = max(c0 - 1, 0), C1 = min(c1 + 1, W - 1);
-                const int rw = C1 - C0 + 1;
-                const long long cnt = (long long)(R1 - R0 + 1) * rw;
-                // (1) trials
-                unsigned my_trials = 0;
-                for (long long q = threadIdx.x; q < cnt; q += blockDim.x) {
-                    const int r = R0 + (int)(q / rw), c = C0 + (int)(q % rw);
-                    const long long i = (long long)r * W + c;
-                    if (st[i] != kBoUnburnt) continue;
-                    uint32_t dm = 0;
-                    for (int d = 0; d < 8; ++d) {
-                        const int sr = r - kDR[d], sc = c - kDC[d];
-                        if (sr < 0 || sr >= H || sc < 0 || sc >= W) continue;
-                        const uint8_t v = st[(long long)sr * W + sc];
-                        if (v >= 1 && v <= kBoMaxFuel) dm |= 1u << d;
-                    }
-                    if (!dm) continue;
-                    my_trials += __popc(dm);
-                    if (burnout_decide(m, sp, beta, key0, key1, (uint32_t)i, dm, t))
-                        st[i] = kBoIgnite;
-                }
-                my_trials = __reduce_add_sync(kFull, my_trials);
-                if ((threadIdx.x & 31) == 0 && my_trials) atomicAdd(&trials, my_trials);
-                if (threadIdx.x == 0) {
-                    nr0 = nc0 = 0x7fffffff;
-                    nr1 = nc1 = -1;
-                    nburn = 0;
-                }
-                __syncthreads();
-                // (2) fuel and new cells
-                int lr0 = 0x7fffffff, lr1 = -1, lc0 = 0x7fffffff, lc1 = -1;
-                unsigned lb = 0, lnew = 0, lint = 0, lst = 0;
-                for (long long q = threadIdx.x; q < cnt; q += blockDim.x) {
-                    const int r = R0 + (int)(q / rw), c = C0 + (int)(q % rw);
-                    const long long i = (long long)r * W + c;
-                    uint8_t v = st[i];
-                    if (v >= 1 && v <= kBoMaxFuel) {
-                        v = v - 1;
-                        st[i] = v == 0 ? kBoBurnt : v;
-                        if (v == 0) continue;
-                    } else if (v == kBoIgnite) {
-                        const uint8_t b = __ldg(&a.burn_time[i]);
-                        st[i] = b < 1 ? 1 : (b > kBoMaxFuel ? kBoMaxFuel : b);
-                        lnew++;
-                        lint += target_bit(m, r, c);
-                        if (r == 0 || r == H - 1 || c == 0 || c == W - 1)
-                            lst |= FIRE_STATUS_BORDER;
-                        if (a.burn_step)
-                            a.burn_step[(long long)s * HW + i] = (int32_t)(t + 1);
-                    } else {
-                        continue;
-                    }
-                    lb++;
-                    lr0 = min(lr0, r);
-                    lr1 = max(lr1, r);
-                    lc0 = min(lc0, c);
-                    lc1 = max(lc1, c);
-                }
-                lb = __reduce_add_sync(kFull, lb);
-                lnew = __reduce_add_sync(kFull, lnew);
-                lint = __reduce_add_sync(kFull, lint);
-                lst = __reduce_or_sync(kFull, lst);
-                lr0 = __reduce_min_sync(kFull, lr0);
-                lc0 = __reduce_min_sync(kFull, lc0);
-                lr1 = __reduce_max_sync(kFull, lr1);
-                lc1 = __reduce_max_sync(kFull, lc1);
-                if ((threadIdx.x & 31) == 0 && lb) {
-                    atomicAdd(&nburn, lb);
-                    atomicAdd(&burnt, lnew);
-                    atomicAdd(&inter, lint);
-                    atomicOr(&status, lst);
-                    atomicMin(&nr0, lr0);
-                    atomicMax(&nr1, lr1);
-                    atomicMin(&nc0, lc0);
-                    atomicMax(&nc1, lc1);
-                }
-                __syncthreads();
-                ++t;
-                if (nburn == 0) break;
-                if (threadIdx.x == 0) {
-                    r0 = nr0;
-                    r1 = nr1;
-                    c0 = nc0;
-                    c1 = nc1;
-                }
-                __syncthreads();
-            }
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            fire_result r;
-            r.burnt = burnt;
-            r.inter = inter;
-            r.target = *m.tgt_count;
-            r.steps = t;
-            r.status = status | (capped ? FIRE_STATUS_STEP_CAP : 0u);
-            r.trials = trials;
-            a.out[s] = r;
-        }
-        __syncthreads();
     }
 }
 
@@ -1291,23 +1155,29 @@ cudaError_t launch_target(const MapDev &m, const uint8_t *burnt, uint32_t *tgt,
 
 const void *simulate_kernel_ptr(bool smem_state)
 {
-    return smem_state ? (const void *)k_simulate<true>
-                      : (const void *)k_simulate<false>;
+    return smem_state ? (const void *)k_simulate<true, false>
+                      : (const void *)k_simulate<false, false>;
+}
+
+const void *simulate_burn_kernel_ptr()
+{
+    return (const void *)k_simulate<false, true>;
 }
 
 cudaError_t launch_simulate(const SimLaunch &a, bool smem_state, int nwarps,
                             int grid, size_t smem_bytes, cudaStream_t st)
 {
     if (smem_state)
-        k_simulate<true><<<grid, nwarps * 32, smem_bytes, st>>>(a);
+        k_simulate<true, false><<<grid, nwarps * 32, smem_bytes, st>>>(a);
     else
-        k_simulate<false><<<grid, nwarps * 32, smem_bytes, st>>>(a);
+        k_simulate<false, false><<<grid, nwarps * 32, smem_bytes, st>>>(a);
     return cudaGetLastError();
 }
 
-cudaError_t launch_burnout(const BurnLaunch &a, int grid, cudaStream_t st)
+cudaError_t launch_simulate_burn(const SimLaunch &a, int nwarps, int grid,
+                                 size_t smem_bytes, cudaStream_t st)
 {
-    k_burnout<<<grid, 256, 0, st>>>(a);
+    k_simulate<false, true><<<grid, nwarps * 32, smem_bytes, st>>>(a);
     return cudaGetLastError();
 }
 

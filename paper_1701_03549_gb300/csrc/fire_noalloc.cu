@@ -188,6 +188,8 @@ extern "C" int fire_simulate_batch_noalloc(fire_ctx *ctx, const fire_map *m,
     a.error_word = counters + 1;
     a.gstate = reinterpret_cast<uint32_t *>(static_cast<char *>(scratch) +
                                             kCounterBytes);
+    a.block_words = 0;
+    a.burn_time = nullptr;
     a.max_steps = max_steps;
     a.qcap = plan.qcap;
     a.cell_uniform = (flags & FIRE_CELL_UNIFORM) ? 1 : 0;

@@ -84,7 +84,7 @@ def test_kernels_compile_for_sm103a_with_little_spilling():
             seen += 1
             spill = int(re.search(r"(\d+) bytes spill stores", block).group(1))
             assert spill <= 64, block
-    assert seen == 2
+    assert seen == 3    # shared / global state, and the burn-time variant
 
 
 def test_tile_row_division_by_magic_multiply():

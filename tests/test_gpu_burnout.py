@@ -115,3 +115,68 @@ def test_cap_status_and_errors(ctx, oracle_mod):
                        torch.tensor(bt, device=dev), device=True, out=out,
                        sync=True)
     assert fire.results_view(out)[0]["status"] & fire.STATUS_BAD_IGNITION
+
+
+def test_per_cell_times_across_tiles(ctx, oracle_mod):
+    """Per-cell burn times 1..12 on a 130 x 161 map (5 x 6 tiles, ragged
+    last row and column): fires started on tile corners and edges keep
+    cells burning across tile boundaries for many steps; results and
+    burn-step maps against the oracle, also under a launch shape with more
+    blocks per SM and a small candidate queue (overflow path)."""
+    import oracle
+
+    L = synth.landscape(130, 161, seed=21, wind_seed=21)
+    rng = np.random.default_rng(5)
+    bt = rng.integers(1, 13, L.veg.shape).astype(np.uint8)
+    starts = [(31, 31), (32, 63), (64, 0), (95, 160), (129, 96), (0, 127)]
+    for r, c in starts:
+        L.veg[r, c] = 2
+    tgt = rng.random(L.veg.shape) < 0.3
+    m = ctx.landscape_upload(L)
+    m.target_upload(tgt)
+    n = len(starts) * 2
+    beta = np.array([[0.5, -1.0, 0.5, 1.5, -0.5], [-1.5, 0.0, 0.5, 2.5, 1.0]]
+                    * len(starts))
+    ign = np.array([s for s in starts for _ in range(2)], np.int32)
+    seeds = np.arange(77, 77 + n, dtype=np.uint64)
+    F = oracle.Features(L)
+    want = [F.simulate(beta[i], tuple(ign[i]), int(seeds[i]), target=tgt,
+                       burn_time=bt) for i in range(n)]
+    for shape in ((0, 0, 0, 0), (2, 12, 64, 0)):
+        ctx.set_launch(*shape)
+        try:
+            res, bs = m.simulate_burnout(beta, ign, seeds, bt, want_steps=True)
+        finally:
+            ctx.set_launch(0, 0)
+        for i, (r, b) in enumerate(want):
+            for k in r:
+                assert int(res[i][k]) == r[k], (shape, i, k)
+            assert np.array_equal(bs[i], b), (shape, i)
+    assert max(r["steps"] for r, _ in want) > 40
+
+
+def test_long_burn_times(ctx, oracle_mod):
+    """Burn times up to the largest accepted (250) on a small map: cells keep
+    trying their neighbours for hundreds of steps; step cap on such a fire."""
+    import oracle
+
+    L = synth.landscape(40, 48, seed=22, wind_seed=22)
+    g = synth.centre_ignition(L.veg)
+    L.veg[g] = 1                       # the ignition cell burns 250 steps
+    bt = np.where(L.veg == 1, 250, 37).astype(np.uint8)
+    m = ctx.landscape_upload(L)
+    beta = np.array([[-4.0, 1.0, 0.0, 0.5, 0.0], [-3.0, -1.0, 0.5, 1.0, 0.0]])
+    ign = np.tile(np.array(g, np.int32), (2, 1))
+    seeds = np.array([3, 4], np.uint64)
+    F = oracle.Features(L)
+    for cap in (0, 120):
+        res, bs = m.simulate_burnout(beta, ign, seeds, bt, want_steps=True,
+                                     max_steps=cap)
+        for i in range(2):
+            r, b = F.simulate(beta[i], tuple(ign[i]), int(seeds[i]),
+                              burn_time=bt, max_steps=cap)
+            for k in r:
+                assert int(res[i][k]) == r[k], (cap, i, k)
+            assert np.array_equal(bs[i], b), (cap, i)
+            if cap == 0:
+                assert r["steps"] >= 250
