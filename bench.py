@@ -1081,6 +1081,11 @@ def run_burnout(args):
     sd = torch.tensor(wl.seeds.view(np.int64), device=dev)
     out = torch.zeros((SIMS, 6), dtype=torch.int32, device=dev)
     ones = torch.ones(wl.land.veg.shape, dtype=torch.uint8, device=dev)
+    # the same times with a 2 on one non-burnable cell: the burn-time kernel
+    # runs (a batch of ones goes to the plain kernel) with the same fires
+    nb = np.argwhere(wl.land.veg == 0)[0]
+    ones_k = ones.clone()
+    ones_k[int(nb[0]), int(nb[1])] = 2
     fuel = torch.tensor(np.asarray((1, 3, 1, 2, 4), np.uint8)[
         np.minimum(wl.land.veg, 4)], device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
@@ -1088,6 +1093,8 @@ def run_burnout(args):
         "batch": lambda: m.simulate_batch(p, gi, sd, device=True, out=out),
         "burn_1": lambda: m.simulate_burnout(p, gi, sd, ones, device=True,
                                              out=out),
+        "burn_1_in_burn_kernel": lambda: m.simulate_burnout(
+            p, gi, sd, ones_k, device=True, out=out),
         "burn_per_fuel": lambda: m.simulate_burnout(p, gi, sd, fuel,
                                                     device=True, out=out),
     }
@@ -1125,8 +1132,10 @@ def run_burnout(args):
                        "state_mode")}},
         "calls": res,
         "burn_1_over_batch": res["burn_1"]["ms"] / res["batch"]["ms"],
+        "burn_kernel_1_over_batch": (res["burn_1_in_burn_kernel"]["ms"] /
+                                     res["batch"]["ms"]),
         "cpu_baseline": None, "e2e": None,
-        "gpu_launches": args.steps * 3, "clocks": ck}
+        "gpu_launches": args.steps * 4, "clocks": ck}
     if rank == 0:
         print(json.dumps(line))
     m.free()

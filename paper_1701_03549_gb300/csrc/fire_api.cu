@@ -110,7 +110,14 @@ int plan_launch(fire_ctx *ctx, int ntiles, long long n, LaunchPlan *p, bool burn
     nwarps = std::min(nwarps, kSimMaxThreads / 32);
     int qcap = queue > 0 ? queue : 4096;
     SimLayout L = sim_layout(ntiles, qcap, true);
-    // the burn-time variant keeps its state in global memory
+    // the burn-time variant keeps its state in global memory; a shape tuned
+    // for shared-memory state gives way to the global-state shape that is
+    // fastest on the plain kernel's benchmarks (4 warps x 8 blocks per SM)
+    if (burn && !override && state != FIRE_STATE_GLOBAL) {
+        nwarps = 4;
+        bps = 8;
+        qcap = queue = 3072;
+    }
     if (burn) state = FIRE_STATE_GLOBAL;
     bool smem_state = state == FIRE_STATE_SHARED ||
                       (state == FIRE_STATE_AUTO && L.total <= ctx->max_smem_optin);
@@ -202,6 +209,7 @@ void fire_destroy(fire_ctx *ctx)
     if (ctx->counter) cudaFree(ctx->counter);
     if (ctx->staging) cudaFree(ctx->staging);
     if (ctx->gstate) cudaFree(ctx->gstate);
+    if (ctx->burn_aux) cudaFree(ctx->burn_aux);
     if (ctx->host_pinned) cudaFreeHost(ctx->host_pinned);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
@@ -495,6 +503,7 @@ int launch_batch(fire_ctx *ctx, const fire_map *m, int n,
     a.gstate = ctx->gstate;
     a.block_words = 0;
     a.burn_time = nullptr;
+    a.long_burn = nullptr;
     a.error_word = ctx->counter + 1;
     a.max_steps = max_steps;
     a.qcap = plan.qcap;

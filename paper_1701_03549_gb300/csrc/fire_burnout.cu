@@ -95,6 +95,44 @@ extern "C" int fire_simulate_burnout(fire_ctx *ctx, const fire_map *m, int n,
         dout = (fire_result *)(p + bp + bi + bs + bb);
         if (want_steps) dsteps = (int32_t *)(p + bp + bi + bs + bb + bo);
     }
+    // cells that burn two steps or more: with none, the batch is the plain
+    // rule of fire_simulate_batch and runs its kernel (the same fires)
+    const size_t nwords = (size_t)m->dev.ntiles * 32;
+    rc = grow_device(ctx, &ctx->burn_aux, &ctx->burn_aux_bytes, nwords * 4 + 16,
+                     "long-burn plane");
+    if (rc) {
+        if (tmp) cudaFree(tmp);
+        return rc;
+    }
+    uint32_t *dlong = (uint32_t *)ctx->burn_aux;
+    uint32_t *dany = dlong + nwords;
+    uint32_t hany = 0;
+    cudaError_t e0 = launch_long_burn(m->dev, db, dlong, dany, ctx->stream);
+    if (e0 == cudaSuccess)
+        e0 = cudaMemcpyAsync(&hany, dany, 4, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e0 == cudaSuccess) e0 = cudaStreamSynchronize(ctx->stream);
+    if (e0 != cudaSuccess) {
+        if (tmp) cudaFree(tmp);
+        return cuda_err(ctx, e0, "long-burn plane");
+    }
+    if (!hany) {
+        rc = launch_batch(ctx, m, n, dp, di, ds, max_steps, 0u, dout, dsteps,
+                          nullptr);
+        cudaError_t e = cudaSuccess;
+        if (!rc && !dev) {
+            e = cudaMemcpyAsync(out, dout, (size_t)n * sizeof(fire_result),
+                                cudaMemcpyDeviceToHost, ctx->stream);
+            if (e == cudaSuccess && want_steps)
+                e = cudaMemcpyAsync(burn_step, dsteps, (size_t)n * HW * 4,
+                                    cudaMemcpyDeviceToHost, ctx->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+        }
+        if (tmp) cudaFree(tmp);
+        if (rc) return rc;
+        if (e != cudaSuccess) return cuda_err(ctx, e, "burn-out results");
+        if (!dev || (flags & FIRE_SYNC)) return fire_sync(ctx);
+        return FIRE_OK;
+    }
     // the bit-plane simulation kernel with burn times: state, two "still
     // burning" planes and a fuel byte per cell in each block's global buffer
     LaunchPlan plan;
@@ -125,6 +163,7 @@ extern "C" int fire_simulate_burnout(fire_ctx *ctx, const fire_map *m, int n,
     a.gstate = ctx->gstate;
     a.block_words = words;
     a.burn_time = db;
+    a.long_burn = dlong;
     a.error_word = ctx->counter + 1;
     a.max_steps = max_steps;
     a.qcap = plan.qcap;

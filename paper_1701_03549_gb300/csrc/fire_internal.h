@@ -59,6 +59,9 @@ struct SimLaunch {
                                // (1..250, others clamped); its blocks keep X, Y,
                                // two "still burning" planes and one fuel byte
                                // per cell in their global state
+    const uint32_t *long_burn; // burn-time variant: tile-major bit plane of the
+                               // cells that burn 2 steps or more (only these
+                               // keep a fuel count)
     uint32_t *error_word;      // set nonzero when a bounded wait runs out
     uint32_t max_steps;        // 0 = no cap
     int qcap;                  // candidate-queue capacity (entries)
@@ -136,6 +139,10 @@ cudaError_t launch_simulate(const SimLaunch &a, bool smem_state, int nwarps,
 // The burn-time variant (global-memory state only).
 cudaError_t launch_simulate_burn(const SimLaunch &a, int nwarps, int grid,
                                  size_t smem_bytes, cudaStream_t st);
+// Tile-major bit plane of the cells whose burn time is 2 or more, and a flag
+// set when there is any (zeroed by the launcher).
+cudaError_t launch_long_burn(const MapDev &m, const uint8_t *burn_time,
+                             uint32_t *plane, uint32_t *any, cudaStream_t st);
 // Words of one block's global state in the burn-time variant.
 inline size_t burn_block_words(int ntiles, long long HW)
 {
@@ -219,6 +226,8 @@ struct fire_ctx {
     std::vector<GraphEntry> graphs;  // captured calls
     unsigned epoch = 0;              // bumped when a device buffer moves
     int fail_alloc_after = -1;       // test hook: fail that growth (-1: off)
+    void *burn_aux = nullptr;        // burn-time calls: long-burn plane + flag
+    size_t burn_aux_bytes = 0;
 };
 
 struct fire_map {

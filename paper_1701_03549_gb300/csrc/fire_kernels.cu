@@ -121,6 +121,25 @@ __global__ void k_pack_bits(int H, int W, int TW, int nwords,
     }
 }
 
+// Tile-major bit plane of the cells that burn two steps or more.
+__global__ void k_long_burn(int H, int W, int TW, int nwords,
+                            const uint8_t *__restrict__ bt,
+                            uint32_t *__restrict__ dst, uint32_t *__restrict__ any)
+{
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= nwords) return;
+    const int k = w >> 5, r = w & 31;
+    const int ti = k / TW, tj = k - ti * TW;
+    const int R = ti * 32 + r;
+    uint32_t word = 0;
+    for (int i = 0; i < 32; ++i) {
+        const int C = tj * 32 + i;
+        if (R < H && C < W && bt[(long long)R * W + C] >= 2) word |= 1u << i;
+    }
+    dst[w] = word;
+    if (word) *any = 1u;
+}
+
 // ---------------------------------------------------------------------------
 // Simulation kernel helpers.
 
@@ -339,7 +358,11 @@ __device__ __forceinline__ void ignite(const SimCtx &s, int k, int ti, int tj,
     const MapDev &m = *s.map;
     uint32_t *P = (t & 1u) ? s.X : s.Y;
     atomicOr(&P[k * 32 + r], 1u << i);
-    if (kBurn) s.fuel[cell] = burn_steps(*s.a, cell);
+    if (kBurn) {
+        // only cells that burn two steps or more keep a fuel count
+        const uint8_t f = burn_steps(*s.a, cell);
+        if (f > 1) s.fuel[cell] = f;
+    }
     if (s.a->burn_step)
         s.a->burn_step[(long long)s.sim * m.H * m.W + cell] = (int32_t)(t + 1);
     const uint32_t tn = t + 1;
@@ -450,7 +473,7 @@ __device__ __forceinline__ void phase_a(const SimCtx &s, int k, uint32_t t,
         // for this tile's rows only by this warp; a tile holding such cells
         // is on the next worklist, and so is a neighbour tile across an edge
         // they lie on)
-        uint32_t cont = 0, mm = b;
+        uint32_t cont = 0, mm = b & __ldg(&a.long_burn[w]);
         const uint32_t rowc = (uint32_t)(ti * 32 + lane) * (uint32_t)m.W +
                               (uint32_t)(tj * 32);
         while (mm) {
@@ -717,7 +740,8 @@ __global__ void __launch_bounds__(kSimMaxThreads, 2) k_simulate(SimLaunch a)
                 s.X[k0 * 32 + r0] |= 1u << i0;   // burning, parity 0
                 if (kBurn) {
                     const uint32_t c0 = (uint32_t)g.row * (uint32_t)m.W + (uint32_t)g.col;
-                    s.fuel[c0] = burn_steps(a, c0);
+                    const uint8_t f = burn_steps(a, c0);
+                    if (f > 1) s.fuel[c0] = f;
                 }
                 if (a.burn_step)
                     a.burn_step[(long long)sim * HW + (long long)g.row * m.W +
@@ -1171,6 +1195,17 @@ cudaError_t launch_simulate(const SimLaunch &a, bool smem_state, int nwarps,
         k_simulate<true, false><<<grid, nwarps * 32, smem_bytes, st>>>(a);
     else
         k_simulate<false, false><<<grid, nwarps * 32, smem_bytes, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_long_burn(const MapDev &m, const uint8_t *burn_time,
+                             uint32_t *plane, uint32_t *any, cudaStream_t st)
+{
+    const int nw = m.ntiles * 32;
+    cudaError_t e = cudaMemsetAsync(any, 0, sizeof(uint32_t), st);
+    if (e != cudaSuccess) return e;
+    k_long_burn<<<(nw + 255) / 256, 256, 0, st>>>(m.H, m.W, m.TW, nw, burn_time,
+                                                 plane, any);
     return cudaGetLastError();
 }
 

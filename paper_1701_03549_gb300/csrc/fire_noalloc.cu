@@ -190,6 +190,7 @@ extern "C" int fire_simulate_batch_noalloc(fire_ctx *ctx, const fire_map *m,
                                             kCounterBytes);
     a.block_words = 0;
     a.burn_time = nullptr;
+    a.long_burn = nullptr;
     a.max_steps = max_steps;
     a.qcap = plan.qcap;
     a.cell_uniform = (flags & FIRE_CELL_UNIFORM) ? 1 : 0;

@@ -1,7 +1,8 @@
 """Burn-out times on the GPU (fire_simulate_burnout) against the oracle.
 
 * burn_time = 1 everywhere: every result and burn-step map bit-identical to
-  fire_simulate_batch (the paper's rule, same keyed draws);
+  fire_simulate_batch (the paper's rule, same keyed draws), both when the call
+  hands the batch to the plain kernel and in the burn-time kernel itself;
 * per-fuel times: results and burn-step maps bit-identical to the oracle's
   burn-out simulation, host and device argument paths;
 * step cap, bad ignition status, and host-side rejection of a zero time.
@@ -41,10 +42,17 @@ def test_unit_times_equal_the_main_kernel(ctx):
     m = ctx.landscape_upload(L)
     beta, ign, seeds = _batch(L, 48, 1)
     r0, b0 = m.simulate_batch(beta, ign, seeds, want_steps=True)
-    r1, b1 = m.simulate_burnout(beta, ign, seeds,
-                                np.ones(L.veg.shape, np.uint8), want_steps=True)
+    ones = np.ones(L.veg.shape, np.uint8)
+    r1, b1 = m.simulate_burnout(beta, ign, seeds, ones, want_steps=True)
     assert np.array_equal(r0, r1)
     assert np.array_equal(b0, b1)
+    # the burn-time kernel itself (a time of 2 on one non-burnable cell makes
+    # the batch take it; every burnable cell still burns one step)
+    rows, cols = np.nonzero(L.veg == 0)
+    ones[rows[0], cols[0]] = 2
+    r2, b2 = m.simulate_burnout(beta, ign, seeds, ones, want_steps=True)
+    assert np.array_equal(r0, r2)
+    assert np.array_equal(b0, b2)
 
 
 @pytest.mark.parametrize("times", [(1, 3, 1, 2, 4), (1, 2, 2, 2, 2),
