@@ -1054,6 +1054,132 @@ def run_surrogate_step(args):
     return 0
 
 
+CROSSOVER_SIDES = (512, 1024, 2048, 4096)
+CROSSOVER_REPS = 16   # automaton runs per simulated candidate in the GAs
+
+
+def _crossover_side(sides, per_sim_ms, target_ms):
+    """Map side at which per-simulation time reaches target_ms: log-log
+    interpolation between the measured sides (None outside their range)."""
+    for k in range(len(sides) - 1):
+        a, b = per_sim_ms[k], per_sim_ms[k + 1]
+        if a <= target_ms <= b and b > a:
+            f = (np.log(target_ms) - np.log(a)) / (np.log(b) - np.log(a))
+            return float(np.exp(np.log(sides[k]) +
+                                f * (np.log(sides[k + 1]) - np.log(sides[k]))))
+    return None
+
+
+def run_crossover(args):
+    """Where the surrogate's screening becomes cheaper than the automaton runs
+    it replaces.  Per map side N (square synthetic landscapes, centre
+    ignition): the automaton's time per simulation over a batch of prior
+    draws Gauss(0, 5) (the screened GA's generation 0) and over the
+    reference parameters, one seed each, at one fixed launch shape (4 warps
+    x 8 blocks per SM, global state, longest-first order); and the
+    surrogate's time per candidate (inputs and forward pass at S = 256,
+    chunks of 64) on the same map.  All CUDA-event timed with the L2 flushed
+    before every timed call.  A forward pass replaces R automaton runs of
+    one candidate (R = 16 in the GAs here): the crossover side is where R
+    runs cost as much as one forward pass."""
+    g = _setup_gpu()
+    if g is None:
+        print(json.dumps({"metric": "surrogate crossover", "error": "no CUDA device"}))
+        return 1
+    torch, fire, ctx, dev, stream, rank, world, local = g
+    from paper_1701_03549_gb300 import surrogate
+
+    S, chunk, ncand = 256, 64, 256
+    sur = surrogate.Surrogate(ctx, S=S, max_batch=chunk)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    ctx.set_launch(4, 8, 3072, fire.STATE_GLOBAL)
+
+    def timed(fn, reps):
+        fn()                                   # warm-up (buffers, tables)
+        ms = []
+        for _ in range(reps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return statistics.median(ms)
+
+    rows = []
+    clocks = Clocks(local)
+    for N in CROSSOVER_SIDES:
+        land = synth.landscape(N, N, seed=31, wind_seed=31)
+        m = ctx.landscape_upload(land)
+        m.target_upload(np.zeros((N, N), np.uint8))
+        ign = np.asarray(synth.centre_ignition(land.veg), np.int32)
+        # enough simulations for several per block of the launch
+        n = 4096 if N <= 2048 else 2432
+        ign_dev = torch.tensor(np.tile(ign, (n, 1)), dtype=torch.int32, device=dev)
+        seeds = torch.arange(1, n + 1, dtype=torch.int64, device=dev)
+        out = torch.zeros((n, 6), dtype=torch.int32, device=dev)
+        row = {"side": N, "simulations": n}
+        for name, P in (("prior", surrogate.sample_params(n, 5)),
+                        ("reference", np.tile(synth.TRUTH_BETA, (n, 1)))):
+            p_dev = torch.tensor(P, dtype=torch.float64, device=dev)
+
+            def sim():
+                m.simulate_batch(p_dev, ign_dev, seeds, device=True, out=out,
+                                 longest_first=True)
+
+            ms = timed(sim, max(1, args.steps))
+            r = fire.results_view(out)
+            row[f"automaton_ms_per_sim_{name}"] = ms / n
+            row[f"mean_burnt_{name}"] = float(r["burnt"].astype(np.float64).mean())
+            row[f"mean_steps_{name}"] = float(r["steps"].astype(np.float64).mean())
+        planes = sur.planes(land)
+        cp = torch.tensor(surrogate.sample_params(ncand, 6), dtype=torch.float64,
+                          device=dev)
+        cg = torch.tensor(np.tile(ign, (ncand, 1)), dtype=torch.int32, device=dev)
+        ms = timed(lambda: sur.predict(planes, N, N, cp, cg, chunk=chunk),
+                   max(1, args.steps))
+        row["surrogate_ms_per_candidate"] = ms / ncand
+        for name in ("prior", "reference"):
+            row[f"forward_in_automaton_runs_{name}"] = (
+                row["surrogate_ms_per_candidate"] /
+                row[f"automaton_ms_per_sim_{name}"])
+        rows.append(row)
+        m.free()
+        del planes
+    ck = clocks.stop()
+    ctx.set_launch(0, 0, 0, 0)
+    F = statistics.median(r["surrogate_ms_per_candidate"] for r in rows)
+    cross = {}
+    for name in ("prior", "reference"):
+        per = [r[f"automaton_ms_per_sim_{name}"] for r in rows]
+        cross[name] = {
+            f"R={CROSSOVER_REPS}": _crossover_side(CROSSOVER_SIDES, per,
+                                                   F / CROSSOVER_REPS),
+            "R=1": _crossover_side(CROSSOVER_SIDES, per, F)}
+    if rank == 0:
+        print(json.dumps({
+            "metric": "map side where one surrogate forward pass costs as much "
+                      f"as the {CROSSOVER_REPS} automaton runs it replaces",
+            "value": cross["prior"][f"R={CROSSOVER_REPS}"], "unit": "cells",
+            "n_gpus": world, "steps": args.steps, "warmup": 1,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16 (surrogate), f32/f64 screen (automaton)",
+            "data": "synthetic",
+            "config": {"workload": "crossover: square maps "
+                       + ", ".join(f"{N}x{N}" for N in CROSSOVER_SIDES)
+                       + "; automaton batches of prior draws and of the "
+                       "reference parameters; surrogate S = 256, random "
+                       "weights (cost does not depend on them)",
+                       "l2": L2_NOTE},
+            "crossover_side": cross, "surrogate_ms_per_candidate_median": F,
+            "rows": rows, "clocks": ck, "cpu_baseline": None, "e2e": None}))
+    sur.net.free()
+    ctx.close()
+    return 0
+
+
 BURNOUT = ("burnout_512: the 512x512 GA generation (4096 simulations) with "
            "per-cell burn times: 1 everywhere (the paper's rule) and per fuel "
            "class (1, 3, 1, 2, 4) for classes 0..4, against fire_simulate_batch "
@@ -1305,14 +1431,15 @@ def main():
                          "reduced batch for profiling; not a headline line)")
     ap.add_argument("--workload",
                     choices=("uneven", "ga512", "recover", "burnout",
-                             "surrogate", "surrogate_step"),
+                             "surrogate", "surrogate_step", "crossover"),
                     default="uneven",
                     help="uneven (default): nine fires 200x300..2000x1500, "
                          "100k simulations in one launch; ga512: one "
                          "512x512 GA generation; recover: parameter "
                          "recovery of the GAs; surrogate: the "
                          "surrogate-screened GA against the plain GA; "
-                         "surrogate_step: the surrogate network alone")
+                         "surrogate_step: the surrogate network alone; "
+                         "crossover: map side where screening pays")
     ap.add_argument("--generations", type=int, default=50)
     ap.add_argument("--train-steps", type=int, default=1500)
     ap.add_argument("--train-groups", type=int, default=6250)
@@ -1336,6 +1463,8 @@ def main():
         return run_surrogate(args)
     if args.workload == "surrogate_step":
         return run_surrogate_step(args)
+    if args.workload == "crossover":
+        return run_crossover(args)
     return run_uneven(args)
 
 

@@ -142,3 +142,14 @@ def test_recovery_errors_and_times():
     assert rec == 3.5 and per == [3.5] * 5
     rec, per = bench._time_to_recover(errs[:1], h.seconds[:1])
     assert rec is None and per == [None] * 5
+
+
+def test_crossover_side_interpolates_log_log():
+    """The crossover side is read off the measured per-simulation times by
+    straight-line interpolation in log(side) against log(time)."""
+    sides = (512, 1024, 2048)
+    per = (0.01, 0.04, 0.16)
+    assert bench._crossover_side(sides, per, 0.02) == pytest.approx(512 * 2 ** 0.5)
+    assert bench._crossover_side(sides, per, 0.04) == pytest.approx(1024)
+    assert bench._crossover_side(sides, per, 0.005) is None
+    assert bench._crossover_side(sides, per, 0.2) is None
