@@ -452,6 +452,19 @@ def _pinned(torch, a):
 # ---------------------------------------------------------------------------
 # Native arm, default step: the nine-fire uneven batch
 
+def _forced_launch(args, ctx):
+    """The launch shape given by --launch W,B,Q,S (warps per block, blocks
+    per SM, queue entries, state mode), set on the context in place of the
+    autotuner's pick (profiling a reduced batch in the shape the full batch
+    runs in); None without the option."""
+    if not args.launch:
+        return None
+    w, b, q, st = (int(v) for v in args.launch.split(","))
+    ctx.set_launch(w, b, q, st)
+    return {"warps_per_block": w, "blocks_per_sm": b, "queue_entries": q,
+            "state_mode": st, "ms": None, "forced": True}
+
+
 def run_uneven(args):
     """One fire_simulate_multi call per step (CUDA-graph replay of the
     ordering kernels and the persistent simulation launch) plus the fitness
@@ -480,8 +493,10 @@ def run_uneven(args):
     # launch shape: the autotuner times its candidates on a stratified tenth
     # of the batch (outside the timed region) and the library keeps the best
     sub = np.arange(0, n, 10)
-    tuned = fire.fire_autotune(ctx, maps, wl.map_of_sim[sub], wl.params[sub],
-                               wl.ignitions[sub], wl.seeds[sub])
+    tuned = _forced_launch(args, ctx)
+    if tuned is None:
+        tuned = fire.fire_autotune(ctx, maps, wl.map_of_sim[sub], wl.params[sub],
+                                   wl.ignitions[sub], wl.seeds[sub])
     t_mi = torch.tensor(wl.map_of_sim, device=dev)
     t_p = torch.tensor(wl.params, dtype=torch.float64, device=dev)
     t_g = torch.tensor(wl.ignitions, device=dev)
@@ -589,7 +604,8 @@ def run_uneven(args):
                 {"sample_every": args.sample, "sims_per_step": n}
                 if args.sample > 1 else {})),
             "launch": {k: tuned[k] for k in ("warps_per_block", "blocks_per_sm",
-                                             "queue_entries", "state_mode")},
+                                             "queue_entries", "state_mode",
+                                             "forced") if k in tuned},
             "target_seeds": tseeds,
             "cell_updates_per_s": cells_all / total_s,
             "cell_updates_vs_dense_sweep": _dense_sweep_roof(
@@ -647,8 +663,10 @@ def run_ga512(args):
     # the autotuner times its candidate shapes on this batch in the step's
     # longest-first order (outside the timed region); the library keeps the
     # fastest
-    tuned = fire.fire_autotune(ctx, [m], None, wl.params, wl.ignitions,
-                               wl.seeds, longest_first=True)
+    tuned = _forced_launch(args, ctx)
+    if tuned is None:
+        tuned = fire.fire_autotune(ctx, [m], None, wl.params, wl.ignitions,
+                                   wl.seeds, longest_first=True)
     p_dev = torch.tensor(wl.params, dtype=torch.float64, device=dev)
     g_dev = torch.tensor(wl.ignitions, dtype=torch.int32, device=dev)
     seeds_host = [wl.seeds + np.uint64(k * nsim) for k in range(nsteps)]
@@ -751,7 +769,8 @@ def run_ga512(args):
                 {"sample_every": args.sample, "sims_per_step": nsim}
                 if args.sample > 1 else {})),
             "launch": {k: tuned[k] for k in ("warps_per_block", "blocks_per_sm",
-                                             "queue_entries", "state_mode")},
+                                             "queue_entries", "state_mode",
+                                             "forced") if k in tuned},
             "target_seed": int(tseed), "target_cells": int(target.sum()),
             "cell_updates_per_s": steps_all * H * W / total_s,
             "cell_updates_vs_dense_sweep": _dense_sweep_roof(
@@ -1440,6 +1459,11 @@ def main():
                          "surrogate-screened GA against the plain GA; "
                          "surrogate_step: the surrogate network alone; "
                          "crossover: map side where screening pays")
+    ap.add_argument("--launch", default="",
+                    help="W,B,Q,S: force the simulation launch shape (warps "
+                         "per block, blocks per SM, queue entries, state "
+                         "mode 1 shared / 2 global) instead of autotuning "
+                         "(uneven and ga512; for profiling)")
     ap.add_argument("--generations", type=int, default=50)
     ap.add_argument("--train-steps", type=int, default=1500)
     ap.add_argument("--train-groups", type=int, default=6250)
