@@ -47,6 +47,43 @@ __device__ __forceinline__ uint4 philox4x32_10(uint32_t x0, uint32_t x1,
     return make_uint4(x0, x1, x2, x3);
 }
 
+// The same block function with the key schedule precomputed: rk[j] holds the
+// round keys (k0 + 2j W0, k1 + 2j W1) in .x, .y and those of round 2j + 1 in
+// .z, .w.  Every trial of one simulation uses the same key, so the schedule
+// is computed once per simulation instead of once per block.
+__device__ __forceinline__ uint4 philox4x32_10_rk(uint32_t x0, uint32_t x1,
+                                                  uint32_t x2, uint32_t x3,
+                                                  const uint4 *rk)
+{
+#pragma unroll
+    for (int j = 0; j < 5; ++j) {
+        const uint4 k = rk[j];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const uint32_t k0 = h ? k.z : k.x, k1 = h ? k.w : k.y;
+            const uint32_t lo0 = kPhiloxM0 * x0;
+            const uint32_t hi0 = __umulhi(kPhiloxM0, x0);
+            const uint32_t lo1 = kPhiloxM1 * x2;
+            const uint32_t hi1 = __umulhi(kPhiloxM1, x2);
+            const uint32_t n0 = hi1 ^ x1 ^ k0;
+            const uint32_t n2 = hi0 ^ x3 ^ k1;
+            x0 = n0; x1 = lo1; x2 = n2; x3 = lo0;
+        }
+    }
+    return make_uint4(x0, x1, x2, x3);
+}
+
+// Round keys of philox4x32_10_rk for the key (k0, k1).
+__host__ __device__ inline void philox_round_keys(uint32_t k0, uint32_t k1,
+                                                  uint4 rk[5])
+{
+    for (uint32_t j = 0; j < 5; ++j) {
+        const uint32_t r0 = 2u * j, r1 = 2u * j + 1u;
+        rk[j] = make_uint4(k0 + r0 * kPhiloxW0, k1 + r0 * kPhiloxW1,
+                           k0 + r1 * kPhiloxW0, k1 + r1 * kPhiloxW1);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Double-precision exp on |x| <= 40: x = k ln2 + r, |r| <= ln2/2, Taylor
 // series of e^r to degree 13, times 2^k.  ln2 is split into a 40-bit head

@@ -77,6 +77,7 @@ constexpr uint16_t kFlagBurnable = 1u << 9;
 
 // Per-simulation shared state of the simulation kernel's block.
 struct SimShared {
+    uint4 rk[5];          // Philox round keys: (k0, k1) of round 2j, then 2j + 1
     double beta[5];
     ScreenParams sp;
     uint32_t key0, key1;

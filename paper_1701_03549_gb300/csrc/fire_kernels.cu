@@ -326,7 +326,7 @@ __device__ __forceinline__ bool trial_cell(const SimCtx &s, uint32_t cell,
             const float p = screen_p(screen_z(sc, b3, (up >> d) & 1u, d));
             q = __fmul_rn(q, __fsub_rn(1.0f, p));
         }
-        const uint32_t u = philox4x32_10(cell, t, 2u, 0u, sh.key0, sh.key1).x;
+        const uint32_t u = philox4x32_10_rk(cell, t, 2u, 0u, sh.rk).x;
         int dec = screen_decide(__fsub_rn(1.0f, q), u, sh.sp.cell_margin);
         if (dec < 0) dec = exact_cell_decide(sh.beta, forest, f, up, dm, u);
         return dec != 0;
@@ -341,7 +341,7 @@ __device__ __forceinline__ bool trial_cell(const SimCtx &s, uint32_t cell,
         const uint32_t half = first ^ k;
         const uint32_t m4 = half ? hi : lo;
         if (!m4) continue;
-        const uint4 u = philox4x32_10(cell, t, half, 0u, sh.key0, sh.key1);
+        const uint4 u = philox4x32_10_rk(cell, t, half, 0u, sh.rk);
         ign = test_dirs(m4, (int)(half * 4), u, sc, b3, sh.sp.margin, up,
                         sh.beta, forest, f);
     }
@@ -656,6 +656,7 @@ __global__ void __launch_bounds__(kSimMaxThreads, 2) k_simulate(SimLaunch a)
             const uint64_t seed = a.seeds[sim];
             sh.key0 = (uint32_t)seed;
             sh.key1 = (uint32_t)(seed >> 32);
+            philox_round_keys(sh.key0, sh.key1, sh.rk);
             const fire_cell g = a.ign[sim];
             const bool ok = map_ok && g.row >= 0 && g.row < m.H &&
                             g.col >= 0 && g.col < m.W &&
@@ -1079,12 +1080,17 @@ __global__ void k_screen_selftest(uint64_t n, uint64_t seed,
         atomicMax(max_dp_bits, (unsigned long long)__double_as_longlong(local_max));
 }
 
+// Philox blocks as the simulation draws them (the precomputed key schedule
+// of philox4x32_10_rk).
 __global__ void k_philox_blocks(uint64_t n, uint4 ctr, uint2 key, uint32_t *out)
 {
+    __shared__ uint4 rk[5];
+    if (threadIdx.x == 0) philox_round_keys(key.x, key.y, rk);
+    __syncthreads();
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
          i += (uint64_t)gridDim.x * blockDim.x) {
-        const uint4 r = philox4x32_10(ctr.x + (uint32_t)i, ctr.y, ctr.z, ctr.w,
-                                      key.x, key.y);
+        const uint4 r = philox4x32_10_rk(ctr.x + (uint32_t)i, ctr.y, ctr.z, ctr.w,
+                                         rk);
         reinterpret_cast<uint4 *>(out)[i] = r;
     }
 }
