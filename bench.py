@@ -800,6 +800,151 @@ def run_ga512(args):
     return 0
 
 
+IGNITION = ("ignition_search_1024: 1024x1024 map (spatially varying wind), "
+            "target from the reference parameters at the centre ignition; "
+            "32x32 candidate ignitions over the target's bounding box, "
+            "snapped to burnt cells, x 64 replicates = 65,536 simulations, "
+            "the reference parameters, Jaccard fitness, cutoff 0.3")
+SINGLE128 = ("single_fire_128: 128x128 map, constant 45 deg wind, the "
+             "reference parameters, centre ignition, 64 replicates, int32 "
+             "burn-step maps")
+
+
+def run_small(args, kind):
+    """The two smaller configurations through their public calls: the
+    ignition search (one ignition_search call: lattice, 65,536 simulations,
+    fitness map and ignition estimate) and the 128 x 128 replicates (one
+    fire_simulate_batch with burn-step maps on device buffers).  The ALU
+    roofline takes its trial count from the same simulations run as one
+    batch."""
+    g = _setup_gpu()
+    if g is None:
+        print(json.dumps({"metric": METRIC, "error": "no CUDA device"}))
+        return 1
+    torch, fire, ctx, dev, stream, rank, world, local = g
+    preset = "ignition_search_1024" if kind == "ignition" else "single_fire_128"
+    land = synth.preset_landscape(preset)
+    H, W = land.veg.shape
+    m = ctx.landscape_upload(land)
+    ign0 = synth.centre_ignition(land.veg)
+    tseed, target = _gpu_target(fire, m, ign0, int((land.veg != 0).sum()))
+    m.target_upload(target)
+    beta = np.asarray(synth.TRUTH_BETA, np.float64)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    nsteps = args.warmup + args.steps
+    first = parallel.rank_seed_offset(rank, 1 << 24)
+    if kind == "ignition":
+        p = synth.PRESETS[preset]
+        LH = LW = p["lattice"]
+        reps = p["replicates"]
+        n = LH * LW * reps
+        _, cells, _ = fire.ignition_search(ctx, m, beta, LH, LW, reps, first,
+                                           kind=fire.FITNESS_JACCARD, cutoff=0.3)
+        ign = np.repeat(cells.reshape(-1, 2), reps, axis=0).astype(np.int32)
+        params = np.tile(beta, (n, 1))
+        seeds = np.arange(first, first + n, dtype=np.uint64)
+        tuned = _forced_launch(args, ctx) or fire.fire_autotune(
+            ctx, [m], None, params, ign, seeds)
+
+        def call(k):
+            fire.ignition_search(ctx, m, beta, LH, LW, reps, first + k * n,
+                                 kind=fire.FITNESS_JACCARD, cutoff=0.3)
+        h2d, d2h = 0, 8 * (LH * LW) + 8 * (LH * LW) + 32
+    else:
+        n = synth.PRESETS[preset]["n_sims"]
+        ign = np.tile(np.asarray(ign0, np.int32), (n, 1))
+        params = np.tile(beta, (n, 1))
+        seeds = np.arange(first, first + n, dtype=np.uint64)
+        tuned = _forced_launch(args, ctx) or fire.fire_autotune(
+            ctx, [m], None, params, ign, seeds)
+        p_dev = torch.tensor(params, device=dev)
+        g_dev = torch.tensor(ign, device=dev)
+        s_dev = torch.empty(n, dtype=torch.int64, device=dev)
+        out = torch.zeros((n, 6), dtype=torch.int32, device=dev)
+        bsd = torch.zeros((n, H, W), dtype=torch.int32, device=dev)
+        s_all = [torch.tensor((seeds + np.uint64(k * n)).view(np.int64),
+                              device=dev) for k in range(nsteps)]
+
+        def call(k):
+            s_dev.copy_(s_all[k])
+            m.simulate_batch(p_dev, g_dev, s_dev, device=True, out=out,
+                             want_steps=True, burn_step=bsd)
+        h2d, d2h = n * 56, n * 24 + n * H * W * 4
+    for k in range(args.warmup):
+        flush.zero_()
+        call(k)
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    ev = [(torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    wall = 0.0
+    for j in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ev[j][0].record(stream)
+        call(args.warmup + j)
+        ev[j][1].record(stream)
+        torch.cuda.synchronize()
+        wall += time.perf_counter() - t0
+    ck = clocks.stop()
+    dev_s = sum(a.elapsed_time(b) for a, b in ev) / 1e3
+    total_s = parallel.max_over_ranks(dev_s, world, dev)
+    wall = parallel.max_over_ranks(wall, world, dev)
+    value = n * args.steps * world / total_s
+    # the same simulations as one batch: trials and kernel time of the
+    # ALU roofline
+    t_p = torch.tensor(params, device=dev)
+    t_g = torch.tensor(ign, device=dev)
+    t_s = torch.tensor(seeds.view(np.int64), device=dev)
+    t_o = torch.zeros((n, 6), dtype=torch.int32, device=dev)
+    m.simulate_batch(t_p, t_g, t_s, device=True, out=t_o)
+    flush.zero_()
+    e0, e1 = (torch.cuda.Event(enable_timing=True) for _ in range(2))
+    e0.record(stream)
+    m.simulate_batch(t_p, t_g, t_s, device=True, out=t_o)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    r = fire.results_view(t_o)
+    trials = int(r["trials"].astype(np.int64).sum())
+    steps_sum = int(r["steps"].astype(np.int64).sum())
+    if rank == 0:
+        peaks, pk, roof = _alu_roof(torch, dev, trials, e0.elapsed_time(e1) / 1e3)
+        roof["traffic"] = None
+        roof["timed"] = ("the simulations of one step as one "
+                         "fire_simulate_batch launch, CUDA events")
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total_s / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u32", "data": "synthetic",
+            "config": {"workload": IGNITION if kind == "ignition" else SINGLE128,
+                       "H": H, "W": W, "sims_per_step": n, "l2": L2_NOTE,
+                       "parallelism": f"replicas x{world}"},
+            "launch": {k: tuned[k] for k in ("warps_per_block", "blocks_per_sm",
+                                             "queue_entries", "state_mode",
+                                             "forced") if k in tuned},
+            "target_seed": int(tseed), "target_cells": int(target.sum()),
+            "cell_updates_per_s": steps_sum * H * W * args.steps / total_s,
+            "trials_per_s": trials * args.steps / total_s,
+            "mean_steps_per_sim": steps_sum / n,
+            "roofline": roof,
+            "cpu_baseline": None,
+            "e2e": {"value": n * args.steps * world / wall, "unit": UNIT,
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "timed": ("the whole ignition_search call (host outputs), "
+                              "wall clock" if kind == "ignition" else
+                              "fire_simulate_batch with the seed copy, wall "
+                              "clock")},
+            "clocks": ck,
+        }
+        print(json.dumps(line))
+    m.free()
+    ctx.close()
+    return 0
+
+
 SURROGATE = ("surrogate_screened_ga_1024: 1024x1024 map (spatially varying "
              "wind), target from the reference parameters at the centre "
              "ignition; BF16 surrogate (S=256, ~1.05M params) trained on "
@@ -1449,12 +1594,15 @@ def main():
                     help="time every K-th simulation of the workload only (a "
                          "reduced batch for profiling; not a headline line)")
     ap.add_argument("--workload",
-                    choices=("uneven", "ga512", "recover", "burnout",
-                             "surrogate", "surrogate_step", "crossover"),
+                    choices=("uneven", "ga512", "ignition", "single128",
+                             "recover", "burnout", "surrogate",
+                             "surrogate_step", "crossover"),
                     default="uneven",
                     help="uneven (default): nine fires 200x300..2000x1500, "
                          "100k simulations in one launch; ga512: one "
-                         "512x512 GA generation; recover: parameter "
+                         "512x512 GA generation; ignition: the 1024x1024 "
+                         "ignition search; single128: 64 replicates on "
+                         "128x128 with burn-step maps; recover: parameter "
                          "recovery of the GAs; surrogate: the "
                          "surrogate-screened GA against the plain GA; "
                          "surrogate_step: the surrogate network alone; "
@@ -1479,6 +1627,8 @@ def main():
         return run_reference(args)
     if args.workload == "ga512":
         return run_ga512(args)
+    if args.workload in ("ignition", "single128"):
+        return run_small(args, args.workload)
     if args.workload == "recover":
         return run_recover(args)
     if args.workload == "burnout":
