@@ -176,12 +176,12 @@ def test_philox_matches_curand_raw_blocks(ctx, orc, tmp_path):
 
 
 def _check_batch(ctx, orc, land, params, ignitions, seeds, target=None,
-                 max_steps=0, warps=0, bps=0):
+                 max_steps=0, warps=0, bps=0, state=0):
     F = orc.Features(land)
     m = ctx.landscape_upload(land)
     if target is not None:
         m.target_upload(target)
-    ctx.set_launch(warps, bps)
+    ctx.set_launch(warps, bps, 0, state)
     try:
         res, bs = m.simulate_batch(params, ignitions, seeds, want_steps=True,
                                    max_steps=max_steps)
@@ -221,6 +221,29 @@ def test_trajectories_ragged_grids(ctx, orc, shape, seed):
     seeds = rng.integers(1, 2 ** 63, n, dtype=np.uint64)
     target = rng.random(shape) < 0.3
     _check_batch(ctx, orc, land, params, ign, seeds, target=target)
+
+
+@pytest.mark.parametrize("shape,seed,state", [((96, 160), 21, 0),
+                                              ((130, 70), 22, 2)])
+def test_trajectories_saturated_thresholds(ctx, orc, shape, seed, state):
+    """Parameters whose z reaches the saturated ranges of the threshold
+    (z >= 37: 1 + e^-z rounds to 1, T = 2^32 and every draw succeeds;
+    z <= -22.5: T = 0 and every draw fails), mixed with Uniform[-30, 30]
+    draws, cases next to those bounds and magnitudes up to 2 10^6, in shared
+    and global state: trajectories and counts equal the oracle's."""
+    land = synth.landscape(*shape, seed=seed, wind_seed=seed)
+    rng = np.random.default_rng(seed)
+    edge = [[25.0, 10, 5, 8, 0], [30.0, -10, 8, 12, 3], [38.0, 0, 0, 0, 0],
+            [36.9, 0, 0, 1.0, 0], [-22.0, 0, 0, 30, 0], [-5.0, 0, 0, 40, 0],
+            [9.0e5, 0, 0, 0, 0], [2.0e6, 0, 0, 0, 0]]
+    n = 28
+    params = np.concatenate([rng.uniform(-30, 30, (n - len(edge), 5)), edge])
+    burnable = np.argwhere(land.veg != 0)
+    ign = burnable[rng.integers(0, len(burnable), n)].astype(np.int32)
+    seeds = rng.integers(1, 2 ** 63, n, dtype=np.uint64)
+    target = rng.random(shape) < 0.3
+    _check_batch(ctx, orc, land, params, ign, seeds, target=target,
+                 state=state)
 
 
 def test_ignitions_on_edges_and_corners(ctx, orc):
