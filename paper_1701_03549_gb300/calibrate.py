@@ -188,6 +188,95 @@ def run_ga(ctx, m, ignition, pop=256, reps=16, generations=50,
     return hist
 
 
+def scar_layout(pop: int, scars: int, reps: int) -> np.ndarray:
+    """Scar index of every simulation of a multi-scar generation: individual
+    i, scar k, replicate r is simulation (i K + k) R + r."""
+    return np.tile(np.repeat(np.arange(scars, dtype=np.int32), reps), pop)
+
+
+def evaluate_multi(ctx, maps, params_dev, ignitions, seeds, reps, kind, torch):
+    """Mean fitness of each parameter vector over several reference scars:
+    every individual is simulated `reps` times on each scar k (maps[k] holds
+    that scar's landscape and target burnt map, ignitions[k] its ignition),
+    in one uneven-batch launch; each simulation is scored against its own
+    scar's target and an individual's fitness is the mean over its K x reps
+    simulations (scar-major, then replicate order)."""
+    dev = params_dev.device
+    P = params_dev.shape[0]
+    K = len(maps)
+    n = P * K * reps
+    mos = scar_layout(P, K, reps)
+    p_sims = params_dev.repeat_interleave(K * reps, dim=0).contiguous()
+    t_mos = torch.tensor(mos, device=dev)
+    t_ign = torch.tensor(np.asarray(ignitions, np.int32).reshape(K, 2)[mos],
+                         device=dev)
+    s = torch.tensor(np.asarray(seeds, np.uint64).view(np.int64), device=dev)
+    out = torch.zeros((n, 6), dtype=torch.int32, device=dev)
+    fit = torch.zeros(n, dtype=torch.float64, device=dev)
+    mean = torch.zeros(P, dtype=torch.float64, device=dev)
+    torch.cuda.synchronize(dev)
+    fire.fire_simulate_multi(ctx, maps, t_mos, p_sims, t_ign, s, device=True,
+                             out=out)
+    fire.fire_fitness(ctx, out, kind, device=True, out=fit)
+    fire.fire_group_mean(ctx, fit, K * reps, device=True, out=mean)
+    ctx.sync()
+    return mean
+
+
+def run_ga_multi(ctx, maps, ignitions, pop=256, reps=8, generations=50,
+                 prior="gauss", lo=-30.0, hi=30.0, ga_seed=1, sim_seed=1,
+                 kind=fire.FITNESS_JACCARD, init=None, checkpoint=None,
+                 stop_after=None):
+    """The Appendix B genetic algorithm fitted to several reference scars at
+    once (the paper's suggestion for parameters one scar leaves weakly
+    determined, Sec. 4): the fitness of an individual is its mean over the
+    scars of the replicate-mean fitness against each scar (evaluate_multi);
+    selection, crossover and mutation are those of run_ga.  maps[k] holds
+    scar k's landscape and target, ignitions[k] its ignition (row, col).
+    Seeds of generation g: sim_seeds(sim_seed, g, pop, K reps).
+    checkpoint and stop_after as in run_ga."""
+    import torch
+
+    dev = torch.device("cuda", ctx.device)
+    G = 5
+    K = len(maps)
+    meta = _meta("ga5multi", pop=pop, reps=reps, generations=generations,
+                 prior=prior, lo=lo, hi=hi, ga_seed=ga_seed,
+                 sim_seed=sim_seed, kind=int(kind), scars=K,
+                 ignitions=[list(map(int, g)) for g in ignitions],
+                 custom_init=init is not None)
+    if init is None:
+        init = (synth.gauss_population(pop, ga_seed) if prior == "gauss"
+                else synth.uniform_population(pop, ga_seed, lo=lo, hi=hi))
+    init = np.clip(np.asarray(init, np.float64), lo, hi)
+    start, hist = 0, History()
+    if checkpoint and os.path.exists(checkpoint):
+        start, init, hist = load_checkpoint(checkpoint, meta)
+    genes = torch.tensor(init, dtype=torch.float64, device=dev)
+    nxt = torch.empty_like(genes)
+    tlo = torch.full((G,), float(lo), dtype=torch.float64, device=dev)
+    thi = torch.full((G,), float(hi), dtype=torch.float64, device=dev)
+    for g in range(start, generations):
+        t0 = time.perf_counter()
+        f = evaluate_multi(ctx, maps, genes, ignitions,
+                           sim_seeds(sim_seed, g, pop, K * reps), reps, kind,
+                           torch)
+        hist.params.append(genes.cpu().numpy())
+        hist.fitness.append(f.cpu().numpy())
+        if g + 1 < generations:
+            torch.cuda.synchronize(dev)
+            fire.ga_step(ctx, genes, f, g, generations, ga_seed, tlo, thi,
+                         device=True, out=nxt)
+            ctx.sync()
+            genes, nxt = nxt, genes
+        hist.seconds.append(time.perf_counter() - t0)
+        if checkpoint:
+            save_checkpoint(checkpoint, g + 1, genes.cpu().numpy(), hist, meta)
+        if stop_after is not None and g + 1 - start >= stop_after:
+            break
+    return hist
+
+
 def evaluate_at(ctx, m, params_dev, ign_dev, seeds, reps, kind, torch):
     """Mean fitness over `reps` replicates of each parameter vector, each
     replicate starting from its own ignition (ign_dev: (P reps, 2) int32

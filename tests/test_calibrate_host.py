@@ -23,3 +23,17 @@ def test_checkpoint_round_trip_and_run_identity(tmp_path):
     with pytest.raises(ValueError):
         calibrate.load_checkpoint(path, other)
     assert not (tmp_path / "ga.npz.tmp.npz").exists()
+
+
+def test_scar_layout_orders_individual_scar_replicate():
+    """Simulation j of a multi-scar generation belongs to individual
+    j // (K R) and scar (j // R) % K, so that one group mean of size K R per
+    individual averages over its scars and replicates."""
+    from paper_1701_03549_gb300 import calibrate
+
+    P, K, R = 3, 4, 2
+    lay = calibrate.scar_layout(P, K, R)
+    assert lay.dtype == np.int32 and lay.shape == (P * K * R,)
+    j = np.arange(P * K * R)
+    assert np.array_equal(lay, (j // R) % K)
+    assert np.array_equal(np.bincount(lay), np.full(K, P * R))

@@ -116,6 +116,55 @@ def test_ga_run_matches_oracle_driven_run(env):
     m.free()
 
 
+def test_multi_scar_ga_run_matches_oracle_driven_run(env):
+    """Three generations of population 6 fitted to three scars at once (two
+    ignitions on one map, one on a map of another size) x 2 replicates:
+    every generation's population and fitness equal those of the same run
+    with the oracle's simulation (each simulation against its own scar's
+    target), fitness, averaging over scars and replicates, and GA step."""
+    torch, fire, oracle, ctx = env
+    from paper_1701_03549_gb300 import calibrate
+
+    lands = [synth.landscape(48, 56, seed=31, wind_seed=31),
+             synth.landscape(48, 56, seed=31, wind_seed=31),
+             synth.landscape(40, 70, seed=32, wind_seed=32)]
+    ignitions = [synth.centre_ignition(lands[0].veg),
+                 tuple(int(v) for v in np.argwhere(lands[1].veg != 0)[300]),
+                 synth.centre_ignition(lands[2].veg)]
+    Fs, targets, maps = [], [], []
+    for land, ign in zip(lands, ignitions):
+        F = oracle.Features(land)
+        _, target = workloads.pick_target(
+            lambda s, F=F, ign=ign: F.simulate(synth.TRUTH_BETA, ign, s)[1] >= 0,
+            int(F.burnable.sum()))
+        m = ctx.landscape_upload(land)
+        m.target_upload(target)
+        Fs.append(F)
+        targets.append(target)
+        maps.append(m)
+    P, R, NG, K = 6, 2, 3, len(maps)
+    hist = calibrate.run_ga_multi(ctx, maps, ignitions, pop=P, reps=R,
+                                  generations=NG, ga_seed=13, sim_seed=7)
+    genes = np.clip(synth.gauss_population(P, 13), -30, 30)
+    lo, hi = np.full(5, -30.0), np.full(5, 30.0)
+    scar = calibrate.scar_layout(P, K, R)
+    for g in range(NG):
+        seeds = calibrate.sim_seeds(7, g, P, K * R)
+        fit = []
+        for j in range(P * K * R):
+            k = int(scar[j])
+            o, _ = Fs[k].simulate(genes[j // (K * R)], ignitions[k],
+                                  int(seeds[j]), target=targets[k],
+                                  want_steps=False)
+            fit.append(oracle.fitness(o["burnt"], o["inter"], o["target"], 1))
+        f = oracle.group_mean(np.asarray(fit), K * R)
+        assert np.array_equal(hist.params[g], genes), g
+        assert np.array_equal(hist.fitness[g], f), g
+        genes = oracle.ga_step(genes, f, g, NG, 13, lo, hi)
+    for m in maps:
+        m.free()
+
+
 def test_ga_improves_fitness_on_a_synthetic_scar(env):
     torch, fire, oracle, ctx = env
     from paper_1701_03549_gb300 import calibrate
