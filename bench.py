@@ -1478,6 +1478,106 @@ def _ga_report(hist, truth, sims_per_gen):
             "final_rel_error": [round(float(x), 4) for x in errs[-1]]}
 
 
+RECOVER_MULTI = ("recover_multi_1024: 1024x1024 map (spatially varying "
+                 "wind); four reference scars of the reference parameters "
+                 "(Table 2) ignited at the burnable cells nearest the quarter "
+                 "points, then the points at 1/8, 7/8 and at 3/8, 5/8 of each "
+                 "side and the centre (the first four whose fire burns >= 1% "
+                 "of the burnable cells for some target seed); "
+                 "plain GA population 1024 fitted to the four "
+                 "scars at once (4 x 8 replicates per individual) against the "
+                 "same GA on the first scar alone (32 replicates), 50 "
+                 "generations each, equal automaton runs per generation")
+
+
+def _nearest_burnable(veg, r, c):
+    """Burnable cell nearest (r, c) (Euclidean; ties to the lower index)."""
+    cells = np.argwhere(np.asarray(veg) != 0)
+    d = (cells[:, 0] - r) ** 2 + (cells[:, 1] - c) ** 2
+    return tuple(int(v) for v in cells[int(np.argmin(d))])
+
+
+def run_recover_multi(args):
+    """Parameter recovery from several scars at once (the paper's suggestion
+    for parameters a single scar leaves weakly determined, Sec. 4) against
+    one scar, at the same number of automaton runs per generation."""
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_1701_03549_gb300 import calibrate, fire
+
+    rank, world, local = parallel.env_rank()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    ctx = fire.Context(local, stream)
+    truth = np.asarray(synth.TRUTH_BETA, np.float64)
+    land = synth.preset_landscape("ignition_search_1024")
+    H, W = land.veg.shape
+    # scar ignitions: the burnable cells nearest the quarter points, then the
+    # points at 1/8 and 7/8, at 3/8 and 5/8 of each side and the centre,
+    # keeping the first four whose reference fire burns at least 1 % of the
+    # burnable cells for some target seed (many fires of the reference
+    # parameters die out early)
+    fr = [(0.25, 0.75), (0.125, 0.875), (0.375, 0.625)]
+    pts = [(int(a * H), int(b * W)) for lo, hi in fr
+           for a, b in ((lo, lo), (lo, hi), (hi, lo), (hi, hi))]
+    pts.append((H // 2, W // 2))
+    ignitions, maps, tseeds, sizes = [], [], [], []
+    for r, c in pts:
+        if len(maps) == 4:
+            break
+        ign = _nearest_burnable(land.veg, r, c)
+        if ign in ignitions:
+            continue
+        m = ctx.landscape_upload(land)
+        try:
+            ts, tg = _gpu_target(fire, m, ign, int((land.veg != 0).sum()))
+        except RuntimeError:
+            m.free()
+            continue
+        m.target_upload(tg)
+        ignitions.append(ign)
+        maps.append(m)
+        tseeds.append(int(ts))
+        sizes.append(int(tg.sum()))
+    gens = args.generations
+    clocks = Clocks(local)
+    multi = calibrate.run_ga_multi(ctx, maps, ignitions, pop=1024, reps=8,
+                                   generations=gens, ga_seed=5,
+                                   sim_seed=1 << 40)
+    single = calibrate.run_ga(ctx, maps[0], ignitions[0], pop=1024, reps=32,
+                              generations=gens, ga_seed=5, sim_seed=1 << 41)
+    ck = clocks.stop()
+    rm = _ga_report(multi, truth, 1024 * 32)
+    rs = _ga_report(single, truth, 1024 * 32)
+    line = {
+        "metric": "time-to-recover 5 params (each within 5% of the reference "
+                  "value), plain GA population 1024 fitted to four scars",
+        "value": rm["recovered_all_s"], "unit": "s", "n_gpus": world,
+        "steps": gens, "warmup": 0,
+        "ms_per_step": 1e3 * rm["seconds"] / gens, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic",
+        "config": {"workload": RECOVER_MULTI, "ignitions": ignitions,
+                   "target_seeds": tseeds, "target_cells": sizes,
+                   "reference": list(truth),
+                   "estimate": "mean of the best 10% of a generation"},
+        "four_scars": rm, "one_scar": rs,
+        "cpu_baseline": None, "e2e": None, "gpu_launches": None,
+        "clocks": ck,
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    for m in maps:
+        m.free()
+    ctx.close()
+    return 0
+
+
 def run_recover(args):
     """Parameter recovery against the reference parameters (Table 2 layout
     per generation; Table 3 layout for the variable-ignition GA) and the GA
@@ -1595,14 +1695,15 @@ def main():
                          "reduced batch for profiling; not a headline line)")
     ap.add_argument("--workload",
                     choices=("uneven", "ga512", "ignition", "single128",
-                             "recover", "burnout", "surrogate",
-                             "surrogate_step", "crossover"),
+                             "recover", "recover_multi", "burnout",
+                             "surrogate", "surrogate_step", "crossover"),
                     default="uneven",
                     help="uneven (default): nine fires 200x300..2000x1500, "
                          "100k simulations in one launch; ga512: one "
                          "512x512 GA generation; ignition: the 1024x1024 "
                          "ignition search; single128: 64 replicates on "
-                         "128x128 with burn-step maps; recover: parameter "
+                         "128x128 with burn-step maps; recover_multi: the "
+                         "GA fitted to four scars at once; recover: parameter "
                          "recovery of the GAs; surrogate: the "
                          "surrogate-screened GA against the plain GA; "
                          "surrogate_step: the surrogate network alone; "
@@ -1631,6 +1732,8 @@ def main():
         return run_small(args, args.workload)
     if args.workload == "recover":
         return run_recover(args)
+    if args.workload == "recover_multi":
+        return run_recover_multi(args)
     if args.workload == "burnout":
         return run_burnout(args)
     if args.workload == "surrogate":
