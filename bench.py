@@ -849,7 +849,8 @@ def run_small(args, kind):
         def call(k):
             fire.ignition_search(ctx, m, beta, LH, LW, reps, first + k * n,
                                  kind=fire.FITNESS_JACCARD, cutoff=0.3)
-        h2d, d2h = 0, 8 * (LH * LW) + 8 * (LH * LW) + 32
+        h2d, d2h = 40, 8 * (LH * LW) + 8 * (LH * LW) + 32
+        e2e_call = call
     else:
         n = synth.PRESETS[preset]["n_sims"]
         ign = np.tile(np.asarray(ign0, np.int32), (n, 1))
@@ -870,6 +871,13 @@ def run_small(args, kind):
             m.simulate_batch(p_dev, g_dev, s_dev, device=True, out=out,
                              want_steps=True, burn_step=bsd)
         h2d, d2h = n * 56, n * 24 + n * H * W * 4
+        pin_p = _pinned(torch, params)
+        pin_g = _pinned(torch, ign)
+        pin_s = [_pinned(torch, seeds + np.uint64(k * n)) for k in range(nsteps)]
+
+        def e2e_call(k):
+            # host buffers: inputs copied in, results and burn-step maps out
+            m.simulate_batch(pin_p, pin_g, pin_s[k], want_steps=True)
     for k in range(args.warmup):
         flush.zero_()
         call(k)
@@ -888,6 +896,14 @@ def run_small(args, kind):
         torch.cuda.synchronize()
         wall += time.perf_counter() - t0
     ck = clocks.stop()
+    if kind != "ignition":   # end to end through host buffers, same seeds
+        wall = 0.0
+        for j in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            e2e_call(args.warmup + j)
+            wall += time.perf_counter() - t0
     dev_s = sum(a.elapsed_time(b) for a, b in ev) / 1e3
     total_s = parallel.max_over_ranks(dev_s, world, dev)
     wall = parallel.max_over_ranks(wall, world, dev)
@@ -935,8 +951,11 @@ def run_small(args, kind):
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "timed": ("the whole ignition_search call (host outputs), "
                               "wall clock" if kind == "ignition" else
-                              "fire_simulate_batch with the seed copy, wall "
-                              "clock")},
+                              "fire_simulate_batch on pinned host buffers "
+                              "(parameters, ignitions and seeds in; results "
+                              "and burn-step maps out), wall clock per call, "
+                              "with the seeds and L2 flush of the "
+                              "device-timed steps")},
             "clocks": ck,
         }
         print(json.dumps(line))

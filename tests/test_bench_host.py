@@ -153,3 +153,14 @@ def test_crossover_side_interpolates_log_log():
     assert bench._crossover_side(sides, per, 0.04) == pytest.approx(1024)
     assert bench._crossover_side(sides, per, 0.005) is None
     assert bench._crossover_side(sides, per, 0.2) is None
+
+
+def test_nearest_burnable_cell_and_tie_rule():
+    """Scar ignitions of the multi-scar recovery: the burnable cell nearest a
+    point, ties to the lower (row-major) index."""
+    veg = np.zeros((7, 9), np.uint8)
+    veg[2, 3] = veg[2, 5] = veg[6, 8] = 1
+    assert bench._nearest_burnable(veg, 2, 4) == (2, 3)   # tie: lower index
+    assert bench._nearest_burnable(veg, 2, 5) == (2, 5)
+    assert bench._nearest_burnable(veg, 6, 6) == (6, 8)
+
