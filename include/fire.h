@@ -293,7 +293,7 @@ typedef struct {
  * map_of_sim is then ignored) to time the shapes as fire_simulate_batch runs
  * with that flag.  Each shape
  * runs once untimed and twice timed (the better time counts): the batch runs
- * about thirty times. */
+ * three times per shape, twelve shapes (fewer when a shape does not fit). */
 FIRE_API int fire_autotune(fire_ctx *ctx, int nmaps, const fire_map *const *maps,
                            const int32_t *map_of_sim, int n,
                            const fire_params *params, const fire_cell *ignitions,
