@@ -285,11 +285,12 @@ def test_seven_gene_ga_run_matches_oracle_driven_run(env):
     m.free()
 
 
-@pytest.mark.parametrize("genes7", [False, True])
+@pytest.mark.parametrize("genes7", [False, True, "scars"])
 def test_checkpoint_resume_is_bit_identical(env, tmp_path, genes7):
     """A GA run stopped after two of five generations and resumed from its
     checkpoint ends with exactly the populations and fitness of the run that
-    was never interrupted (five and seven genes)."""
+    was never interrupted (five and seven genes, and five genes fitted to two
+    scars)."""
     torch, fire, oracle, ctx = env
     from paper_1701_03549_gb300 import calibrate
 
@@ -305,7 +306,21 @@ def test_checkpoint_resume_is_bit_identical(env, tmp_path, genes7):
     burnable = land.veg != 0
     path = str(tmp_path / "ga.npz")
 
+    m2 = None
+    if genes7 == "scars":
+        ign2 = tuple(int(v) for v in np.argwhere(burnable)[500])
+        m2 = ctx.landscape_upload(land)
+        _, bs2 = m2.simulate_batch(np.asarray([synth.TRUTH_BETA]),
+                                   np.asarray([ign2], np.int32),
+                                   np.asarray([synth.TARGET_SEED], np.uint64),
+                                   want_steps=True)
+        m2.target_upload(bs2[0] >= 0)
+
     def run(**kw):
+        if genes7 == "scars":
+            return calibrate.run_ga_multi(ctx, [m, m2], [ign, ign2], pop=12,
+                                          reps=2, generations=5, ga_seed=2,
+                                          sim_seed=3, **kw)
         if genes7:
             return calibrate.run_ga_ignition(ctx, m, target, burnable, pop=12,
                                              reps=2, generations=5, ga_seed=2,
@@ -322,3 +337,5 @@ def test_checkpoint_resume_is_bit_identical(env, tmp_path, genes7):
         assert np.array_equal(resumed.params[g], full.params[g]), g
         assert np.array_equal(resumed.fitness[g], full.fitness[g]), g
     m.free()
+    if m2 is not None:
+        m2.free()
