@@ -690,10 +690,18 @@ __global__ void __launch_bounds__(kSimMaxThreads, 2) k_simulate(SimLaunch a)
             const uint4 *src = reinterpret_cast<const uint4 *>(m.blk);
             uint4 *dx = reinterpret_cast<uint4 *>(s.X);
             uint4 *dy = reinterpret_cast<uint4 *>(s.Y);
-            for (int i = threadIdx.x; i < m.ntiles * 8; i += blockDim.x) {
-                const uint4 v = src[i];
-                dx[i] = v;
-                dy[i] = v;
+            // two 16-byte loads in flight per thread before their stores
+            const int n16 = m.ntiles * 8, bd = blockDim.x;
+            for (int i = threadIdx.x; i < n16; i += 2 * bd) {
+                const bool two = i + bd < n16;
+                const uint4 v0 = src[i];
+                const uint4 v1 = two ? src[i + bd] : v0;
+                dx[i] = v0;
+                dy[i] = v0;
+                if (two) {
+                    dx[i + bd] = v1;
+                    dy[i + bd] = v1;
+                }
             }
             if (kBurn) {
                 uint4 *dk = reinterpret_cast<uint4 *>(s.K0);
@@ -822,19 +830,45 @@ __global__ void __launch_bounds__(kSimMaxThreads, 2) k_simulate(SimLaunch a)
         __syncthreads();
         uint32_t nb = 0, ni = 0;
         bool border = false;
-        for (int w = threadIdx.x; w < m.ntiles * 32; w += blockDim.x) {
-            const uint32_t bw = (s.X[w] | s.Y[w]) & ~__ldg(&m.blk[w]);
-            if (a.burnt_bits)
+        if (a.burnt_bits) {
+            for (int w = threadIdx.x; w < m.ntiles * 32; w += blockDim.x) {
+                const uint32_t bw = (s.X[w] | s.Y[w]) & ~__ldg(&m.blk[w]);
                 a.burnt_bits[(long long)sim * m.ntiles * 32 + w] = bw;
-            if (!bw) continue;
-            nb += __popc(bw);
-            ni += __popc(bw & __ldg(&m.tgt[w]));
-            const int k = w >> 5;
-            const int ti = tile_row(sh, k), tj = k - ti * m.TW;
-            const int R = ti * 32 + (w & 31);
-            if (R == 0 || R == m.H - 1 || (tj == 0 && (bw & 1u)) ||
-                (tj == m.TW - 1 && ((bw >> ((m.W - 1) & 31)) & 1u)))
-                border = true;
+                if (!bw) continue;
+                nb += __popc(bw);
+                ni += __popc(bw & __ldg(&m.tgt[w]));
+                const int k = w >> 5;
+                const int ti = tile_row(sh, k), tj = k - ti * m.TW;
+                const int R = ti * 32 + (w & 31);
+                if (R == 0 || R == m.H - 1 || (tj == 0 && (bw & 1u)) ||
+                    (tj == m.TW - 1 && ((bw >> ((m.W - 1) & 31)) & 1u)))
+                    border = true;
+            }
+        } else {
+            // four consecutive rows of one tile per thread (16-byte loads)
+            const uint4 *X4 = reinterpret_cast<const uint4 *>(s.X);
+            const uint4 *Y4 = reinterpret_cast<const uint4 *>(s.Y);
+            const uint4 *B4 = reinterpret_cast<const uint4 *>(m.blk);
+            const uint4 *T4 = reinterpret_cast<const uint4 *>(m.tgt);
+            for (int v = threadIdx.x; v < m.ntiles * 8; v += blockDim.x) {
+                const uint4 x = X4[v], y = Y4[v], bl = __ldg(&B4[v]);
+                const uint32_t bw[4] = {(x.x | y.x) & ~bl.x, (x.y | y.y) & ~bl.y,
+                                        (x.z | y.z) & ~bl.z, (x.w | y.w) & ~bl.w};
+                if (!(bw[0] | bw[1] | bw[2] | bw[3])) continue;
+                const uint4 tg = __ldg(&T4[v]);
+                nb += __popc(bw[0]) + __popc(bw[1]) + __popc(bw[2]) + __popc(bw[3]);
+                ni += __popc(bw[0] & tg.x) + __popc(bw[1] & tg.y) +
+                      __popc(bw[2] & tg.z) + __popc(bw[3] & tg.w);
+                const int k = v >> 3;
+                const int ti = tile_row(sh, k), tj = k - ti * m.TW;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int R = ti * 32 + ((v & 7) << 2) + j;
+                    if (bw[j] && (R == 0 || R == m.H - 1 || (tj == 0 && (bw[j] & 1u)) ||
+                                  (tj == m.TW - 1 && ((bw[j] >> ((m.W - 1) & 31)) & 1u))))
+                        border = true;
+                }
+            }
         }
         nb = __reduce_add_sync(kFull, nb);
         ni = __reduce_add_sync(kFull, ni);
