@@ -74,12 +74,27 @@ def _peaks():
                 "sm_max_mhz": 2070.0}, "fallback"
 
 
+def _strip_comments(src: str) -> str:
+    """C/C++ source without its comments and blank-line runs (string and
+    character literals kept), so that a record of the kernel's counters stays
+    valid across edits of its comments only."""
+    import re
+
+    pat = re.compile(r'//[^\n]*|/\*.*?\*/|"(?:\\.|[^"\\])*"|\'(?:\\.|[^\'\\])*\'',
+                     re.S)
+    out = pat.sub(lambda m: m.group(0) if m.group(0)[0] in "\"'" else " ", src)
+    lines = [ln.rstrip() for ln in out.splitlines()]
+    return "\n".join(ln for ln in lines if ln.strip())
+
+
 def _kernel_hash():
+    """SHA-256 of the simulation kernel's sources (code only, comments
+    stripped): the key of the committed ncu records."""
     h = hashlib.sha256()
     for f in ("fire_kernels.cu", "fire_device.cuh", "fire_internal.h"):
         with open(os.path.join(ROOT, "paper_1701_03549_gb300", "csrc", f),
-                  "rb") as fh:
-            h.update(fh.read())
+                  encoding="utf-8") as fh:
+            h.update(_strip_comments(fh.read()).encode())
     return h.hexdigest()
 
 

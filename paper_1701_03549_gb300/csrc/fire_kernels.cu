@@ -12,7 +12,9 @@
 //    cells coded "burning, parity t"; a tile's owner warp writes new cells
 //    with the other parity code and retires the previous step's burning cells
 //    to 11, and neither write changes the parity-t burning set that other
-//    warps read across tile edges.  One block barrier per step suffices.
+//    warps read across tile edges.  Each step has two phases separated by
+//    block barriers: the tile scans (phase A) fill the block's candidate
+//    queue, the block's threads then decide the queued candidates (phase B).
 //  * Frontier: a worklist of active tiles per step (tiles holding burning
 //    cells, tiles bordering them across an edge that has burning cells, and
 //    tiles whose burning cells must be retired), deduplicated with per-tile
@@ -25,8 +27,11 @@
 //    (cell, step, d/4, 0), key = seed) and decides each trial through the
 //    single-precision screen, falling back to the exact double-precision
 //    threshold only near the decision boundary.
-//  * Fused fitness: |A*| and |A n A*| are accumulated as cells ignite, by
-//    popcount of the new-cell words against the target bit plane.
+//  * Fused fitness: at extinction a final sweep of the planes popcounts the
+//    burnt cells and those also in the target bit plane (|A*| and |A n A*|
+//    of Eq. 2) and records whether the fire reached the grid's border.
+//  * Draws: every trial of a simulation uses the same Philox key, so the
+//    key schedule (ten round keys) is computed once per simulation.
 #include <cstdio>
 
 #include "fire_device.cuh"

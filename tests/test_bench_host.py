@@ -164,3 +164,16 @@ def test_nearest_burnable_cell_and_tie_rule():
     assert bench._nearest_burnable(veg, 2, 5) == (2, 5)
     assert bench._nearest_burnable(veg, 6, 6) == (6, 8)
 
+
+
+def test_kernel_hash_ignores_comments_only():
+    """The key of the committed ncu records hashes the kernel's code with its
+    comments stripped: editing a comment keeps it, editing code changes it,
+    and comment markers inside literals are code."""
+    a = "int f(int x) {  // add one\n    return x + 1; /* done */\n}\n"
+    b = "/* header */\nint f(int x) {\n\n    return x + 1;   // changed note\n}\n"
+    c = "int f(int x) {\n    return x + 2;\n}\n"
+    assert bench._strip_comments(a) == bench._strip_comments(b)
+    assert bench._strip_comments(a) != bench._strip_comments(c)
+    s = 'const char *p = "// kept"; char q = \'/\';'
+    assert bench._strip_comments(s) == s
