@@ -177,3 +177,25 @@ def test_kernel_hash_ignores_comments_only():
     assert bench._strip_comments(a) != bench._strip_comments(c)
     s = 'const char *p = "// kept"; char q = \'/\';'
     assert bench._strip_comments(s) == s
+
+
+def test_forced_launch_option():
+    """--launch W,B,Q,S sets that shape on the context in place of the
+    autotuner's pick; without it the autotuner decides."""
+    class Ctx:
+        def __init__(self):
+            self.shape = None
+
+        def set_launch(self, *a):
+            self.shape = a
+
+    class Args:
+        launch = "8,4,3072,2"
+
+    c = Ctx()
+    t = bench._forced_launch(Args(), c)
+    assert c.shape == (8, 4, 3072, 2)
+    assert (t["warps_per_block"], t["blocks_per_sm"], t["queue_entries"],
+            t["state_mode"], t["forced"]) == (8, 4, 3072, 2, True)
+    Args.launch = ""
+    assert bench._forced_launch(Args(), Ctx()) is None
