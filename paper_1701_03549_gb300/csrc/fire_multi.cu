@@ -261,7 +261,7 @@ int fire_autotune(fire_ctx *ctx, int nmaps, const fire_map *const *maps,
         {8, 4, 4096, FIRE_STATE_GLOBAL},  {8, 4, 3072, FIRE_STATE_GLOBAL},
         {6, 5, 3072, FIRE_STATE_GLOBAL},
         {4, 8, 3072, FIRE_STATE_GLOBAL},  {4, 8, 2048, FIRE_STATE_GLOBAL},
-        {2, 16, 1536, FIRE_STATE_GLOBAL},
+        {2, 16, 1024, FIRE_STATE_GLOBAL},
     };
     const int saved[4] = {ctx->warps_per_block, ctx->blocks_per_sm,
                           ctx->queue_entries, ctx->state_mode};
